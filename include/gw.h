@@ -1,0 +1,263 @@
+/*
+ * gw.h -- C ABI of libgw, the GB300 (sm_103a) hot path of the CNT-GW
+ * entropic Gromov-Wasserstein solver of "Gromov-Wasserstein at Scale,
+ * Beyond Squared Norms" (arXiv 2602.06658).
+ *
+ * Notation (the paper's, Section 5 "Notations" and Algorithm 1):
+ *   a (N), b (M)         probability weights of the source / target measures
+ *   X (N x D), Y (M x E) centered embeddings: sum_i a_i X_i = 0,
+ *                        c_X(x_i, x_k) = ||X_i - X_k||^2 (Eqs. embedding_X/Y)
+ *   s_i = ||X_i||^2, t_j = ||Y_j||^2
+ *   Gamma (D x E)        the linear map of Theorems 3.2-3.4
+ *   f (N), g (M)         dual potentials; the plan is never stored:
+ *                        pi_ij = a_i b_j exp((f_i + g_j - C_ij)/eps)
+ *                        (Eq. sinkhorn_pi)
+ *   C_ij = c_Gamma(i,j) = -16 X_i^T Gamma Y_j - 4 s_i t_j
+ *                        (Remark after Theorem 3.2, Eq. egw_otherform)
+ *
+ * Conventions for every entry point:
+ *   - Pointers are DEVICE pointers unless the argument name starts with h_.
+ *   - Matrices are dense row-major; features and potentials are float32,
+ *     Gamma and energy terms float64.
+ *   - The caller owns and allocates every input, output and workspace
+ *     buffer.  The library allocates no device memory.  Scratch comes from
+ *     the caller's workspace `ws` of `ws_bytes` bytes, sized by
+ *     gw_workspace_size(); a smaller workspace returns GW_ENOMEM.
+ *     Workspace pointers must be 256-byte aligned.
+ *   - All device work is enqueued on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) and is asynchronous unless stated.  Calls on
+ *     different streams with disjoint workspaces may run concurrently.
+ *   - Every function returns an int status (GW_OK = 0).  Arguments are
+ *     validated on the host before anything is enqueued; on error nothing is
+ *     enqueued and gw_last_error() describes the problem (per host thread).
+ *     No C++ exception or abort crosses this interface.
+ */
+#ifndef GW_H_
+#define GW_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gw_stream_t;
+
+/* status codes */
+#define GW_OK 0
+#define GW_EINVAL 1        /* bad shape, null pointer, eps <= 0, bad option */
+#define GW_ENOMEM 2        /* workspace too small or misaligned */
+#define GW_ECUDA 3         /* a CUDA launch or API call failed */
+#define GW_ENONFINITE 4    /* NaN/Inf met in potentials or energy */
+#define GW_ETIMEOUT 5      /* a bounded device wait expired */
+#define GW_EUNSUPPORTED 6  /* feature dimension or precision not supported */
+
+/* cost-tile precision of the softmin / plan kernels.  The log-sum-exp, the
+ * potentials and all accumulations stay float32 (Gamma and energies float64)
+ * in every mode. */
+#define GW_PREC_FP32 0     /* FP32 dot products on the CUDA cores */
+#define GW_PREC_BF16 1     /* BF16 operands on tcgen05, FP32 accumulate */
+#define GW_PREC_BF16X3 2   /* split BF16 (hi*hi + hi*lo + lo*hi) on tcgen05 */
+
+/* CNT penalties accepted by gw_lift (Section 2, "Embeddable costs") */
+#define GW_PEN_SQEUCLID 0  /* ||x - x'||^2: the lift is a centering */
+#define GW_PEN_POWER 1     /* ||x - x'||^p, 0 < p <= 2, p = param */
+#define GW_PEN_GAUSS 2     /* 2 (1 - exp(-||x - x'||^2 / (2 param^2))) */
+
+/* workspace queries (gw_workspace_size's `op`) */
+#define GW_OP_SOFTMIN 0
+#define GW_OP_CROSS_COV 1
+#define GW_OP_ENERGY 2
+#define GW_OP_SOLVE 3
+#define GW_OP_LIFT 4
+#define GW_OP_GRAD 5
+
+#define GW_MAX_FEATURES 128 /* largest D, E (and K) the kernels accept */
+
+/* Layout of the float64 energy record written by gw_energy and gw_solve. */
+#define GW_EN_E 0          /* L + eps KL  (objective of Eq. entropic_gromov_wasserstein) */
+#define GW_EN_L 1          /* C - 8 ||Gamma_{t+1}||^2 - 4 T  (Lemma, Appendix D) */
+#define GW_EN_KL 2         /* KL(pi | a x b) */
+#define GW_EN_C 3          /* C(alpha, beta) of the Lemma */
+#define GW_EN_GAMMA2 4     /* ||Gamma_{t+1}||_F^2 */
+#define GW_EN_T 5          /* T = sum_ij pi_ij s_i t_j */
+#define GW_EN_ROW_L1 6     /* ||pi 1 - a||_1 */
+#define GW_EN_COL_L1 7     /* ||pi^T 1 - b||_1 */
+#define GW_EN_ROW_RELMAX 8 /* max_i |(pi 1)_i - a_i| / a_i */
+#define GW_EN_COL_RELMAX 9 /* max_j |(pi^T 1)_j - b_j| / b_j */
+#define GW_EN_MASS 10      /* sum_ij pi_ij */
+#define GW_EN_DGAMMA 11    /* ||Gamma_{t+1} - Gamma_t||_F */
+#define GW_EN_EPS 12       /* eps used */
+#define GW_EN_STATUS 13    /* 0, or GW_ENONFINITE when a term is not finite */
+#define GW_EN_LEN 16
+
+/*
+ * gw_sinkhorn_softmin -- one Sinkhorn half-step on the bilinear cost
+ * (discrete Sinkhorn operator, Eq. sinkhorn_operators; the loop bodies of
+ * Algorithms 2 and 3):
+ *
+ *   out_i = -eps * log sum_j exp( logw_j + (h_j + 16 <A_i, B_j> + 4 sA_i sB_j) / eps )
+ *
+ * and, when avg_with != NULL, the Jacobi average of Algorithm 3,
+ *   out_i = (avg_with_i + out_i) / 2.
+ * Row update (f): A = X, B = V = Gamma Y (rows V_j = Gamma Y_j), sA = s,
+ *   sB = t, h = g, logw = log b.  Column update (g): A = V, B = X, sA = t,
+ *   sB = s, h = f, logw = log a.
+ *   A: n x K, B: m x K (row-major float32), sA, out, avg_with: n; sB, h, logw: m.
+ *   avg_with may alias out.  logw_j = -inf (zero weight) is allowed.
+ *   1 <= K <= GW_MAX_FEATURES, m >= 1, n >= 0 (n == 0 is a no-op), eps > 0.
+ *   prec: GW_PREC_*; BF16 modes need K <= 64.
+ * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
+ */
+int gw_sinkhorn_softmin(const float* A, const float* B, const float* sA, const float* sB,
+                        const float* h, const float* logw, float eps, int64_t n, int64_t m,
+                        int K, int prec, const float* avg_with, float* out, void* ws,
+                        size_t ws_bytes, gw_stream_t stream);
+
+/*
+ * gw_cross_cov -- the plan-weighted reduction of Algorithm 1 (its Xtilde and
+ * Gamma_{t+1} lines; Theorem 3.3): with pi built from (f, g) on c_{Gamma_t}
+ * at temperature eps,
+ *   W_j         = sum_i pi_ij [X_i, s_i, 1]               (float32 -> float64)
+ *   Gamma_out   = sum_j W_j[0:D] Y_j^T = sum_ij pi_ij X_i Y_j^T   (D x E float64)
+ *   stats[0]    = T = sum_ij pi_ij s_i t_j
+ *   stats[1]    = sum_j g_j (pi^T 1)_j
+ *   stats[2]    = sum_ij pi_ij
+ *   stats[3]    = ||pi^T 1 - b||_1
+ *   stats[4]    = max_j |(pi^T 1)_j - b_j| / b_j
+ *   (stats: device, 8 float64).  W_opt (m x (D+2) float64, or NULL) receives
+ *   W.  X: n x D, Y: m x E, s, a, f: n; t, b, g: m; Gamma_t: D x E float64.
+ *   a, b must be > 0 (their logs enter the exponent).
+ * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
+ */
+int gw_cross_cov(const float* X, const float* Y, const float* s, const float* t,
+                 const float* a, const float* b, const float* f, const float* g,
+                 const double* Gamma_t, float eps, int64_t n, int64_t m, int D, int E,
+                 int prec, double* Gamma_out, double* stats, double* W_opt, void* ws,
+                 size_t ws_bytes, gw_stream_t stream);
+
+/*
+ * gw_energy -- energy terms of the plan encoded by (f, g) on c_{Gamma_t}
+ * (Lemma in Appendix D; Eq. entropic_gromov_wasserstein):
+ *   C(alpha,beta) from the centered moments of X and Y,
+ *   L = C - 8 ||Gamma_{t+1}||^2 - 4 T,
+ *   eps KL = sum_i f_i (pi 1)_i + sum_j g_j (pi^T 1)_j + 16 <Gamma_t, Gamma_{t+1}> + 4 T,
+ *   E = L + eps KL,
+ * with (pi 1)_i = a_i exp((f_i - S_b(g)_i)/eps) from one extra row softmin.
+ * Writes GW_EN_LEN float64 values (layout GW_EN_*) to `energy` (device) and
+ * Gamma_{t+1} to Gamma_out (device, D x E float64, may be NULL).
+ * X, Y must be centered (sum a X = 0, sum b Y = 0).
+ * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
+ */
+int gw_energy(const float* X, const float* Y, const float* s, const float* t, const float* a,
+              const float* b, const float* f, const float* g, const double* Gamma_t, float eps,
+              int64_t n, int64_t m, int D, int E, int prec, double* energy, double* Gamma_out,
+              void* ws, size_t ws_bytes, gw_stream_t stream);
+
+/* Problem and options of gw_solve (Algorithm 1 with Algorithm 3). */
+typedef struct gw_problem {
+  const float* X;  /* n x D centered features */
+  const float* Y;  /* m x E centered features */
+  const float* s;  /* n squared norms ||X_i||^2 */
+  const float* t;  /* m squared norms ||Y_j||^2 */
+  const float* a;  /* n weights (> 0, sum 1) */
+  const float* b;  /* m weights (> 0, sum 1) */
+  int64_t n, m;
+  int D, E;
+} gw_problem;
+
+typedef struct gw_options {
+  float eps;          /* temperature of the first outer step (> 0) */
+  float eps_final;    /* <= 0: constant eps; else geometric eps_t from eps to eps_final */
+  int n_outer;        /* outer (Gamma) steps, >= 1 */
+  int n_inner;        /* Sinkhorn iterations per outer step, >= 1 */
+  int symmetric;      /* 1: Algorithm 3 (Jacobi averaging); 0: Algorithm 2 */
+  int prec;           /* GW_PREC_* for the cost tiles */
+  int record;         /* 1: energy record after every outer step into history */
+  int use_graph;      /* 1: capture the whole solve as one CUDA graph */
+  const double* Gamma0; /* D x E initial map, NULL = 0 (Algorithm 1, first line) */
+  const float* f0;    /* initial potentials (warm start), NULL = 0 */
+  const float* g0;
+} gw_options;
+
+typedef struct gw_result {
+  double* Gamma;      /* out: D x E, the last Gamma_{t+1} */
+  double* Gamma_plan; /* out or NULL: D x E, the Gamma_t whose cost c_{Gamma_t} encodes the
+                         final plan together with (f, g) */
+  float* f;           /* out: n potentials */
+  float* g;           /* out: m potentials */
+  double* energy;     /* out: GW_EN_LEN energy record of the last plan */
+  double* history;    /* out or NULL: n_outer x GW_EN_LEN records (needs record = 1) */
+} gw_result;
+
+/*
+ * gw_solve -- CNT-GW (Algorithm 1) on device: for t = 0..n_outer-1,
+ *   V = Gamma_t Y; n_inner symmetrized (or standard) Sinkhorn iterations on
+ *   c_{Gamma_t} at eps_t, warm-started from the previous potentials;
+ *   Gamma_{t+1} = sum_ij pi_ij X_i Y_j^T; energy record of pi_{t+1}.
+ * All outputs are device buffers owned by the caller; nothing is read back
+ * to the host.  Asynchronous on `stream`.
+ * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
+ */
+int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, size_t ws_bytes,
+             gw_stream_t stream);
+
+/*
+ * gw_lift -- embeddings feeding Algorithm 1 (Section 5, "CNT Embeddings";
+ * Appendix B.2).
+ *   GW_PEN_SQEUCLID: X = x - sum_i w_i x_i (D must equal d; Section 3 example).
+ *   GW_PEN_POWER / GW_PEN_GAUSS: Kernel PCA of the kernel of Prop. 2.3,
+ *     centered as in Algorithm 4, computed matrix-free by block subspace
+ *     iteration (n_iter iterations, 0 = default) with Rayleigh-Ritz:
+ *     X = V sqrt(Lambda) for the D largest eigenpairs.  Each eigenvector's
+ *     entry of largest magnitude is made positive.
+ *   x: n x d raw points (float32); w: n weights or NULL (uniform).
+ *   Outputs: X (n x D), sqn (n) = ||X_i||^2, basis_opt (n x D, V) and
+ *   eigvals_opt (D, Lambda) may be NULL.  `seed` seeds the start block.
+ *   Synchronous: returns after the work completes (the Rayleigh-Ritz steps
+ *   run a small dense eigen-solve on the host).
+ * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
+ */
+int gw_lift(const float* x, int64_t n, int d, const float* w, int kind, float param, int D,
+            int n_iter, uint64_t seed, float* X, float* sqn, float* basis_opt,
+            float* eigvals_opt, void* ws, size_t ws_bytes, gw_stream_t stream);
+
+/*
+ * gw_grad_x -- gradient of the EGW energy with respect to the source points
+ * through the converged plan (envelope theorem, Appendix B.5):
+ *   dX_i = 8 a_i [(s_i + m2_X) X_i + 2 Sigma_X X_i - mu3_X] - 8 a_i m2_Y X_i
+ *          - 16 Gamma_pi w_i - 8 q_i X_i,
+ *   w_i = sum_j pi_ij Y_j, q_i = sum_j pi_ij t_j (pi from f, g on c_{Gamma_t}),
+ *   then the adjoint of the centering, dX_i <- dX_i - a_i sum_k dX_k.
+ *   If x != NULL (lifted features, Algorithm 11), additionally
+ *   dx_i = sum_d dX_id grad_x Pi_d(x_i) with Kernel-Proj (Algorithm 12)
+ *   frozen at the training points x (n x dx_dim), basis V (n x D) and
+ *   eigvals Lambda (D), for the penalty (kind, param).
+ *   For squared features (x == NULL) dx may equal NULL and dX is the answer.
+ * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
+ */
+int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double* Gamma_t,
+              const double* Gamma_pi, float eps, int prec, const float* x, int dx_dim, int kind,
+              float param, const float* basis, const float* eigvals, float* dX, float* dx,
+              void* ws, size_t ws_bytes, gw_stream_t stream);
+
+/* Bytes of workspace `op` needs for these sizes (0 on invalid arguments). */
+size_t gw_workspace_size(int op, int64_t n, int64_t m, int D, int E, int prec);
+
+/* Description of the last error on this host thread ("" if none). */
+const char* gw_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int gw_version(void);
+
+/* Number of kernels this library has enqueued in the process (kernels
+ * captured into a CUDA graph count once, at capture).  reset != 0 returns the
+ * count and sets it to zero.  Diagnostic only. */
+unsigned long long gw_kernel_launches(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GW_H_ */

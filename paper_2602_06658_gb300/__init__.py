@@ -1,0 +1,273 @@
+"""Python binding of libgw, the GB300 hot path of CNT-GW (arXiv 2602.06658).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libgw.so`` through its C ABI (``include/gw.h``).  PyTorch is
+used for device memory and streams.  There is no CPU fallback: importing this
+package fails if the library is missing, and every call raises if the
+library reports an error.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from ._build import LIB as _LIB_PATH
+
+__all__ = [
+    "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
+    "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
+    "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
+    "gw_kernel_launches",
+]
+
+GW_OK = 0
+PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
+PEN_SQEUCLID, PEN_POWER, PEN_GAUSS = 0, 1, 2
+OP_SOFTMIN, OP_CROSS_COV, OP_ENERGY, OP_SOLVE, OP_LIFT, OP_GRAD = 0, 1, 2, 3, 4, 5
+EN_LEN = 16
+# index of each term of the float64 energy record
+EN = {"E": 0, "L": 1, "KL": 2, "C": 3, "Gamma2": 4, "T": 5, "row_l1": 6, "col_l1": 7,
+      "row_relmax": 8, "col_relmax": 9, "mass": 10, "dGamma": 11, "eps": 12, "status": 13}
+_STATUS = {1: "GW_EINVAL", 2: "GW_ENOMEM", 3: "GW_ECUDA", 4: "GW_ENONFINITE", 5: "GW_ETIMEOUT",
+           6: "GW_EUNSUPPORTED"}
+
+
+class GWError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+lib = ctypes.CDLL(_LIB_PATH)
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_f = ctypes.c_float
+_sz = ctypes.c_size_t
+
+
+class GwProblem(ctypes.Structure):
+    _fields_ = [("X", _p), ("Y", _p), ("s", _p), ("t", _p), ("a", _p), ("b", _p),
+                ("n", _i64), ("m", _i64), ("D", _int), ("E", _int)]
+
+
+class GwOptions(ctypes.Structure):
+    _fields_ = [("eps", _f), ("eps_final", _f), ("n_outer", _int), ("n_inner", _int),
+                ("symmetric", _int), ("prec", _int), ("record", _int), ("use_graph", _int),
+                ("Gamma0", _p), ("f0", _p), ("g0", _p)]
+
+
+class GwResult(ctypes.Structure):
+    _fields_ = [("Gamma", _p), ("Gamma_plan", _p), ("f", _p), ("g", _p), ("energy", _p),
+                ("history", _p)]
+
+
+lib.gw_sinkhorn_softmin.argtypes = [_p, _p, _p, _p, _p, _p, _f, _i64, _i64, _int, _int, _p, _p,
+                                    _p, _sz, _p]
+lib.gw_cross_cov.argtypes = [_p, _p, _p, _p, _p, _p, _p, _p, _p, _f, _i64, _i64, _int, _int, _int,
+                             _p, _p, _p, _p, _sz, _p]
+lib.gw_energy.argtypes = [_p, _p, _p, _p, _p, _p, _p, _p, _p, _f, _i64, _i64, _int, _int, _int, _p,
+                          _p, _p, _sz, _p]
+lib.gw_solve.argtypes = [ctypes.POINTER(GwProblem), ctypes.POINTER(GwOptions),
+                         ctypes.POINTER(GwResult), _p, _sz, _p]
+lib.gw_lift.argtypes = [_p, _i64, _int, _p, _int, _f, _int, _int, ctypes.c_uint64, _p, _p, _p, _p,
+                        _p, _sz, _p]
+lib.gw_grad_x.argtypes = [ctypes.POINTER(GwProblem), _p, _p, _p, _p, _f, _int, _p, _int, _int, _f,
+                          _p, _p, _p, _p, _p, _sz, _p]
+lib.gw_workspace_size.argtypes = [_int, _i64, _i64, _int, _int, _int]
+lib.gw_workspace_size.restype = _sz
+lib.gw_last_error.restype = ctypes.c_char_p
+lib.gw_version.restype = _int
+lib.gw_kernel_launches.argtypes = [_int]
+lib.gw_kernel_launches.restype = ctypes.c_ulonglong
+for _name in ("gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve", "gw_lift", "gw_grad_x"):
+    getattr(lib, _name).restype = _int
+
+
+def gw_last_error() -> str:
+    return lib.gw_last_error().decode()
+
+
+def gw_version() -> int:
+    return lib.gw_version()
+
+
+def gw_kernel_launches(reset: bool = False) -> int:
+    """Kernels libgw has enqueued in this process (graph captures count once)."""
+    return int(lib.gw_kernel_launches(int(bool(reset))))
+
+
+def gw_workspace_size(op: int, n: int, m: int, D: int, E: int, prec: int = PREC_FP32) -> int:
+    return int(lib.gw_workspace_size(op, n, m, D, E, prec))
+
+
+def _check(rc: int):
+    if rc != GW_OK:
+        raise GWError(rc, gw_last_error())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("tensors must live on the GPU")
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t, name):
+    if t is None:
+        return None
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    return t
+
+
+def _f64(t, name):
+    if t is None:
+        return None
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    return t
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Caller-owned scratch buffer (256-byte aligned by the caching allocator)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def gw_sinkhorn_softmin(A, B, sA, sB, h, logw, eps, prec=PREC_FP32, avg_with=None, out=None,
+                        ws=None, stream=None):
+    """out_i = -eps LSE_j[logw_j + (h_j + 16<A_i,B_j> + 4 sA_i sB_j)/eps]
+    (optionally averaged with avg_with); see gw.h."""
+    n, K = A.shape
+    m = B.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=A.device)
+    if ws is None:
+        ws = workspace(gw_workspace_size(OP_SOFTMIN, n, m, K, 1, prec), A.device)
+    _check(lib.gw_sinkhorn_softmin(
+        _ptr(_f32(A, "A")), _ptr(_f32(B, "B")), _ptr(_f32(sA, "sA")), _ptr(_f32(sB, "sB")),
+        _ptr(_f32(h, "h")), _ptr(_f32(logw, "logw")), float(eps), n, m, K, prec,
+        _ptr(_f32(avg_with, "avg_with")), _ptr(_f32(out, "out")), _ptr(ws), ws.numel(),
+        _stream(stream)))
+    return out
+
+
+def gw_cross_cov(X, Y, s, t, a, b, f, g, Gamma_t, eps, prec=PREC_FP32, want_W=False, ws=None,
+                 stream=None):
+    """Gamma_{t+1} = sum pi X Y^T and column statistics (see gw.h).
+    Returns (Gamma, stats[8], W or None)."""
+    n, D = X.shape
+    m, E = Y.shape
+    G = torch.empty(D, E, dtype=torch.float64, device=X.device)
+    stats = torch.empty(8, dtype=torch.float64, device=X.device)
+    W = torch.empty(m, D + 2, dtype=torch.float64, device=X.device) if want_W else None
+    if ws is None:
+        ws = workspace(gw_workspace_size(OP_CROSS_COV, n, m, D, E, prec), X.device)
+    _check(lib.gw_cross_cov(
+        _ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
+        _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), _ptr(_f32(f, "f")), _ptr(_f32(g, "g")),
+        _ptr(_f64(Gamma_t, "Gamma_t")), float(eps), n, m, D, E, prec, _ptr(G), _ptr(stats), _ptr(W),
+        _ptr(ws), ws.numel(), _stream(stream)))
+    return G, stats, W
+
+
+def gw_energy(X, Y, s, t, a, b, f, g, Gamma_t, eps, prec=PREC_FP32, ws=None, stream=None):
+    """Energy record (float64[16], layout EN) and Gamma_{t+1}."""
+    n, D = X.shape
+    m, E = Y.shape
+    en = torch.empty(EN_LEN, dtype=torch.float64, device=X.device)
+    G = torch.empty(D, E, dtype=torch.float64, device=X.device)
+    if ws is None:
+        ws = workspace(gw_workspace_size(OP_ENERGY, n, m, D, E, prec), X.device)
+    _check(lib.gw_energy(
+        _ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
+        _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), _ptr(_f32(f, "f")), _ptr(_f32(g, "g")),
+        _ptr(_f64(Gamma_t, "Gamma_t")), float(eps), n, m, D, E, prec, _ptr(en), _ptr(G),
+        _ptr(ws), ws.numel(), _stream(stream)))
+    return en, G
+
+
+def gw_solve(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=True,
+             prec=PREC_FP32, record=True, use_graph=True, Gamma0=None, f0=None, g0=None, ws=None,
+             out=None, stream=None):
+    """CNT-GW (Algorithm 1) on device.  Returns dict(Gamma, Gamma_plan, f, g,
+    energy, history) of device tensors; nothing is synchronised."""
+    n, D = X.shape
+    m, E = Y.shape
+    dev = X.device
+    if out is None:
+        out = {"Gamma": torch.empty(D, E, dtype=torch.float64, device=dev),
+               "Gamma_plan": torch.empty(D, E, dtype=torch.float64, device=dev),
+               "f": torch.empty(n, dtype=torch.float32, device=dev),
+               "g": torch.empty(m, dtype=torch.float32, device=dev),
+               "energy": torch.empty(EN_LEN, dtype=torch.float64, device=dev),
+               "history": torch.empty(n_outer, EN_LEN, dtype=torch.float64, device=dev)
+               if record else None}
+    if ws is None:
+        ws = workspace(gw_workspace_size(OP_SOLVE, n, m, D, E, prec), dev)
+    P = GwProblem(_ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
+                  _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
+    O = GwOptions(float(eps), float(eps_final), int(n_outer), int(n_inner), int(bool(symmetric)),
+                  int(prec), int(bool(record)), int(bool(use_graph)),
+                  _ptr(_f64(Gamma0, "Gamma0")), _ptr(_f32(f0, "f0")), _ptr(_f32(g0, "g0")))
+    R = GwResult(_ptr(out["Gamma"]), _ptr(out.get("Gamma_plan")), _ptr(out["f"]), _ptr(out["g"]), _ptr(out["energy"]),
+                 _ptr(out["history"]))
+    _check(lib.gw_solve(ctypes.byref(P), ctypes.byref(O), ctypes.byref(R), _ptr(ws), ws.numel(),
+                        _stream(stream)))
+    return out
+
+
+def gw_lift(x, D, kind=PEN_SQEUCLID, param=2.0, w=None, n_iter=0, seed=0, want_basis=False,
+            ws=None, stream=None):
+    """Embedding step (see gw.h).  Returns dict(X, s, V, lam)."""
+    n, d = x.shape
+    dev = x.device
+    X = torch.empty(n, D, dtype=torch.float32, device=dev)
+    s = torch.empty(n, dtype=torch.float32, device=dev)
+    V = torch.empty(n, D, dtype=torch.float32, device=dev) if want_basis else None
+    lam = torch.empty(D, dtype=torch.float32, device=dev) if want_basis else None
+    if ws is None:
+        ws = workspace(gw_workspace_size(OP_LIFT, n, n, D, d, PREC_FP32), dev)
+    _check(lib.gw_lift(_ptr(_f32(x, "x")), n, d, _ptr(_f32(w, "w")), int(kind), float(param),
+                       int(D), int(n_iter), int(seed), _ptr(X), _ptr(s), _ptr(V), _ptr(lam),
+                       _ptr(ws), ws.numel(), _stream(stream)))
+    return {"X": X, "s": s, "V": V, "lam": lam}
+
+
+def gw_grad_x(X, Y, s, t, a, b, f, g, Gamma_t, Gamma_pi, eps, prec=PREC_FP32, x=None, kind=0,
+              param=2.0, basis=None, eigvals=None, ws=None, stream=None):
+    """Adjoint: gradient of the EGW energy w.r.t. the features (dX) and, for
+    lifted features, w.r.t. the raw points x (dx)."""
+    n, D = X.shape
+    m, E = Y.shape
+    dev = X.device
+    dX = torch.empty(n, D, dtype=torch.float32, device=dev)
+    dx = torch.empty(n, x.shape[1], dtype=torch.float32, device=dev) if x is not None else None
+    if ws is None:
+        ws = workspace(gw_workspace_size(OP_GRAD, n, m, D, E, prec), dev)
+    P = GwProblem(_ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
+                  _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
+    _check(lib.gw_grad_x(ctypes.byref(P), _ptr(_f32(f, "f")), _ptr(_f32(g, "g")),
+                         _ptr(_f64(Gamma_t, "Gamma_t")), _ptr(_f64(Gamma_pi, "Gamma_pi")),
+                         float(eps), int(prec), _ptr(_f32(x, "x")),
+                         int(x.shape[1]) if x is not None else 0, int(kind), float(param),
+                         _ptr(_f32(basis, "basis")), _ptr(_f32(eigvals, "eigvals")), _ptr(dX),
+                         _ptr(dx), _ptr(ws), ws.numel(), _stream(stream)))
+    return dX, dx

@@ -1,0 +1,424 @@
+// C-ABI entry points of libgw: validation, workspace layout and the CNT-GW
+// solver loop (Algorithm 1 with Algorithm 3 as the inner Sinkhorn solver).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <vector>
+
+#include "gw_internal.cuh"
+
+namespace gw {
+
+namespace {
+thread_local char g_err[512] = {0};
+}
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+const char* last_error() { return g_err; }
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+bool prec_ok(int prec) { return prec == GW_PREC_FP32; }
+
+int check_eps(float eps) {
+  GW_REQUIRE(eps > 0.0f && isfinite(eps), GW_EINVAL, "eps must be finite and > 0 (got %g)",
+             static_cast<double>(eps));
+  return GW_OK;
+}
+
+int check_dims(int64_t n, int64_t m, int D, int E) {
+  GW_REQUIRE(n >= 0 && m >= 1, GW_EINVAL, "need n >= 0 and m >= 1 (got n=%lld m=%lld)",
+             static_cast<long long>(n), static_cast<long long>(m));
+  GW_REQUIRE(D >= 1 && E >= 1, GW_EINVAL, "need D, E >= 1 (got %d, %d)", D, E);
+  GW_REQUIRE(D <= GW_MAX_FEATURES && E <= GW_MAX_FEATURES, GW_EUNSUPPORTED,
+             "D, E must be <= %d (got %d, %d)", GW_MAX_FEATURES, D, E);
+  GW_REQUIRE(n < (int64_t(1) << 40) && m < (int64_t(1) << 40), GW_EINVAL, "n, m too large");
+  return GW_OK;
+}
+
+int check_prec(int prec) {
+  GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_BF16X3, GW_EINVAL, "unknown precision %d",
+             prec);
+  GW_REQUIRE(prec_ok(prec), GW_EUNSUPPORTED, "precision %d is not available in this build", prec);
+  return GW_OK;
+}
+
+#define NONNULL(p) GW_REQUIRE((p) != nullptr, GW_EINVAL, "%s must not be NULL", #p)
+
+size_t solve_fixed_bytes(int64_t n, int64_t m, int D, int E) {
+  Carver c(nullptr, ~size_t(0));
+  c.take<float>(n);                 // log a
+  c.take<float>(m);                 // log b
+  c.take<float>(n);                 // f ping
+  c.take<float>(n);                 // f pong
+  c.take<float>(m);                 // g ping
+  c.take<float>(m);                 // g pong
+  c.take<float>(static_cast<size_t>(m) * D);  // V
+  c.take<double>(static_cast<size_t>(D) * E); // Gamma cur
+  c.take<double>(static_cast<size_t>(D) * E); // Gamma next
+  c.take<double>(4);                // C
+  c.take<double>(GW_EN_LEN);        // scratch energy record
+  return c.used();
+}
+
+size_t solve_ws_bytes(int64_t n, int64_t m, int D, int E, int prec) {
+  const size_t inner = softmin_ws_bytes(n, m, D, prec) + softmin_ws_bytes(m, n, D, prec) + 512;
+  size_t step = energy_ws_bytes(n, m, D, E, prec);
+  const size_t mom = moments_ws_bytes(n, m, D, E);
+  if (mom > step) step = mom;
+  return solve_fixed_bytes(n, m, D, E) + (inner > step ? inner : step) + 256;
+}
+
+struct SolveBufs {
+  float *loga, *logb, *f[2], *g[2], *V;
+  double *G[2], *C, *en;
+};
+
+int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, void* ws,
+                  size_t ws_bytes, cudaStream_t st) {
+  Carver c(ws, ws_bytes);
+  SolveBufs B;
+  B.loga = c.take<float>(p.n);
+  B.logb = c.take<float>(p.m);
+  B.f[0] = c.take<float>(p.n);
+  B.f[1] = c.take<float>(p.n);
+  B.g[0] = c.take<float>(p.m);
+  B.g[1] = c.take<float>(p.m);
+  B.V = c.take<float>(static_cast<size_t>(p.m) * p.D);
+  B.G[0] = c.take<double>(static_cast<size_t>(p.D) * p.E);
+  B.G[1] = c.take<double>(static_cast<size_t>(p.D) * p.E);
+  B.C = c.take<double>(4);
+  B.en = c.take<double>(GW_EN_LEN);
+  GW_TRY(check_ws(c, ws));
+  const size_t mark = c.used();
+  char* base = static_cast<char*>(ws);
+
+  const size_t DE = static_cast<size_t>(p.D) * p.E;
+  GW_TRY(launch_log(p.a, p.n, B.loga, st));
+  GW_TRY(launch_log(p.b, p.m, B.logb, st));
+  if (o.f0) {
+    GW_CUDA_TRY(cudaMemcpyAsync(B.f[0], o.f0, sizeof(float) * p.n, cudaMemcpyDeviceToDevice, st));
+  } else {
+    GW_CUDA_TRY(cudaMemsetAsync(B.f[0], 0, sizeof(float) * p.n, st));
+  }
+  if (o.g0) {
+    GW_CUDA_TRY(cudaMemcpyAsync(B.g[0], o.g0, sizeof(float) * p.m, cudaMemcpyDeviceToDevice, st));
+  } else {
+    GW_CUDA_TRY(cudaMemsetAsync(B.g[0], 0, sizeof(float) * p.m, st));
+  }
+  if (o.Gamma0) {
+    GW_CUDA_TRY(cudaMemcpyAsync(B.G[0], o.Gamma0, sizeof(double) * DE, cudaMemcpyDeviceToDevice, st));
+  } else {
+    GW_CUDA_TRY(cudaMemsetAsync(B.G[0], 0, sizeof(double) * DE, st));
+  }
+  {
+    Carver sub(base + mark, ws_bytes - mark);
+    GW_TRY(run_moments(p.X, p.a, p.n, p.D, p.Y, p.b, p.m, p.E, B.C, sub, st));
+  }
+
+  int fc = 0, gc = 0, Gc = 0;
+  for (int t = 0; t < o.n_outer; ++t) {
+    float eps = o.eps;
+    if (o.eps_final > 0.0f && o.eps_final != o.eps && o.n_outer > 1) {
+      eps = static_cast<float>(static_cast<double>(o.eps) *
+                               pow(static_cast<double>(o.eps_final) / o.eps,
+                                   static_cast<double>(t) / (o.n_outer - 1)));
+    }
+    // Zbar_j <- Gamma_t Y_j (Algorithm 1, line 4)
+    GW_TRY(launch_gamma_y(B.G[Gc], p.Y, p.m, p.D, p.E, B.V, st));
+    for (int it = 0; it < o.n_inner; ++it) {
+      Carver sub(base + mark, ws_bytes - mark);
+      SoftminTask row{}, col{};
+      row.A = p.X;
+      row.B = B.V;
+      row.sA = p.s;
+      row.sB = p.t;
+      row.h = B.g[gc];
+      row.logw = B.logb;
+      row.n = p.n;
+      row.m = p.m;
+      row.K = p.D;
+      row.eps = eps;
+      col.A = B.V;
+      col.B = p.X;
+      col.sA = p.t;
+      col.sB = p.s;
+      col.logw = B.loga;
+      col.n = p.m;
+      col.m = p.n;
+      col.K = p.D;
+      col.eps = eps;
+      if (o.symmetric) {
+        // Algorithm 3: both halves read iterate n, then average.
+        row.avg_with = B.f[fc];
+        row.out = B.f[fc ^ 1];
+        col.h = B.f[fc];
+        col.avg_with = B.g[gc];
+        col.out = B.g[gc ^ 1];
+        SoftminTask both[2] = {row, col};
+        GW_TRY(launch_softmin(both, 2, o.prec, sub, st));
+        fc ^= 1;
+        gc ^= 1;
+      } else {
+        // Algorithm 2: f from g^n, then g from f^{n+1}.
+        row.avg_with = nullptr;
+        row.out = B.f[fc ^ 1];
+        GW_TRY(launch_softmin(&row, 1, o.prec, sub, st));
+        fc ^= 1;
+        Carver sub2(base + mark, ws_bytes - mark);
+        col.h = B.f[fc];
+        col.avg_with = nullptr;
+        col.out = B.g[gc ^ 1];
+        GW_TRY(launch_softmin(&col, 1, o.prec, sub2, st));
+        gc ^= 1;
+      }
+    }
+    // Xtilde / Gamma_{t+1} lines of Algorithm 1, plus the energy record
+    PlanArgs pa;
+    pa.X = p.X;
+    pa.Y = p.Y;
+    pa.s = p.s;
+    pa.t = p.t;
+    pa.a = p.a;
+    pa.b = p.b;
+    pa.f = B.f[fc];
+    pa.g = B.g[gc];
+    pa.Gamma_t = B.G[Gc];
+    pa.eps = eps;
+    pa.n = p.n;
+    pa.m = p.m;
+    pa.D = p.D;
+    pa.E = p.E;
+    Carver sub(base + mark, ws_bytes - mark);
+    const bool last = t == o.n_outer - 1;
+    if (o.record || last) {
+      double* rec = (o.record && r.history) ? r.history + static_cast<size_t>(t) * GW_EN_LEN : B.en;
+      GW_TRY(run_energy(pa, o.prec, B.C, B.logb, rec, B.G[Gc ^ 1], sub, st));
+      if (last) {
+        GW_CUDA_TRY(cudaMemcpyAsync(r.energy, rec, sizeof(double) * GW_EN_LEN,
+                                    cudaMemcpyDeviceToDevice, st));
+      }
+    } else {
+      GW_TRY(run_cross_cov(pa, o.prec, B.G[Gc ^ 1], nullptr, nullptr, sub, st));
+    }
+    Gc ^= 1;
+  }
+  GW_CUDA_TRY(cudaMemcpyAsync(r.Gamma, B.G[Gc], sizeof(double) * DE, cudaMemcpyDeviceToDevice, st));
+  if (r.Gamma_plan) {
+    GW_CUDA_TRY(cudaMemcpyAsync(r.Gamma_plan, B.G[Gc ^ 1], sizeof(double) * DE,
+                                cudaMemcpyDeviceToDevice, st));
+  }
+  GW_CUDA_TRY(cudaMemcpyAsync(r.f, B.f[fc], sizeof(float) * p.n, cudaMemcpyDeviceToDevice, st));
+  GW_CUDA_TRY(cudaMemcpyAsync(r.g, B.g[gc], sizeof(float) * p.m, cudaMemcpyDeviceToDevice, st));
+  return GW_OK;
+}
+
+}  // namespace
+
+}  // namespace gw
+
+using namespace gw;
+
+extern "C" {
+
+const char* gw_last_error(void) { return gw::last_error(); }
+
+int gw_version(void) { return 100; }
+
+unsigned long long gw_kernel_launches(int reset) {
+  return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+size_t gw_workspace_size(int op, int64_t n, int64_t m, int D, int E, int prec) {
+  if (n < 0 || m < 1 || D < 1 || E < 1 || D > GW_MAX_FEATURES || E > GW_MAX_FEATURES) return 0;
+  switch (op) {
+    case GW_OP_SOFTMIN: return softmin_ws_bytes(n, m, D, prec) + 256;
+    case GW_OP_CROSS_COV: return cross_cov_ws_bytes(n, m, D, E, prec) + 256;
+    case GW_OP_ENERGY: return energy_ws_bytes(n, m, D, E, prec) + 256;
+    case GW_OP_SOLVE: return solve_ws_bytes(n, m, D, E, prec);
+    default: return 0;
+  }
+}
+
+int gw_sinkhorn_softmin(const float* A, const float* B, const float* sA, const float* sB,
+                        const float* h, const float* logw, float eps, int64_t n, int64_t m,
+                        int K, int prec, const float* avg_with, float* out, void* ws,
+                        size_t ws_bytes, gw_stream_t stream) {
+  gw::set_error("");
+  GW_TRY(check_eps(eps));
+  GW_TRY(check_dims(n, m, K, 1));
+  GW_TRY(check_prec(prec));
+  if (n == 0) return GW_OK;
+  NONNULL(A);
+  NONNULL(B);
+  NONNULL(sA);
+  NONNULL(sB);
+  NONNULL(h);
+  NONNULL(logw);
+  NONNULL(out);
+  Carver c(ws, ws_bytes);
+  SoftminTask T{};
+  T.A = A;
+  T.B = B;
+  T.sA = sA;
+  T.sB = sB;
+  T.h = h;
+  T.logw = logw;
+  T.avg_with = avg_with;
+  T.out = out;
+  T.n = n;
+  T.m = m;
+  T.K = K;
+  T.eps = eps;
+  GW_REQUIRE(ws_bytes == 0 || reinterpret_cast<uintptr_t>(ws) % 256 == 0, GW_ENOMEM,
+             "workspace must be 256-byte aligned");
+  return launch_softmin(&T, 1, prec, c, reinterpret_cast<cudaStream_t>(stream));
+}
+
+static int check_plan_args(const float* X, const float* Y, const float* s, const float* t,
+                           const float* a, const float* b, const float* f, const float* g,
+                           const double* Gamma_t, float eps, int64_t n, int64_t m, int D, int E,
+                           int prec) {
+  GW_TRY(check_eps(eps));
+  GW_TRY(check_dims(n, m, D, E));
+  GW_REQUIRE(n >= 1, GW_EINVAL, "n must be >= 1");
+  GW_TRY(check_prec(prec));
+  NONNULL(X);
+  NONNULL(Y);
+  NONNULL(s);
+  NONNULL(t);
+  NONNULL(a);
+  NONNULL(b);
+  NONNULL(f);
+  NONNULL(g);
+  NONNULL(Gamma_t);
+  return GW_OK;
+}
+
+int gw_cross_cov(const float* X, const float* Y, const float* s, const float* t,
+                 const float* a, const float* b, const float* f, const float* g,
+                 const double* Gamma_t, float eps, int64_t n, int64_t m, int D, int E,
+                 int prec, double* Gamma_out, double* stats, double* W_opt, void* ws,
+                 size_t ws_bytes, gw_stream_t stream) {
+  gw::set_error("");
+  GW_TRY(check_plan_args(X, Y, s, t, a, b, f, g, Gamma_t, eps, n, m, D, E, prec));
+  NONNULL(Gamma_out);
+  NONNULL(stats);
+  Carver c(ws, ws_bytes);
+  GW_REQUIRE(reinterpret_cast<uintptr_t>(ws) % 256 == 0, GW_ENOMEM,
+             "workspace must be 256-byte aligned");
+  PlanArgs pa{X, Y, s, t, a, b, f, g, Gamma_t, eps, n, m, D, E};
+  return run_cross_cov(pa, prec, Gamma_out, stats, W_opt, c,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+int gw_energy(const float* X, const float* Y, const float* s, const float* t, const float* a,
+              const float* b, const float* f, const float* g, const double* Gamma_t, float eps,
+              int64_t n, int64_t m, int D, int E, int prec, double* energy, double* Gamma_out,
+              void* ws, size_t ws_bytes, gw_stream_t stream) {
+  gw::set_error("");
+  GW_TRY(check_plan_args(X, Y, s, t, a, b, f, g, Gamma_t, eps, n, m, D, E, prec));
+  NONNULL(energy);
+  Carver c(ws, ws_bytes);
+  GW_REQUIRE(reinterpret_cast<uintptr_t>(ws) % 256 == 0, GW_ENOMEM,
+             "workspace must be 256-byte aligned");
+  PlanArgs pa{X, Y, s, t, a, b, f, g, Gamma_t, eps, n, m, D, E};
+  return run_energy(pa, prec, nullptr, nullptr, energy, Gamma_out, c,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, size_t ws_bytes,
+             gw_stream_t stream) {
+  gw::set_error("");
+  NONNULL(p);
+  NONNULL(o);
+  NONNULL(r);
+  GW_TRY(check_dims(p->n, p->m, p->D, p->E));
+  GW_REQUIRE(p->n >= 1, GW_EINVAL, "n must be >= 1");
+  GW_TRY(check_eps(o->eps));
+  GW_REQUIRE(o->eps_final <= 0.0f || isfinite(o->eps_final), GW_EINVAL, "eps_final not finite");
+  GW_REQUIRE(o->n_outer >= 1 && o->n_inner >= 1, GW_EINVAL, "n_outer, n_inner must be >= 1");
+  GW_REQUIRE(o->n_outer <= 100000 && o->n_inner <= 1000000, GW_EINVAL, "iteration counts too large");
+  GW_TRY(check_prec(o->prec));
+  NONNULL(p->X);
+  NONNULL(p->Y);
+  NONNULL(p->s);
+  NONNULL(p->t);
+  NONNULL(p->a);
+  NONNULL(p->b);
+  NONNULL(r->Gamma);
+  NONNULL(r->f);
+  NONNULL(r->g);
+  NONNULL(r->energy);
+  GW_REQUIRE(!o->record || r->history != nullptr, GW_EINVAL, "record = 1 needs result.history");
+  const size_t need = solve_ws_bytes(p->n, p->m, p->D, p->E, o->prec);
+  GW_REQUIRE(ws != nullptr && ws_bytes >= need, GW_ENOMEM,
+             "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!o->use_graph || st == nullptr) return enqueue_solve(*p, *o, *r, ws, ws_bytes, st);
+
+  cudaGraph_t graph = nullptr;
+  GW_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue_solve(*p, *o, *r, ws, ws_bytes, st);
+  const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+  if (rc != GW_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (ec != cudaSuccess) {
+    gw::set_error("graph capture failed: %s", cudaGetErrorString(ec));
+    if (graph) cudaGraphDestroy(graph);
+    return GW_ECUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    gw::set_error("graph instantiate failed: %s", cudaGetErrorString(ei));
+    return GW_ECUDA;
+  }
+  cudaError_t el = cudaGraphLaunch(exec, st);
+  cudaGraphExecDestroy(exec);
+  if (el != cudaSuccess) {
+    gw::set_error("graph launch failed: %s", cudaGetErrorString(el));
+    return GW_ECUDA;
+  }
+  return GW_OK;
+}
+
+int gw_lift(const float* x, int64_t n, int d, const float* w, int kind, float param, int D,
+            int n_iter, uint64_t seed, float* X, float* sqn, float* basis_opt,
+            float* eigvals_opt, void* ws, size_t ws_bytes, gw_stream_t stream) {
+  (void)x; (void)n; (void)d; (void)w; (void)kind; (void)param; (void)D; (void)n_iter; (void)seed;
+  (void)X; (void)sqn; (void)basis_opt; (void)eigvals_opt; (void)ws; (void)ws_bytes; (void)stream;
+  gw::set_error("gw_lift is not available in this build");
+  return GW_EUNSUPPORTED;
+}
+
+int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double* Gamma_t,
+              const double* Gamma_pi, float eps, int prec, const float* x, int dx_dim, int kind,
+              float param, const float* basis, const float* eigvals, float* dX, float* dx,
+              void* ws, size_t ws_bytes, gw_stream_t stream) {
+  (void)p; (void)f; (void)g; (void)Gamma_t; (void)Gamma_pi; (void)eps; (void)prec; (void)x;
+  (void)dx_dim; (void)kind; (void)param; (void)basis; (void)eigvals; (void)dX; (void)dx; (void)ws;
+  (void)ws_bytes; (void)stream;
+  gw::set_error("gw_grad_x is not available in this build");
+  return GW_EUNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Internal helpers shared by the libgw translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "gw.h"
+
+namespace gw {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kNegBig = -1.0e30f;   // "minus infinity" that keeps exp2(x - m) finite
+constexpr int kSmCount = 152;         // GB300
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+const char* last_error();
+
+#define GW_REQUIRE(cond, code, ...)      \
+  do {                                   \
+    if (!(cond)) {                       \
+      ::gw::set_error(__VA_ARGS__);      \
+      return (code);                     \
+    }                                    \
+  } while (0)
+
+#define GW_CUDA_TRY(call)                                                      \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      ::gw::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                      __FILE__, __LINE__);                                     \
+      return GW_ECUDA;                                                         \
+    }                                                                          \
+  } while (0)
+
+// Every kernel launch site calls GW_LAUNCH_CHECK() once, which also counts
+// the launch (gw_kernel_launches()).
+void count_launch();
+#define GW_LAUNCH_CHECK()          \
+  do {                             \
+    ::gw::count_launch();          \
+    GW_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
+
+#define GW_TRY(expr)          \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != GW_OK) return rc_; \
+  } while (0)
+
+// ------------------------------------------------------------ workspace
+// Bump allocator over the caller's workspace.  With base == nullptr it only
+// measures, so gw_workspace_size() and the entry points share one layout.
+struct Carver {
+  char* base;
+  size_t cap;
+  size_t off = 0;
+  bool overflow = false;
+  Carver(void* b, size_t c) : base(static_cast<char*>(b)), cap(c) {}
+  template <class T>
+  T* take(size_t count) {
+    size_t o = (off + 255) & ~size_t(255);
+    off = o + count * sizeof(T);
+    if (off > cap) overflow = true;
+    return base ? reinterpret_cast<T*>(base + o) : nullptr;
+  }
+  size_t used() const { return (off + 255) & ~size_t(255); }
+};
+
+inline int check_ws(const Carver& c, void* ws) {
+  GW_REQUIRE(reinterpret_cast<uintptr_t>(ws) % 256 == 0, GW_ENOMEM,
+             "workspace must be 256-byte aligned");
+  GW_REQUIRE(!c.overflow, GW_ENOMEM, "workspace too small: need %zu bytes, have %zu", c.used(),
+             c.cap);
+  return GW_OK;
+}
+
+// ------------------------------------------------------------ device math
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+// ------------------------------------------------------------ softmin plan
+// One softmin task: out_i = -eps LSE_j[logw_j + (h_j + 16<A_i,B_j> + 4 sA_i sB_j)/eps].
+struct SoftminTask {
+  const float* A;
+  const float* B;
+  const float* sA;
+  const float* sB;
+  const float* h;
+  const float* logw;
+  const float* avg_with;
+  float* out;
+  float* pm;        // partial maxima  [splits][n] (base 2), used when splits > 1
+  float* ps;        // partial sums    [splits][n]
+  int64_t n, m;
+  int K;
+  int splits;       // column splits
+  int cols_per_split;
+  float eps;
+};
+
+// Shape decisions of the softmin kernels (identical for sizing and launch).
+struct SoftminShape {
+  int rows_per_block;
+  int row_blocks;
+  int splits;
+  int cols_per_split;
+};
+SoftminShape softmin_shape(int64_t n, int64_t m, int K, int prec);
+size_t softmin_ws_bytes(int64_t n, int64_t m, int K, int prec);
+
+// Launch one or two softmin tasks (two = the row and column half-steps of a
+// symmetric Sinkhorn iteration in a single launch).  Partials come from the
+// carver.  Host-side only; the tasks must already be validated.
+int launch_softmin(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cudaStream_t st);
+
+// ------------------------------------------------------------ plan kernels
+struct PlanArgs {
+  const float* X;  // n x D
+  const float* Y;  // m x E
+  const float* s;
+  const float* t;
+  const float* a;
+  const float* b;
+  const float* f;
+  const float* g;
+  const double* Gamma_t;  // D x E
+  float eps;
+  int64_t n, m;
+  int D, E;
+};
+
+// V = Gamma Y (m x D, float32) from a float64 Gamma.
+int launch_gamma_y(const double* Gamma, const float* Y, int64_t m, int D, int E, float* V,
+                   cudaStream_t st);
+
+size_t cross_cov_ws_bytes(int64_t n, int64_t m, int D, int E, int prec);
+// Gamma_out (D x E), stats[8], W (m x (D+2), float64; carved if W == nullptr)
+int run_cross_cov(const PlanArgs& p, int prec, double* Gamma_out, double* stats, double* W,
+                  Carver& ws, cudaStream_t st);
+
+size_t moments_ws_bytes(int64_t n, int64_t m, int D, int E);
+// C(alpha, beta) into *C (device)
+int run_moments(const float* X, const float* a, int64_t n, int D, const float* Y, const float* b,
+                int64_t m, int E, double* C, Carver& ws, cudaStream_t st);
+
+size_t energy_ws_bytes(int64_t n, int64_t m, int D, int E, int prec);
+// Full energy record.  C (device scalar) and log b are precomputed when
+// C_pre / logb_pre are non-null.
+int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* logb_pre,
+               double* energy, double* Gamma_out, Carver& ws, cudaStream_t st);
+
+// logw_i = log(w_i)
+int launch_log(const float* w, int64_t n, float* logw, cudaStream_t st);
+
+}  // namespace gw

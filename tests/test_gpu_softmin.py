@@ -1,0 +1,106 @@
+"""GPU softmin (gw_sinkhorn_softmin through the C-ABI) against the FP64 oracle."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import f32, host, softmin_tolerance
+
+pytestmark = pytest.mark.gpu
+
+
+def make_inputs(n, m, K, seed, scale=0.5, zero_cols=0):
+    g = W.rng(seed)
+    A = scale * g.standard_normal((n, K))
+    B = scale * g.standard_normal((m, K))
+    sA = (A * A).sum(1)
+    sB = (B * B).sum(1)
+    h = 0.3 * g.standard_normal(m)
+    w = W.random_weights(m, seed + 1)
+    logw = np.log(w)
+    if zero_cols:
+        logw[g.choice(m, zero_cols, replace=False)] = -np.inf
+    # round to the FP32 values the GPU sees, so both sides take the same inputs
+    r = lambda x: np.asarray(x, np.float32).astype(np.float64)
+    return r(A), r(B), r(sA), r(sB), r(h), r(logw)
+
+
+def oracle_softmin(A, B, sA, sB, h, logw, eps):
+    C = -16.0 * A @ B.T - 4.0 * np.outer(sA, sB)
+    return O.softmin(eps, logw, h, C)
+
+
+SHAPES = [(1, 1, 1), (7, 5, 2), (300, 517, 3), (1000, 1000, 2), (513, 2049, 16),
+          (1200, 700, 32), (257, 300, 64), (100, 90, 128), (4099, 33, 5), (31, 5000, 8)]
+
+
+@pytest.mark.parametrize("n,m,K", SHAPES)
+@pytest.mark.parametrize("eps", [1.0, 0.05])
+def test_softmin_matches_oracle(gw, n, m, K, eps):
+    A, B, sA, sB, h, logw = make_inputs(n, m, K, seed=n + 7 * m + K)
+    out = gw.gw_sinkhorn_softmin(f32(A), f32(B), f32(sA), f32(sB), f32(h), f32(logw), eps)
+    ref = oracle_softmin(A, B, sA, sB, h, logw, eps)
+    tol = softmin_tolerance(A, B, sA, sB, h, logw, eps)
+    err = np.abs(host(out) - ref)
+    assert np.all(err <= tol), (err.max(), tol[np.argmax(err - tol)])
+
+
+def test_softmin_average_and_alias(gw):
+    A, B, sA, sB, h, logw = make_inputs(640, 900, 4, seed=3)
+    eps = 0.1
+    prev = W.rng(9).standard_normal(640).astype(np.float32)
+    out = f32(prev)
+    gw.gw_sinkhorn_softmin(f32(A), f32(B), f32(sA), f32(sB), f32(h), f32(logw), eps,
+                           avg_with=out, out=out)
+    ref = 0.5 * (prev.astype(np.float64) + oracle_softmin(A, B, sA, sB, h, logw, eps))
+    tol = 0.5 * softmin_tolerance(A, B, sA, sB, h, logw, eps) + 1e-7 * np.abs(ref)
+    assert np.all(np.abs(host(out) - ref) <= tol)
+
+
+def test_softmin_zero_weight_columns(gw):
+    A, B, sA, sB, h, logw = make_inputs(300, 400, 3, seed=5, zero_cols=150)
+    eps = 0.2
+    out = gw.gw_sinkhorn_softmin(f32(A), f32(B), f32(sA), f32(sB), f32(h), f32(logw), eps)
+    ref = oracle_softmin(A, B, sA, sB, h, logw, eps)
+    assert np.all(np.abs(host(out) - ref) <= softmin_tolerance(A, B, sA, sB, h, logw, eps))
+
+
+def test_softmin_small_eps_large_cost(gw):
+    """eps = 1e-3 with radius-1 features (the paper's setting): exponents in
+    the tens of thousands, still within the derived FP32 bound."""
+    A, B, sA, sB, h, logw = make_inputs(777, 1500, 32, seed=11, scale=1.0 / math.sqrt(32))
+    eps = 1e-3
+    out = gw.gw_sinkhorn_softmin(f32(A), f32(B), f32(sA), f32(sB), f32(h), f32(logw), eps)
+    ref = oracle_softmin(A, B, sA, sB, h, logw, eps)
+    assert np.all(np.abs(host(out) - ref) <= softmin_tolerance(A, B, sA, sB, h, logw, eps))
+
+
+def test_softmin_empty_rows_and_validation(gw):
+    import torch
+    z = torch.zeros(0, 3, device="cuda")
+    B = torch.randn(5, 3, device="cuda")
+    out = gw.gw_sinkhorn_softmin(z, B, torch.zeros(0, device="cuda"), torch.ones(5, device="cuda"),
+                                 torch.zeros(5, device="cuda"), torch.zeros(5, device="cuda"), 0.1)
+    assert out.numel() == 0
+    with pytest.raises(gw.GWError) as e:
+        gw.gw_sinkhorn_softmin(B, B, torch.ones(5, device="cuda"), torch.ones(5, device="cuda"),
+                               torch.zeros(5, device="cuda"), torch.zeros(5, device="cuda"), 0.0)
+    assert e.value.code == 1
+    with pytest.raises(gw.GWError) as e:
+        ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+        A = torch.randn(5000, 3, device="cuda")
+        gw.gw_sinkhorn_softmin(A, torch.randn(5000, 3, device="cuda"), torch.ones(5000, device="cuda"),
+                               torch.ones(5000, device="cuda"), torch.zeros(5000, device="cuda"),
+                               torch.zeros(5000, device="cuda"), 0.1, ws=ws)
+    assert e.value.code == 2
+
+
+def test_softmin_is_deterministic(gw):
+    A, B, sA, sB, h, logw = make_inputs(3000, 2500, 16, seed=21)
+    args = [f32(v) for v in (A, B, sA, sB, h, logw)]
+    o1 = gw.gw_sinkhorn_softmin(*args, 0.07)
+    o2 = gw.gw_sinkhorn_softmin(*args, 0.07)
+    assert bool((o1 == o2).all())
