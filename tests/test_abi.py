@@ -22,17 +22,24 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def builder():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "gw_build", os.path.join(ROOT, "paper_2602_06658_gb300", "_build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
 def test_library_exports_every_declared_symbol():
-    from paper_2602_06658_gb300 import _build
-    path = _build.build()
+    path = builder().build()
     lib = ctypes.CDLL(path)
     for name in declared_functions():
         assert hasattr(lib, name), name
 
 
 def test_host_side_queries_without_gpu():
-    from paper_2602_06658_gb300 import _build
-    lib = ctypes.CDLL(_build.build())
+    lib = ctypes.CDLL(builder().build())
     lib.gw_workspace_size.restype = ctypes.c_size_t
     lib.gw_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int]
