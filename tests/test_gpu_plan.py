@@ -83,9 +83,12 @@ def test_energy_matches_oracle(gw, n, m, D, E, eps):
     pi = dense_plan(P)
     X, Y, a, b = P["X"], P["Y"], P["a"], P["b"]
     ref = O.egw_energy(pi, X, Y, a, b, eps)
-    # the GPU's energy takes the Lemma with the centered moments; the oracle's
-    # C is the pairwise definition.  Both are FP64 on the same FP32 inputs.
-    assert abs(en[gw.EN["C"]] - ref["C"]) <= 1e-10 * abs(ref["C"])
+    # The GPU's C takes the Lemma's moments, which assume sum a X = 0; the
+    # oracle's C is the pairwise definition (translation invariant).  The FP32
+    # inputs are centered only up to the FP32 rounding of X (mu ~ 2^-24 |X|),
+    # which moves the moment form by about 16 |mu| m3 ~ 1e-7 relative.
+    mu = max(np.abs(a @ X).max(), np.abs(b @ Y).max())
+    assert abs(en[gw.EN["C"]] - ref["C"]) <= (1e-12 + 64 * mu) * abs(ref["C"])
     rel = plan_tolerance(P, pi, D)
     scale = ref["C"] + 8 * np.sum(O.cross_covariance(pi, X, Y) ** 2) + 4 * (P["s"] @ pi @ P["t"])
     assert abs(en[gw.EN["L"]] - ref["L"]) <= 4 * rel * scale
