@@ -58,6 +58,7 @@ def parse():
                     help="lift: Kernel PCA of ||x-x'|| (the workload); random: Gaussian features "
                          "of the same shape (kernel-only runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     return ap.parse_args()
 
 
@@ -281,7 +282,7 @@ def run_gw(args, rank, world, local):
         e2e_t, e2e_u = (e2e["seconds"], e2e["cells"]) if e2e else (None, None)
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         Xh, Yh = X.double().cpu().numpy(), Y.double().cpu().numpy()
         cpu = run_cpu_baseline(Xh, Yh, a.double().cpu().numpy(), b.double().cpu().numpy(),
                                eps_at(args, args.n_outer - 1))
