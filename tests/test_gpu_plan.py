@@ -91,9 +91,13 @@ def test_energy_matches_oracle(gw, n, m, D, E, eps):
     assert abs(en[gw.EN["C"]] - ref["C"]) <= (1e-12 + 64 * mu) * abs(ref["C"])
     rel = plan_tolerance(P, pi, D)
     scale = ref["C"] + 8 * np.sum(O.cross_covariance(pi, X, Y) ** 2) + 4 * (P["s"] @ pi @ P["t"])
-    assert abs(en[gw.EN["L"]] - ref["L"]) <= 4 * rel * scale
-    assert abs(en[gw.EN["KL"]] - ref["KL"]) <= 4 * rel * (scale / eps + abs(ref["KL"])) + 1e-9
-    assert abs(en[gw.EN["E"]] - ref["E"]) <= 1e-4 * abs(ref["E"])
+    tol_L = 4 * rel * scale
+    tol_KL = 4 * rel * (scale / eps + abs(ref["KL"])) + 1e-9
+    assert abs(en[gw.EN["L"]] - ref["L"]) <= tol_L
+    assert abs(en[gw.EN["KL"]] - ref["KL"]) <= tol_KL
+    # E = L + eps KL: the sum of the two bounds (these are arbitrary,
+    # unconverged states; the 1e-4 target applies to converged solves)
+    assert abs(en[gw.EN["E"]] - ref["E"]) <= tol_L + eps * tol_KL
     row, col = pi.sum(1), pi.sum(0)
     assert abs(en[gw.EN["row_l1"]] - np.abs(row - a).sum()) <= 4 * rel + 1e-9
     assert abs(en[gw.EN["col_l1"]] - np.abs(col - b).sum()) <= 4 * rel + 1e-9
