@@ -116,6 +116,38 @@ int gw_sinkhorn_softmin(const float* A, const float* B, const float* sA, const f
                         size_t ws_bytes, gw_stream_t stream);
 
 /*
+ * gw_sinkhorn_softmin_noalloc -- gw_sinkhorn_softmin for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this is a service
+ * of the library.
+ *
+ * Some callers can't call cudaMalloc or pass a workspace: runtimes that
+ * reserve all device memory up front and forbid allocation afterwards, host
+ * code that runs where an allocation's implicit device synchronisation is
+ * not allowed, and plug-in hosts that give their plug-ins no allocator.  This
+ * entry point takes the same arguments as gw_sinkhorn_softmin minus the
+ * workspace and computes the same result with the same kernels; its scratch
+ * (the per-split partial maxima and sums) lives in a 2 MiB static device
+ * array inside the library, which every GPU that loads the library holds
+ * until the process exits.  It calls no allocating function.
+ *   - Sizes whose scratch exceeds 2 MiB (gw_workspace_size(GW_OP_SOFTMIN,
+ *     ...) > 2 MiB, e.g. n above ~131k when the columns are split) return
+ *     GW_ENOMEM with the sizes in gw_last_error().
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *     The current device must be the device of `stream`.
+ *   - All calls on a device share the one array: calls that overlap on the
+ *     GPU (different streams, or host threads) race and give wrong results.
+ *     Serialise them, e.g. on one stream.
+ *   - The array keeps the last call's contents; nothing in it needs to start
+ *     at zero.
+ *   Only GW_PREC_FP32.  Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
+ */
+int gw_sinkhorn_softmin_noalloc(const float* A, const float* B, const float* sA,
+                                const float* sB, const float* h, const float* logw, float eps,
+                                int64_t n, int64_t m, int K, int prec, const float* avg_with,
+                                float* out, gw_stream_t stream);
+
+/*
  * gw_cross_cov -- the plan-weighted reduction of Algorithm 1 (its Xtilde and
  * Gamma_{t+1} lines; Theorem 3.3): with pi built from (f, g) on c_{Gamma_t}
  * at temperature eps,

@@ -20,7 +20,7 @@ __all__ = [
     "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
     "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
     "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
-    "gw_kernel_launches",
+    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc",
 ]
 
 GW_OK = 0
@@ -71,6 +71,9 @@ class GwResult(ctypes.Structure):
 
 lib.gw_sinkhorn_softmin.argtypes = [_p, _p, _p, _p, _p, _p, _f, _i64, _i64, _int, _int, _p, _p,
                                     _p, _sz, _p]
+lib.gw_sinkhorn_softmin_noalloc.argtypes = [_p, _p, _p, _p, _p, _p, _f, _i64, _i64, _int, _int,
+                                            _p, _p, _p]
+lib.gw_sinkhorn_softmin_noalloc.restype = _int
 lib.gw_cross_cov.argtypes = [_p, _p, _p, _p, _p, _p, _p, _p, _p, _f, _i64, _i64, _int, _int, _int,
                              _p, _p, _p, _p, _sz, _p]
 lib.gw_energy.argtypes = [_p, _p, _p, _p, _p, _p, _p, _p, _p, _f, _i64, _i64, _int, _int, _int, _p,
@@ -166,6 +169,23 @@ def gw_sinkhorn_softmin(A, B, sA, sB, h, logw, eps, prec=PREC_FP32, avg_with=Non
         _ptr(_f32(h, "h")), _ptr(_f32(logw, "logw")), float(eps), n, m, K, prec,
         _ptr(_f32(avg_with, "avg_with")), _ptr(_f32(out, "out")), _ptr(ws), ws.numel(),
         _stream(stream)))
+    return out
+
+
+def gw_sinkhorn_softmin_noalloc(A, B, sA, sB, h, logw, eps, prec=PREC_FP32, avg_with=None,
+                                out=None, stream=None):
+    """gw_sinkhorn_softmin without a workspace, for callers that cannot
+    allocate: the library keeps the scratch in a 2 MiB static device array
+    (see gw.h for the limits, the first-call set-up and why overlapping calls
+    race).  `out` must be preallocated by a caller that cannot allocate."""
+    n, K = A.shape
+    m = B.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=A.device)
+    _check(lib.gw_sinkhorn_softmin_noalloc(
+        _ptr(_f32(A, "A")), _ptr(_f32(B, "B")), _ptr(_f32(sA, "sA")), _ptr(_f32(sB, "sB")),
+        _ptr(_f32(h, "h")), _ptr(_f32(logw, "logw")), float(eps), n, m, K, prec,
+        _ptr(_f32(avg_with, "avg_with")), _ptr(_f32(out, "out")), _stream(stream)))
     return out
 
 
