@@ -59,6 +59,7 @@ typedef struct CUstream_st* gw_stream_t;
 #define GW_PREC_FP32 0     /* FP32 dot products on the CUDA cores */
 #define GW_PREC_BF16 1     /* BF16 operands on tcgen05, FP32 accumulate */
 #define GW_PREC_BF16X3 2   /* split BF16 (hi*hi + hi*lo + lo*hi) on tcgen05 */
+#define GW_PREC_F16X3 3    /* split FP16 with scaling (hi*hi + hi*lo + lo*hi) on tcgen05 */
 
 /* CNT penalties accepted by gw_lift (Section 2, "Embeddable costs") */
 #define GW_PEN_SQEUCLID 0  /* ||x - x'||^2: the lift is a centering */
@@ -107,7 +108,8 @@ typedef struct CUstream_st* gw_stream_t;
  *   A: n x K, B: m x K (row-major float32), sA, out, avg_with: n; sB, h, logw: m.
  *   avg_with may alias out.  logw_j = -inf (zero weight) is allowed.
  *   1 <= K <= GW_MAX_FEATURES, m >= 1, n >= 0 (n == 0 is a no-op), eps > 0.
- *   prec: GW_PREC_*; BF16 modes need K <= 64.
+ *   prec: GW_PREC_*.  Tensor-core modes need 6 + K (BF16) or 6 + 3K (BF16X3,
+ *   F16X3) <= 192 and |exponent| < 1e9 (base 2) for real cells.
  * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
  */
 int gw_sinkhorn_softmin(const float* A, const float* B, const float* sA, const float* sB,

@@ -33,7 +33,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
 
-bool prec_ok(int prec) { return prec == GW_PREC_FP32; }
+bool prec_ok(int prec) { return prec >= GW_PREC_FP32 && prec <= GW_PREC_F16X3; }
 
 int check_eps(float eps) {
   GW_REQUIRE(eps > 0.0f && isfinite(eps), GW_EINVAL, "eps must be finite and > 0 (got %g)",
@@ -52,7 +52,7 @@ int check_dims(int64_t n, int64_t m, int D, int E) {
 }
 
 int check_prec(int prec) {
-  GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_BF16X3, GW_EINVAL, "unknown precision %d",
+  GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_F16X3, GW_EINVAL, "unknown precision %d",
              prec);
   GW_REQUIRE(prec_ok(prec), GW_EUNSUPPORTED, "precision %d is not available in this build", prec);
   return GW_OK;

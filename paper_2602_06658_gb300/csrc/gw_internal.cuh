@@ -133,6 +133,12 @@ struct SoftminShape {
 SoftminShape softmin_shape(int64_t n, int64_t m, int K, int prec);
 size_t softmin_ws_bytes(int64_t n, int64_t m, int K, int prec);
 
+// Tensor-core form (gw_softmin_tc.cu): support test, workspace and launch
+// (fills splits / pm / ps of the tasks; the caller merges the partials).
+bool softmin_tc_supported(int K, int prec);
+size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec);
+int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cudaStream_t st);
+
 // Launch one or two softmin tasks (two = the row and column half-steps of a
 // symmetric Sinkhorn iteration in a single launch).  Partials come from the
 // carver.  Host-side only; the tasks must already be validated.

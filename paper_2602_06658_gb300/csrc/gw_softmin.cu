@@ -197,6 +197,7 @@ SoftminShape softmin_shape(int64_t n, int64_t m, int K, int prec) {
 }
 
 size_t softmin_ws_bytes(int64_t n, int64_t m, int K, int prec) {
+  if (prec != GW_PREC_FP32) return softmin_tc_ws_bytes(n, m, K, prec);
   Carver c(nullptr, ~size_t(0));
   const SoftminShape sh = softmin_shape(n, m, K, prec);
   if (sh.splits > 1) {
@@ -207,45 +208,50 @@ size_t softmin_ws_bytes(int64_t n, int64_t m, int K, int prec) {
 }
 
 int launch_softmin(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cudaStream_t st) {
-  GW_REQUIRE(prec == GW_PREC_FP32, GW_EUNSUPPORTED, "softmin precision %d not built", prec);
   SoftminTask t[2];
-  int blocks[2] = {0, 0};
-  int KP = 0;
-  for (int q = 0; q < ntasks; ++q) {
-    t[q] = tasks[q];
-    const SoftminShape sh = softmin_shape(t[q].n, t[q].m, t[q].K, prec);
-    t[q].splits = sh.splits;
-    t[q].cols_per_split = sh.cols_per_split;
-    t[q].pm = t[q].ps = nullptr;
-    if (sh.splits > 1) {
-      t[q].pm = ws.take<float>(static_cast<size_t>(sh.splits) * t[q].n);
-      t[q].ps = ws.take<float>(static_cast<size_t>(sh.splits) * t[q].n);
+  for (int q = 0; q < ntasks; ++q) t[q] = tasks[q];
+  GW_REQUIRE(ntasks == 1 || t[0].K == t[1].K, GW_EINVAL, "fused softmin tasks need the same K");
+  if (prec != GW_PREC_FP32) {
+    GW_TRY(launch_softmin_tc(t, ntasks, prec, ws, st));
+  } else {
+    int blocks[2] = {0, 0};
+    for (int q = 0; q < ntasks; ++q) {
+      const SoftminShape sh = softmin_shape(t[q].n, t[q].m, t[q].K, prec);
+      t[q].splits = sh.splits;
+      t[q].cols_per_split = sh.cols_per_split;
+      t[q].pm = t[q].ps = nullptr;
+      if (sh.splits > 1) {
+        t[q].pm = ws.take<float>(static_cast<size_t>(sh.splits) * t[q].n);
+        t[q].ps = ws.take<float>(static_cast<size_t>(sh.splits) * t[q].n);
+      }
+      blocks[q] = sh.row_blocks * sh.splits;
     }
-    blocks[q] = sh.row_blocks * sh.splits;
-    const int kp = kpad(t[q].K);
-    KP = kp > KP ? kp : KP;
+    GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for softmin partials");
+    SoftminTask u1 = t[1];
+    if (ntasks == 1) {
+      u1 = t[0];
+      u1.n = 0;
+    }
+    const int total = blocks[0] + blocks[1];
+    if (total > 0) {
+      switch (kpad(t[0].K)) {
+        case 4: launch_fp32<4>(t[0], u1, blocks[0], total, st); break;
+        case 8: launch_fp32<8>(t[0], u1, blocks[0], total, st); break;
+        case 16: launch_fp32<16>(t[0], u1, blocks[0], total, st); break;
+        case 32: launch_fp32<32>(t[0], u1, blocks[0], total, st); break;
+        case 64: launch_fp32<64>(t[0], u1, blocks[0], total, st); break;
+        default: launch_fp32<128>(t[0], u1, blocks[0], total, st); break;
+      }
+      GW_LAUNCH_CHECK();
+    }
   }
-  GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for softmin partials");
-  GW_REQUIRE(ntasks == 1 || kpad(t[0].K) == kpad(t[1].K), GW_EINVAL,
-             "fused softmin tasks need the same padded K");
   if (ntasks == 1) {
     t[1] = t[0];
     t[1].n = 0;
   }
-  const int total = blocks[0] + blocks[1];
-  if (total == 0) return GW_OK;
-  switch (KP) {
-    case 4: launch_fp32<4>(t[0], t[1], blocks[0], total, st); break;
-    case 8: launch_fp32<8>(t[0], t[1], blocks[0], total, st); break;
-    case 16: launch_fp32<16>(t[0], t[1], blocks[0], total, st); break;
-    case 32: launch_fp32<32>(t[0], t[1], blocks[0], total, st); break;
-    case 64: launch_fp32<64>(t[0], t[1], blocks[0], total, st); break;
-    default: launch_fp32<128>(t[0], t[1], blocks[0], total, st); break;
-  }
-  GW_LAUNCH_CHECK();
   const bool need_combine = t[0].splits > 1 || (ntasks == 2 && t[1].splits > 1);
   if (need_combine) {
-    const int64_t nn = t[0].n + (ntasks == 2 ? t[1].n : 0);
+    const int64_t nn = t[0].n + t[1].n;
     const int thr = 256;
     softmin_combine_kernel<<<ceil_div(nn, thr), thr, 0, st>>>(t[0], t[1], t[0].n);
     GW_LAUNCH_CHECK();

@@ -1,0 +1,577 @@
+// Softmin on the bilinear cost with the cost tile on the 5th-generation
+// tensor cores (tcgen05), sm_103a.
+//
+//   out_i = -eps * LSE_j [ logw_j + (h_j + 16 <A_i, B_j> + 4 sA_i sB_j) / eps ]
+//
+// The whole exponent z_ij (base 2) is one matrix product of two 16-bit
+// operand matrices built from A and B (the discrete Sinkhorn operator,
+// Eq. sinkhorn_operators, on c_Gamma):
+//   columns [0, mult*K)        the scaled dot product alpha <A_i, B_j>, with
+//                              alpha = 16 log2(e) / eps, as one product
+//                              (mult = 1) or as a two-way split
+//                              hi*hi + hi*lo + lo*hi (mult = 3);
+//   3 columns                  beta sA_i sB_j (beta = 4 log2(e) / eps) as a
+//                              two-way split product;
+//   3 columns                  the column bias w_j = (h_j/eps + logw_j) log2(e),
+//                              a three-way split times a power-of-two constant;
+//   zero padding to KP (a multiple of 64).
+// So the epilogue only keeps a running (max, sum of exp2) per row.
+//
+// CTA layout (one CTA per SM): 256 rows as two M = 128 accumulators, column
+// tiles of BN = 128 streamed by TMA through a ring of S stages (128-byte
+// swizzle), double-buffered in TMEM (2 buffers x 2 halves x 128 columns =
+// all 512 columns).  Warp 0 issues TMA, warp 1 issues tcgen05.mma, warps 2-9
+// each own 32 rows (one TMEM lane quarter of one half).  Every wait is
+// bounded in time; on a timeout the CTA drains its copies and MMAs, frees
+// TMEM and writes NaN rows.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "gw_internal.cuh"
+#include "gw_tc.cuh"
+
+namespace gw {
+
+namespace {
+
+constexpr int kBM = 256;       // rows per CTA (two M = 128 halves)
+constexpr int kBN = 128;       // columns per tile
+constexpr int kThreadsTc = 320;
+constexpr float kBiasConst = 32768.0f;       // A-side multiplier of the bias columns
+constexpr float kHalfMax = 65504.0f;
+constexpr float kRunInit = -1.0e9f;          // running max start (below every real exponent)
+
+struct TcOperandShape {
+  int K;        // feature dimension
+  int mult;     // 1 or 3 products in the dot
+  int KP;       // padded operand width
+  int col_u;    // first rank-one column
+  int col_w;    // first bias column
+};
+
+TcOperandShape tc_shape(int K, int prec) {
+  TcOperandShape s;
+  s.K = K;
+  s.mult = prec == GW_PREC_BF16 ? 1 : 3;
+  s.col_u = s.mult * K;
+  s.col_w = s.col_u + 3;
+  const int need = s.col_w + 3;
+  s.KP = ((need + 63) / 64) * 64;
+  return s;
+}
+
+bool tc_is_bf16(int prec) { return prec != GW_PREC_F16X3; }
+
+int max_splits(int col_tiles) { return col_tiles < 64 ? col_tiles : 64; }
+
+template <class T>
+__device__ __forceinline__ T to16(float x);
+template <>
+__device__ __forceinline__ __half to16<__half>(float x) {
+  return __float2half_rn(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+__device__ __forceinline__ float from16(__half x) { return __half2float(x); }
+__device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// max |x| of four arrays -> mx[0..3] (non-negative floats compare as ints)
+__global__ void tc_absmax_kernel(const float* A, int64_t nA, const float* B, int64_t nB,
+                                 const float* sA, int64_t n, const float* sB, int64_t m,
+                                 unsigned* mx) {
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < nA; i += stride) v[0] = fmaxf(v[0], fabsf(A[i]));
+  for (int64_t i = t0; i < nB; i += stride) v[1] = fmaxf(v[1], fabsf(B[i]));
+  for (int64_t i = t0; i < n; i += stride) v[2] = fmaxf(v[2], fabsf(sA[i]));
+  for (int64_t i = t0; i < m; i += stride) v[3] = fmaxf(v[3], fabsf(sB[i]));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&mx[k], __float_as_uint(v[k]));
+  }
+}
+
+// Scale pair (sa, sb) with sa * sb = prod that balances max|x sa| and max|y sb|.
+__device__ __forceinline__ void balance(float prod, float mxa, float mxb, float* sa, float* sb) {
+  if (!(mxa > 0.f) || !(mxb > 0.f)) {
+    *sa = 1.0f;
+    *sb = prod;
+    return;
+  }
+  const float r = sqrtf(prod * mxb / mxa);
+  *sa = r;
+  *sb = prod / r;
+}
+
+// Operand rows.  role 0 = A side (row operand), role 1 = B side (column
+// operand, bias columns included).  Rows >= rows_valid are padding: zeros,
+// and for the B side a bias of -65504 * kBiasConst so they add nothing.
+template <class T>
+__global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, const float* logw,
+                               int64_t rows_valid, int64_t rows_pad, TcOperandShape shp, int role,
+                               float alpha, float beta, float inv_eps, const unsigned* mx, T* op) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
+  if (r >= rows_pad) return;
+  const float mA = __uint_as_float(mx[0]), mB = __uint_as_float(mx[1]);
+  const float msA = __uint_as_float(mx[2]), msB = __uint_as_float(mx[3]);
+  float sa, sb, ua, ub;
+  balance(alpha, mA, mB, &sa, &sb);
+  balance(beta, msA, msB, &ua, &ub);
+  const float sc = role == 0 ? sa : sb;
+  const float us = role == 0 ? ua : ub;
+  T* row = op + r * shp.KP;
+  const bool valid = r < rows_valid;
+  const int K = shp.K;
+  for (int k = threadIdx.x; k < shp.KP; k += blockDim.x) {
+    float v = 0.0f;
+    if (valid) {
+      if (k < shp.col_u) {
+        const int part = k / K, kk = k % K;
+        const float x = X[r * K + kk] * sc;
+        const float hi = from16(to16<T>(x));
+        // A side [hi, hi, lo], B side [hi, lo, hi]: hi*hi + hi*lo + lo*hi
+        const bool lo = shp.mult == 3 && ((role == 0 && part == 2) || (role == 1 && part == 1));
+        v = lo ? x - hi : hi;
+      } else if (k < shp.col_w) {
+        const int part = k - shp.col_u;
+        const float x = sq[r] * us;
+        const float hi = from16(to16<T>(x));
+        if (role == 0) v = part < 2 ? hi : x - hi;   // [hi, hi, lo]
+        else v = part == 1 ? x - hi : hi;            // [hi, lo, hi]
+      } else if (k < shp.col_w + 3) {
+        if (role == 0) {
+          v = kBiasConst;
+        } else {
+          float w = (h[r] * inv_eps + logw[r]) * kLog2e / kBiasConst;
+          w = fmaxf(w, -kHalfMax);             // zero weights: effectively -inf
+          const float w0 = from16(to16<T>(w));
+          const float r1 = w - w0;
+          const float w1 = from16(to16<T>(r1));
+          const float w2 = r1 - w1;
+          const int part = k - shp.col_w;
+          v = part == 0 ? w0 : (part == 1 ? w1 : w2);
+        }
+      }
+    } else if (role == 1 && k == shp.col_w) {
+      v = -kHalfMax;
+    }
+    row[k] = to16<T>(v);
+  }
+}
+
+struct TcTask {
+  int64_t n, m;           // real rows / columns
+  int row_tiles;          // ceil(n / 256)
+  int col_tiles;          // m_pad / 128
+  int splits;
+  int tiles_per_split;
+  int blocks;
+  float eps;
+  const float* avg_with;
+  float* out;
+  float* pm;
+  float* ps;
+};
+
+template <int KP, int S>
+struct TcSmem {
+  static constexpr int KB = KP / 64;
+  static constexpr int kABytes = 2 * KB * 16384;          // 256 rows
+  static constexpr int kStageBytes = KB * 16384;          // 128 rows
+  static constexpr int kBarOff = kABytes + S * kStageBytes;
+  // + barriers + alignment slack; at least 120 KB so that one CTA owns the
+  // SM (it allocates all 512 TMEM columns)
+  static constexpr int kBytes = kBarOff + 1280 > 122880 ? kBarOff + 1280 : 122880;
+};
+
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = tc::globaltimer();
+  while (!tc::mbar_try_wait(bar, parity)) {
+    if (tc::globaltimer() - t0 > tc::kWaitLimitNs) return false;
+  }
+  return true;
+}
+
+template <int KP, int S, bool BF16>
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    softmin_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mB0,
+                      const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mB1,
+                      TcTask t0, TcTask t1) {
+  using L = TcSmem<KP, S>;
+  constexpr int KB = L::KB;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* As = smem;
+  unsigned char* Bs = smem + L::kABytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kBarOff);
+  uint64_t* full = bars;                // [S]
+  uint64_t* empty = bars + S;           // [S]
+  uint64_t* tfull = bars + 2 * S;       // [2]
+  uint64_t* tempty = bars + 2 * S + 2;  // [2]
+  uint64_t* afull = bars + 2 * S + 4;
+  uint64_t* drain = bars + 2 * S + 5;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ int consumed;
+
+  const bool second = static_cast<int>(blockIdx.x) >= t0.blocks;
+  const TcTask& T = second ? t1 : t0;
+  const CUtensorMap* mA = second ? &mA1 : &mA0;
+  const CUtensorMap* mB = second ? &mB1 : &mB0;
+  const int bid = second ? blockIdx.x - t0.blocks : blockIdx.x;
+  const int rt = bid / T.splits;
+  const int sp = bid % T.splits;
+  const int row0 = rt * kBM;
+  const int tile0 = sp * T.tiles_per_split;
+  const int ntiles = min(T.tiles_per_split, T.col_tiles - tile0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    consumed = 0;
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], 8);
+    }
+    tc::mbar_init(afull, 1);
+    tc::mbar_init(drain, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 512);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  volatile int* ab = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- producer
+      tc::prefetch_tmap(mA);
+      tc::prefetch_tmap(mB);
+      tc::mbar_arrive_expect_tx(afull, L::kABytes);
+      for (int h = 0; h < 2; ++h)
+        for (int kb = 0; kb < KB; ++kb)
+          tc::tma_load_2d(As + (h * KB + kb) * 16384, mA, kb * 64, row0 + h * 128, afull);
+      int issued = 0;
+      for (int t = 0; t < ntiles; ++t) {
+        const int s = t % S;
+        if (!tc::mbar_wait(&empty[s], ((t / S) & 1) ^ 1, ab)) break;
+        tc::mbar_arrive_expect_tx(&full[s], L::kStageBytes);
+        for (int kb = 0; kb < KB; ++kb)
+          tc::tma_load_2d(Bs + s * L::kStageBytes + kb * 16384, mB, kb * 64, (tile0 + t) * kBN,
+                          &full[s]);
+        issued = t + 1;
+      }
+      if (*ab) {
+        // wind down: wait for the copies still in flight before leaving
+        mbar_drain(afull, 0);
+        const int done = *reinterpret_cast<volatile int*>(&consumed);
+        for (int t = done; t < issued; ++t) mbar_drain(&full[t % S], (t / S) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------- MMA issuer
+      const uint32_t idesc = tc::f16_idesc(128, kBN, BF16);
+      bool ok = tc::mbar_wait(afull, 0, ab);
+      for (int t = 0; ok && t < ntiles; ++t) {
+        const int s = t % S, b = t & 1;
+        if (!tc::mbar_wait(&tempty[b], ((t >> 1) & 1) ^ 1, ab)) break;
+        if (!tc::mbar_wait(&full[s], (t / S) & 1, ab)) break;
+        tc::tc_fence_after();
+        const unsigned char* Bst = Bs + s * L::kStageBytes;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+          for (int ks = 0; ks < KP / 16; ++ks) {
+            const uint32_t aaddr = tc::smem_u32(As + (h * KB + ks / 4) * 16384 + (ks % 4) * 32);
+            const uint32_t baddr = tc::smem_u32(Bst + (ks / 4) * 16384 + (ks % 4) * 32);
+            tc::mma_f16(tbase + (b * 2 + h) * 128, tc::sw128_desc(aaddr), tc::sw128_desc(baddr),
+                        idesc, ks > 0 ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(&empty[s]);
+        tc::mma_commit(&tfull[b]);
+        *reinterpret_cast<volatile int*>(&consumed) = t + 1;
+      }
+      // every MMA issued above has finished before TMEM is freed
+      tc::mma_commit(drain);
+      mbar_drain(drain, 0);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int e = warp - 2;
+    const int h = e >> 2;
+    const int q = warp & 3;
+    const int64_t row = static_cast<int64_t>(row0) + h * 128 + q * 32 + lane;
+    float mrun = kRunInit, srun = 0.0f;
+    bool ok = true;
+    for (int t = 0; t < ntiles; ++t) {
+      const int b = t & 1;
+      // one lane waits, the warp follows: tcgen05.ld needs a converged warp
+      int got = 0;
+      if (lane == 0) got = tc::mbar_wait(&tfull[b], (t >> 1) & 1, ab) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (!got) {
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      const uint32_t tcol = tbase + (static_cast<uint32_t>(q * 32) << 16) + (b * 2 + h) * 128;
+#pragma unroll 1
+      for (int c = 0; c < kBN / 32; ++c) {
+        float v[32];
+        tc::tmem_ld32(tcol + c * 32, v);
+        float cm = v[0];
+#pragma unroll
+        for (int k = 1; k < 32; ++k) cm = fmaxf(cm, v[k]);
+        if (cm > mrun) {
+          srun *= ex2(mrun - cm);
+          mrun = cm;
+        }
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; k += 2) {
+          s0 += ex2(v[k] - mrun);
+          s1 += ex2(v[k + 1] - mrun);
+        }
+        srun += s0 + s1;
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[b]);
+    }
+    if (row < T.n) {
+      if (!ok || *ab) {
+        const float nan = __int_as_float(0x7fc00000);
+        if (T.splits == 1) T.out[row] = nan;
+        else {
+          T.pm[static_cast<int64_t>(sp) * T.n + row] = nan;
+          T.ps[static_cast<int64_t>(sp) * T.n + row] = nan;
+        }
+      } else if (T.splits == 1) {
+        float v = -T.eps * kLn2 * (mrun + log2f(srun));
+        if (T.avg_with) v = 0.5f * (T.avg_with[row] + v);
+        T.out[row] = v;
+      } else {
+        T.pm[static_cast<int64_t>(sp) * T.n + row] = mrun;
+        T.ps[static_cast<int64_t>(sp) * T.n + row] = srun;
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tbase, 512);
+  }
+}
+
+// ------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+int make_map(CUtensorMap* map, void* ptr, int64_t rows, int KP, bool bf16, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  GW_REQUIRE(enc != nullptr, GW_ECUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(KP), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(KP) * 2};
+  cuuint32_t box[2] = {64, static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  GW_REQUIRE(r == CUDA_SUCCESS, GW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return GW_OK;
+}
+
+int tc_splits(int row_tiles, int col_tiles, int other_blocks) {
+  // Pick the column split that fills whole waves of 152 CTAs best.
+  int best = 1;
+  double best_eff = 0.0;
+  const int smax = max_splits(col_tiles);
+  for (int s = 1; s <= smax; ++s) {
+    const int blocks = row_tiles * s + other_blocks * s;
+    const int waves = (blocks + kSmCount - 1) / kSmCount;
+    const double eff = static_cast<double>(blocks) / (static_cast<double>(waves) * kSmCount);
+    const double tiles = static_cast<double>(col_tiles) / s;
+    if (tiles < 4.0 && s > 1) break;   // keep >= 4 tiles per CTA to amortise set-up
+    if (eff > best_eff + 1e-3) {
+      best_eff = eff;
+      best = s;
+    }
+    if (eff > 0.97) break;
+  }
+  return best;
+}
+
+template <int KP, int S, bool BF16>
+int launch_tc_kernel(const CUtensorMap* maps, const TcTask& a, const TcTask& b, cudaStream_t st) {
+  using L = TcSmem<KP, S>;
+  auto kern = softmin_tc_kernel<KP, S, BF16>;
+  static bool attr_set = false;  // set once per process (same value every time)
+  if (!attr_set) {
+    GW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
+    attr_set = true;
+  }
+  kern<<<a.blocks + b.blocks, kThreadsTc, L::kBytes, st>>>(maps[0], maps[1], maps[2], maps[3], a, b);
+  GW_LAUNCH_CHECK();
+  return GW_OK;
+}
+
+template <bool BF16>
+int dispatch_tc(int KP, const CUtensorMap* maps, const TcTask& a, const TcTask& b, cudaStream_t st) {
+  switch (KP) {
+    case 64: return launch_tc_kernel<64, 4, BF16>(maps, a, b, st);
+    case 128: return launch_tc_kernel<128, 3, BF16>(maps, a, b, st);
+    case 192: return launch_tc_kernel<192, 2, BF16>(maps, a, b, st);
+    default: break;
+  }
+  set_error("tensor-core softmin: operand width %d (K too large for this precision)", KP);
+  return GW_EUNSUPPORTED;
+}
+
+}  // namespace
+
+bool softmin_tc_supported(int K, int prec) {
+  if (prec != GW_PREC_BF16 && prec != GW_PREC_BF16X3 && prec != GW_PREC_F16X3) return false;
+  return tc_shape(K, prec).KP <= 192;
+}
+
+size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
+  const TcOperandShape shp = tc_shape(K, prec);
+  const int64_t n_pad = ((n + kBM - 1) / kBM) * kBM;
+  const int64_t m_pad = ((m + kBN - 1) / kBN) * kBN;
+  Carver c(nullptr, ~size_t(0));
+  c.take<uint16_t>(static_cast<size_t>(n_pad) * shp.KP);
+  c.take<uint16_t>(static_cast<size_t>(m_pad) * shp.KP);
+  c.take<unsigned>(4);
+  // partials for the largest split count any launch may pick
+  const int s = max_splits(static_cast<int>(m_pad / kBN));
+  c.take<float>(static_cast<size_t>(s) * n);
+  c.take<float>(static_cast<size_t>(s) * n);
+  return c.used();
+}
+
+// Prepare operands for one or two tasks and launch the tensor-core kernel.
+// Fills tasks[q].splits / pm / ps so the caller can merge split partials.
+int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cudaStream_t st) {
+  GW_REQUIRE(softmin_tc_supported(tasks[0].K, prec), GW_EUNSUPPORTED,
+             "tensor-core softmin does not support K=%d with precision %d", tasks[0].K, prec);
+  const bool bf16 = tc_is_bf16(prec);
+  CUtensorMap maps[4];
+  TcTask tt[2];
+  memset(tt, 0, sizeof(tt));
+  const TcOperandShape shp = tc_shape(tasks[0].K, prec);
+  int row_tiles[2] = {0, 0}, col_tiles[2] = {0, 0};
+  for (int q = 0; q < ntasks; ++q) {
+    row_tiles[q] = ceil_div(tasks[q].n, kBM);
+    col_tiles[q] = ceil_div(tasks[q].m, kBN);
+  }
+  // one split count for the launch, chosen from both tasks' tiles
+  const int splits = tc_splits(row_tiles[0], col_tiles[0], ntasks == 2 ? row_tiles[1] : 0);
+  for (int q = 0; q < ntasks; ++q) {
+    SoftminTask& T = tasks[q];
+    const int64_t n_pad = static_cast<int64_t>(row_tiles[q]) * kBM;
+    const int64_t m_pad = static_cast<int64_t>(col_tiles[q]) * kBN;
+    uint16_t* opA = ws.take<uint16_t>(static_cast<size_t>(n_pad) * shp.KP);
+    uint16_t* opB = ws.take<uint16_t>(static_cast<size_t>(m_pad) * shp.KP);
+    unsigned* mx = ws.take<unsigned>(4);
+    int s = splits < col_tiles[q] ? splits : col_tiles[q];
+    const int tps = ceil_div(col_tiles[q], s);
+    s = ceil_div(col_tiles[q], tps);
+    T.splits = s;
+    T.cols_per_split = tps * kBN;
+    T.pm = T.ps = nullptr;
+    if (s > 1) {
+      T.pm = ws.take<float>(static_cast<size_t>(s) * T.n);
+      T.ps = ws.take<float>(static_cast<size_t>(s) * T.n);
+    }
+    GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
+    GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned), st));
+    tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
+                                                   T.sB, T.m, mx);
+    GW_LAUNCH_CHECK();
+    const float inv_eps = 1.0f / T.eps;
+    const float alpha = 16.0f * kLog2e * inv_eps;
+    const float beta = 4.0f * kLog2e * inv_eps;
+    dim3 blk(64, 4);
+    if (bf16) {
+      tc_prep_kernel<__nv_bfloat16><<<ceil_div(n_pad, 4), blk, 0, st>>>(
+          T.A, T.sA, nullptr, nullptr, T.n, n_pad, shp, 0, alpha, beta, inv_eps, mx,
+          reinterpret_cast<__nv_bfloat16*>(opA));
+      GW_LAUNCH_CHECK();
+      tc_prep_kernel<__nv_bfloat16><<<ceil_div(m_pad, 4), blk, 0, st>>>(
+          T.B, T.sB, T.h, T.logw, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
+          reinterpret_cast<__nv_bfloat16*>(opB));
+      GW_LAUNCH_CHECK();
+    } else {
+      tc_prep_kernel<__half><<<ceil_div(n_pad, 4), blk, 0, st>>>(
+          T.A, T.sA, nullptr, nullptr, T.n, n_pad, shp, 0, alpha, beta, inv_eps, mx,
+          reinterpret_cast<__half*>(opA));
+      GW_LAUNCH_CHECK();
+      tc_prep_kernel<__half><<<ceil_div(m_pad, 4), blk, 0, st>>>(
+          T.B, T.sB, T.h, T.logw, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
+          reinterpret_cast<__half*>(opB));
+      GW_LAUNCH_CHECK();
+    }
+    GW_TRY(make_map(&maps[2 * q], opA, n_pad, shp.KP, bf16, 128));
+    GW_TRY(make_map(&maps[2 * q + 1], opB, m_pad, shp.KP, bf16, kBN));
+    TcTask& K = tt[q];
+    K.n = T.n;
+    K.m = T.m;
+    K.row_tiles = row_tiles[q];
+    K.col_tiles = col_tiles[q];
+    K.splits = s;
+    K.tiles_per_split = tps;
+    K.blocks = row_tiles[q] * s;
+    K.eps = T.eps;
+    K.avg_with = T.avg_with;
+    K.out = T.out;
+    K.pm = T.pm;
+    K.ps = T.ps;
+  }
+  if (ntasks == 1) {
+    maps[2] = maps[0];
+    maps[3] = maps[1];
+    tt[1] = tt[0];
+    tt[1].blocks = 0;
+  }
+  return bf16 ? dispatch_tc<true>(shp.KP, maps, tt[0], tt[1], st)
+              : dispatch_tc<false>(shp.KP, maps, tt[0], tt[1], st);
+}
+
+}  // namespace gw

@@ -104,3 +104,44 @@ def test_softmin_is_deterministic(gw):
     o1 = gw.gw_sinkhorn_softmin(*args, 0.07)
     o2 = gw.gw_sinkhorn_softmin(*args, 0.07)
     assert bool((o1 == o2).all())
+
+
+TC_SHAPES = [(1, 1, 1), (7, 5, 2), (300, 517, 3), (513, 2049, 16), (1200, 700, 32),
+             (257, 300, 60), (4099, 33, 5), (31, 5000, 8), (2000, 2000, 32)]
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+@pytest.mark.parametrize("n,m,K", TC_SHAPES)
+@pytest.mark.parametrize("eps", [1.0, 0.05])
+def test_tensor_core_softmin_matches_oracle(gw, prec, n, m, K, eps):
+    from helpers import softmin_tolerance_prec
+    if prec in (2, 3) and 3 * K + 6 > 192:
+        pytest.skip("split modes take K <= 62")
+    A, B, sA, sB, h, logw = make_inputs(n, m, K, seed=n + 7 * m + K)
+    out = gw.gw_sinkhorn_softmin(f32(A), f32(B), f32(sA), f32(sB), f32(h), f32(logw), eps, prec=prec)
+    ref = oracle_softmin(A, B, sA, sB, h, logw, eps)
+    tol = softmin_tolerance_prec(A, B, sA, sB, h, logw, eps, prec)
+    err = np.abs(host(out) - ref)
+    assert np.all(err <= tol), (prec, err.max(), tol[np.argmax(err - tol)], np.argmax(err - tol))
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_tensor_core_small_eps_and_zero_weights(gw, prec):
+    from helpers import softmin_tolerance_prec
+    A, B, sA, sB, h, logw = make_inputs(777, 1500, 32, seed=11, scale=1.0 / math.sqrt(32),
+                                        zero_cols=100)
+    eps = 1e-3
+    out = gw.gw_sinkhorn_softmin(f32(A), f32(B), f32(sA), f32(sB), f32(h), f32(logw), eps, prec=prec)
+    ref = oracle_softmin(A, B, sA, sB, h, logw, eps)
+    assert np.all(np.abs(host(out) - ref) <= softmin_tolerance_prec(A, B, sA, sB, h, logw, eps, prec))
+
+
+def test_tensor_core_average_alias_and_determinism(gw):
+    A, B, sA, sB, h, logw = make_inputs(3000, 2500, 16, seed=21)
+    args = [f32(v) for v in (A, B, sA, sB, h, logw)]
+    o1 = gw.gw_sinkhorn_softmin(*args, 0.07, prec=3)
+    o2 = gw.gw_sinkhorn_softmin(*args, 0.07, prec=3)
+    assert bool((o1 == o2).all())
+    prev = o1.clone()
+    gw.gw_sinkhorn_softmin(*args, 0.07, prec=3, avg_with=prev, out=prev)
+    assert bool((prev == o1).all())   # (x + x) / 2 == x exactly

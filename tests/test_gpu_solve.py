@@ -115,3 +115,18 @@ def test_annealed_schedule_and_lifted_dims(gw):
     for k, h in enumerate(res["history"]):
         assert abs(hist[k, gw.EN["eps"]] - h["eps"]) <= 1e-7 * h["eps"]
         assert abs(hist[k, gw.EN["E"]] - h["E"]) <= 1e-4 * abs(h["E"]), k
+
+
+@pytest.mark.parametrize("prec", [3, 2])
+def test_config1_end_to_end_tensor_core(gw, cfg1_oracle, prec):
+    """The split tensor-core modes reach the FP32 bar on the 2D workload."""
+    P, res = cfg1_oracle
+    out = gw.gw_solve(f32(P["X"]), f32(P["Y"]), f32(P["s"]), f32(P["t"]), f32(P["a"]), f32(P["b"]),
+                      P["eps"], 20, 50, prec=prec)
+    en = host(out["energy"])
+    last = res["history"][-1]
+    assert en[gw.EN["status"]] == 0
+    assert abs(en[gw.EN["E"]] - last["E"]) <= 1e-4 * abs(last["E"])
+    row, col = gpu_marginals(gw, P, out)
+    assert np.max(np.abs(row - last["row"]) / P["a"]) <= 1e-3
+    assert np.max(np.abs(col - last["col"]) / P["b"]) <= 1e-3
