@@ -33,8 +33,8 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "Sinkhorn cells/s (N*M*iters/s)"
-PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2}
-DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}
+PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2, "f16x3": 3}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "f16x3": "f16x3"}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")

@@ -251,6 +251,7 @@ size_t gw_workspace_size(int op, int64_t n, int64_t m, int D, int E, int prec) {
     case GW_OP_CROSS_COV: return cross_cov_ws_bytes(n, m, D, E, prec) + 256;
     case GW_OP_ENERGY: return energy_ws_bytes(n, m, D, E, prec) + 256;
     case GW_OP_SOLVE: return solve_ws_bytes(n, m, D, E, prec);
+    case GW_OP_LIFT: return lift_ws_bytes(n, D) + 256;   /* (n points, D features) */
     default: return 0;
   }
 }
@@ -404,10 +405,21 @@ int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, s
 int gw_lift(const float* x, int64_t n, int d, const float* w, int kind, float param, int D,
             int n_iter, uint64_t seed, float* X, float* sqn, float* basis_opt,
             float* eigvals_opt, void* ws, size_t ws_bytes, gw_stream_t stream) {
-  (void)x; (void)n; (void)d; (void)w; (void)kind; (void)param; (void)D; (void)n_iter; (void)seed;
-  (void)X; (void)sqn; (void)basis_opt; (void)eigvals_opt; (void)ws; (void)ws_bytes; (void)stream;
-  gw::set_error("gw_lift is not available in this build");
-  return GW_EUNSUPPORTED;
+  gw::set_error("");
+  NONNULL(x);
+  NONNULL(X);
+  NONNULL(sqn);
+  GW_REQUIRE(n >= 2, GW_EINVAL, "gw_lift needs n >= 2 points (got %lld)", static_cast<long long>(n));
+  GW_REQUIRE(d >= 1 && d <= 4, GW_EUNSUPPORTED, "gw_lift takes points of dimension 1..4 (got %d)", d);
+  GW_REQUIRE(D >= 1 && D <= GW_MAX_FEATURES, GW_EUNSUPPORTED, "D must be in [1, %d]", GW_MAX_FEATURES);
+  GW_REQUIRE(kind == GW_PEN_SQEUCLID || kind == GW_PEN_POWER || kind == GW_PEN_GAUSS, GW_EINVAL,
+             "unknown penalty %d", kind);
+  GW_REQUIRE(kind != GW_PEN_POWER || (param > 0.0f && param <= 2.0f), GW_EINVAL,
+             "power penalty needs 0 < p <= 2 (got %g)", static_cast<double>(param));
+  GW_REQUIRE(kind != GW_PEN_GAUSS || param > 0.0f, GW_EINVAL, "gaussian penalty needs sigma > 0");
+  GW_REQUIRE(n_iter >= 0 && n_iter <= 10000, GW_EINVAL, "n_iter out of range");
+  return run_lift(x, n, d, w, kind, param, D, n_iter, seed, X, sqn, basis_opt, eigvals_opt, ws,
+                  ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double* Gamma_t,

@@ -180,6 +180,12 @@ size_t energy_ws_bytes(int64_t n, int64_t m, int D, int E, int prec);
 int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* logb_pre,
                double* energy, double* Gamma_out, Carver& ws, cudaStream_t st);
 
+// Kernel PCA / centering lift (gw_lift.cu); synchronous.
+size_t lift_ws_bytes(int64_t n, int D);
+int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float param, int D,
+             int n_iter, uint64_t seed, float* X, float* sqn, float* basis, float* eigvals,
+             void* ws, size_t ws_bytes, cudaStream_t st);
+
 // logw_i = log(w_i)
 int launch_log(const float* w, int64_t n, float* logw, cudaStream_t st);
 

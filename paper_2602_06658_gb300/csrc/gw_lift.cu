@@ -1,0 +1,536 @@
+// Embeddings feeding Algorithm 1 (Section 5 "CNT Embeddings"; Appendix B.2).
+//
+// Squared-Euclidean cost: X = x - sum_i w_i x_i.
+// Other CNT costs: Kernel PCA of the kernel of Prop. 2.3 centered as in
+// Algorithm 4.  With u_i = c(x_i, x_1), the kernel is K = (u 1^T + 1 u^T - C)/2
+// and the weighted double centering (I - 1 w^T) . (I - w 1^T) removes the
+// rank-one u terms, so
+//     K~ = -1/2 (I - 1 w^T) C (I - w 1^T).
+// Its D largest eigenpairs come from block subspace iteration: Q <- K~ Q
+// (matrix-free: C is never stored, each product is one N x N tiled pass),
+// re-orthonormalised by Cholesky QR, and a final Rayleigh-Ritz step.  The
+// small r x r Cholesky and eigen-problems run on the host in float64 (cyclic
+// Jacobi); every N-sized step runs in the kernels below.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gw_internal.cuh"
+
+namespace gw {
+
+namespace {
+
+constexpr int kLiftThreads = 128;
+constexpr int kLiftTile = 32;   // source points staged per shared-memory tile
+constexpr int kGramBlocks = 148;
+
+struct CostParams {
+  int kind;
+  float param;
+};
+
+__device__ __forceinline__ float cnt_cost(float d2, CostParams cp) {
+  if (cp.kind == GW_PEN_SQEUCLID) return d2;
+  if (cp.kind == GW_PEN_POWER) {
+    if (cp.param == 1.0f) return sqrtf(d2);
+    if (cp.param == 2.0f) return d2;
+    return d2 > 0.0f ? exp2f(0.5f * cp.param * log2f(d2)) : 0.0f;
+  }
+  // GW_PEN_GAUSS: 2 (1 - exp(-d2 / (2 sigma^2)))
+  return 2.0f * (1.0f - expf(-d2 / (2.0f * cp.param * cp.param)));
+}
+
+// Zp[split][i][:] = sum_{k in split} C(x_i, x_k) P_k   (rows of P padded to RP)
+template <int RP>
+__global__ void __launch_bounds__(kLiftThreads)
+    cost_matvec_kernel(const float* x, int64_t n, int d, const float* P, CostParams cp,
+                       int64_t cols_per_split, float* Zp) {
+  __shared__ __align__(16) float Ps[kLiftTile][RP];
+  __shared__ float xs[kLiftTile][4];
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kLiftThreads + threadIdx.x;
+  const bool ok = i < n;
+  float xi[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int c = 0; c < d && c < 4; ++c) xi[c] = ok ? x[i * d + c] : 0.f;
+  float z[RP];
+#pragma unroll
+  for (int r = 0; r < RP; ++r) z[r] = 0.f;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * cols_per_split;
+  const int64_t k1 = k0 + cols_per_split < n ? k0 + cols_per_split : n;
+  for (int64_t kb = k0; kb < k1; kb += kLiftTile) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kLiftTile * RP; idx += kLiftThreads) {
+      const int kk = idx / RP, r = idx % RP;
+      const int64_t k = kb + kk;
+      Ps[kk][r] = k < k1 ? P[k * RP + r] : 0.f;
+    }
+    if (threadIdx.x < kLiftTile) {
+      const int64_t k = kb + threadIdx.x;
+      for (int c = 0; c < 4; ++c) xs[threadIdx.x][c] = (k < k1 && c < d) ? x[k * d + c] : 0.f;
+    }
+    __syncthreads();
+    const int cnt = static_cast<int>(k1 - kb < kLiftTile ? k1 - kb : kLiftTile);
+    for (int kk = 0; kk < cnt; ++kk) {
+      float d2 = 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float df = xi[c] - xs[kk][c];
+        d2 = fmaf(df, df, d2);
+      }
+      const float cv = cnt_cost(d2, cp);
+      const float4* pr = reinterpret_cast<const float4*>(&Ps[kk][0]);
+#pragma unroll
+      for (int r4 = 0; r4 < RP / 4; ++r4) {
+        const float4 pv = pr[r4];
+        z[4 * r4 + 0] = fmaf(cv, pv.x, z[4 * r4 + 0]);
+        z[4 * r4 + 1] = fmaf(cv, pv.y, z[4 * r4 + 1]);
+        z[4 * r4 + 2] = fmaf(cv, pv.z, z[4 * r4 + 2]);
+        z[4 * r4 + 3] = fmaf(cv, pv.w, z[4 * r4 + 3]);
+      }
+    }
+  }
+  if (!ok) return;
+  float* out = Zp + (static_cast<int64_t>(blockIdx.y) * n + i) * RP;
+#pragma unroll
+  for (int r = 0; r < RP; ++r) out[r] = z[r];
+}
+
+// Column sums weighted by w (or plain) of an n x RP matrix: partials per block.
+__global__ void colsum_partial_kernel(const float* Q, const float* w, double wu, int64_t n,
+                                      int RP, double* part) {
+  // blockDim.x == RP (<= 128); rows strided over blocks; weight w_i, or wu
+  const int r = threadIdx.x;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double wi = w ? static_cast<double>(w[i]) : wu;
+    acc += wi * static_cast<double>(Q[i * RP + r]);
+  }
+  part[static_cast<int64_t>(blockIdx.x) * RP + r] = acc;
+}
+
+__global__ void colsum_final_kernel(const double* part, int blocks, int RP, double* out) {
+  const int r = threadIdx.x;
+  if (r >= RP) return;
+  double acc = 0.0;
+  for (int b = 0; b < blocks; ++b) acc += part[static_cast<int64_t>(b) * RP + r];
+  out[r] = acc;
+}
+
+// P = Q - w (1^T Q)
+__global__ void center_right_kernel(const float* Q, const float* w, float wu, const double* cs,
+                                    int64_t n, int RP, float* P) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= n * RP) return;
+  const int64_t i = q / RP;
+  const int r = static_cast<int>(q % RP);
+  const float wi = w ? w[i] : wu;
+  P[q] = Q[q] - wi * static_cast<float>(cs[r]);
+}
+
+// Z = -1/2 (Zraw - 1 (w^T Zraw)), Zraw = sum over splits of Zp
+__global__ void reduce_splits_f32_kernel(const float* Zp, int splits, int64_t count, float* Z) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  float acc = 0.f;
+  for (int s = 0; s < splits; ++s) acc += Zp[s * count + q];
+  Z[q] = acc;
+}
+
+__global__ void center_left_kernel(float* Z, const double* wz, int64_t n, int RP) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= n * RP) return;
+  const int r = static_cast<int>(q % RP);
+  Z[q] = -0.5f * (Z[q] - static_cast<float>(wz[r]));
+}
+
+// Gram partials: part[b][r1][r2] = sum_{i in block b} U_i[r1] Z_i[r2]
+__global__ void gram_partial_kernel(const float* U, const float* Z, int64_t n, int RP,
+                                    double* part) {
+  extern __shared__ float sh[];
+  float* Us = sh;               // [32][RP]
+  float* Zs = sh + 32 * RP;     // [32][RP]
+  const int RR = RP * RP;
+  const int per = (RR + blockDim.x - 1) / blockDim.x;
+  double acc[64];
+  for (int q = 0; q < per; ++q) acc[q] = 0.0;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk;
+  const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
+  for (int64_t ib = i0; ib < i1; ib += 32) {
+    __syncthreads();
+    const int cnt = static_cast<int>(i1 - ib < 32 ? i1 - ib : 32);
+    for (int idx = threadIdx.x; idx < cnt * RP; idx += blockDim.x) {
+      Us[idx] = U[ib * RP + idx];
+      Zs[idx] = Z[ib * RP + idx];
+    }
+    __syncthreads();
+    for (int q = 0; q < per; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e >= RR) break;
+      const int r1 = e / RP, r2 = e % RP;
+      double a = 0.0;
+      for (int ii = 0; ii < cnt; ++ii)
+        a = fma(static_cast<double>(Us[ii * RP + r1]), static_cast<double>(Zs[ii * RP + r2]), a);
+      acc[q] += a;
+    }
+  }
+  for (int q = 0; q < per; ++q) {
+    const int e = threadIdx.x + q * blockDim.x;
+    if (e < RR) part[static_cast<int64_t>(blockIdx.x) * RR + e] = acc[q];
+  }
+}
+
+__global__ void gram_final_kernel(const double* part, int blocks, int RR, double* G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= RR) return;
+  double a = 0.0;
+  for (int b = 0; b < blocks; ++b) a += part[static_cast<int64_t>(b) * RR + e];
+  G[e] = a;
+}
+
+// Out_i[c] = sum_r In_i[r] M[r][c]  (M: RP x cols, float64), cols <= RP
+__global__ void right_mult_kernel(const float* In, int64_t n, int RP, const double* M, int cols,
+                                  int out_stride, float* Out) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= n * cols) return;
+  const int64_t i = q / cols;
+  const int c = static_cast<int>(q % cols);
+  double a = 0.0;
+  for (int r = 0; r < RP; ++r) a = fma(static_cast<double>(In[i * RP + r]), M[r * cols + c], a);
+  Out[i * out_stride + c] = static_cast<float>(a);
+}
+
+// Deterministic start block: uniform(-1, 1) from a counter hash (splitmix64).
+__global__ void random_block_kernel(float* Q, int64_t count, uint64_t seed) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * static_cast<uint64_t>(q + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  Q[q] = static_cast<float>(static_cast<double>(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+}
+
+// Sign convention: the entry of largest magnitude of each eigenvector is positive.
+__global__ void sign_fix_kernel(float* V, int64_t n, int D, float* X, float* sqn,
+                                const float* sqrt_lam) {
+  // one block; thread c handles column c (D <= 128)
+  __shared__ int flip[128];
+  for (int c = threadIdx.x; c < D; c += blockDim.x) {
+    float best = 0.f;
+    float val = 0.f;
+    for (int64_t i = 0; i < n; ++i) {
+      const float v = V[i * D + c];
+      if (fabsf(v) > best) {
+        best = fabsf(v);
+        val = v;
+      }
+    }
+    flip[c] = val < 0.f;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < D; ++c) {
+      float v = V[i * D + c];
+      if (flip[c]) v = -v;
+      V[i * D + c] = v;
+      const float xv = v * sqrt_lam[c];
+      X[i * D + c] = xv;
+      s = fmaf(xv, xv, s);
+    }
+    sqn[i] = s;
+  }
+}
+
+// Squared lift: X = x - sum w x; sqn = ||X||^2 (one block, d <= 128)
+__global__ void center_points_kernel(const float* x, const float* w, int64_t n, int d, float* X,
+                                     float* sqn) {
+  __shared__ double mean[128];
+  __shared__ double red[256];
+  for (int c = 0; c < d; ++c) {
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+      a += (w ? static_cast<double>(w[i]) : 1.0 / static_cast<double>(n)) * x[i * d + c];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int t = 0; t < static_cast<int>(blockDim.x); ++t) s += red[t];
+      mean[c] = s;
+    }
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < d; ++c) {
+      const float v = static_cast<float>(static_cast<double>(x[i * d + c]) - mean[c]);
+      X[i * d + c] = v;
+      s = fmaf(v, v, s);
+    }
+    sqn[i] = s;
+  }
+}
+
+int rpad(int D) {
+  const int want = D + 8;
+  const int opts[] = {16, 32, 48, 64, 80, 96, 128};
+  for (int o : opts)
+    if (o >= want) return o;
+  return 128;
+}
+
+int lift_splits(int64_t n) {
+  const int rb = ceil_div(n, kLiftThreads);
+  int s = ceil_div(4 * kSmCount, rb);
+  const int smax = ceil_div(n, 256);
+  if (s > smax) s = smax;
+  return s < 1 ? 1 : s;
+}
+
+// ---- host-side small dense linear algebra (float64) ----
+// Cholesky G = R^T R (upper R); returns false if G is not positive definite.
+bool cholesky_upper(std::vector<double>& G, int r) {
+  for (int j = 0; j < r; ++j) {
+    double s = G[j * r + j];
+    for (int k = 0; k < j; ++k) s -= G[k * r + j] * G[k * r + j];
+    if (!(s > 0.0)) return false;
+    const double d = sqrt(s);
+    G[j * r + j] = d;
+    for (int i = j + 1; i < r; ++i) {
+      double t = G[j * r + i];
+      for (int k = 0; k < j; ++k) t -= G[k * r + j] * G[k * r + i];
+      G[j * r + i] = t / d;
+    }
+    for (int i = 0; i < j; ++i) G[j * r + i] = 0.0;
+  }
+  return true;
+}
+
+// inverse of an upper-triangular matrix
+std::vector<double> inv_upper(const std::vector<double>& R, int r) {
+  std::vector<double> W(static_cast<size_t>(r) * r, 0.0);
+  for (int j = 0; j < r; ++j) {
+    W[j * r + j] = 1.0 / R[j * r + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s += R[i * r + k] * W[k * r + j];
+      W[i * r + j] = -s / R[i * r + i];
+    }
+  }
+  return W;
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric r x r matrix A (row-major).
+// On return A's diagonal holds the eigenvalues and U's columns the vectors.
+void jacobi_eig(std::vector<double>& A, std::vector<double>& U, int r) {
+  U.assign(static_cast<size_t>(r) * r, 0.0);
+  for (int i = 0; i < r; ++i) U[i * r + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < r; ++j) {
+        tot += A[i * r + j] * A[i * r + j];
+        if (i != j) off += A[i * r + j] * A[i * r + j];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < r - 1; ++p)
+      for (int q = p + 1; q < r; ++q) {
+        const double apq = A[p * r + q];
+        if (fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * r + q] - A[p * r + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < r; ++k) {
+          const double akp = A[k * r + p], akq = A[k * r + q];
+          A[k * r + p] = c * akp - s * akq;
+          A[k * r + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < r; ++k) {
+          const double apk = A[p * r + k], aqk = A[q * r + k];
+          A[p * r + k] = c * apk - s * aqk;
+          A[q * r + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < r; ++k) {
+          const double ukp = U[k * r + p], ukq = U[k * r + q];
+          U[k * r + p] = c * ukp - s * ukq;
+          U[k * r + q] = s * ukp + c * ukq;
+        }
+      }
+  }
+}
+
+struct LiftBufs {
+  float *Q, *P, *Z, *Zp, *V, *sl;
+  double *cs_part, *cs, *g_part, *G, *M;
+  int splits, RP;
+};
+
+LiftBufs carve_lift(Carver& c, int64_t n, int D) {
+  LiftBufs B;
+  B.RP = rpad(D);
+  B.splits = lift_splits(n);
+  const size_t nr = static_cast<size_t>(n) * B.RP;
+  B.Q = c.take<float>(nr);
+  B.P = c.take<float>(nr);
+  B.Z = c.take<float>(nr);
+  B.Zp = B.splits > 1 ? c.take<float>(nr * B.splits) : nullptr;
+  B.V = c.take<float>(static_cast<size_t>(n) * D);
+  B.sl = c.take<float>(static_cast<size_t>(D));
+  B.cs_part = c.take<double>(static_cast<size_t>(kGramBlocks) * B.RP);
+  B.cs = c.take<double>(B.RP);
+  B.g_part = c.take<double>(static_cast<size_t>(kGramBlocks) * B.RP * B.RP);
+  B.G = c.take<double>(static_cast<size_t>(B.RP) * B.RP);
+  B.M = c.take<double>(static_cast<size_t>(B.RP) * B.RP);
+  return B;
+}
+
+int weighted_colsum(const float* Q, const float* w, double wu, int64_t n, int RP, LiftBufs& B,
+                    cudaStream_t st) {
+  colsum_partial_kernel<<<kGramBlocks, RP, 0, st>>>(Q, w, wu, n, RP, B.cs_part);
+  GW_LAUNCH_CHECK();
+  colsum_final_kernel<<<1, 128, 0, st>>>(B.cs_part, kGramBlocks, RP, B.cs);
+  GW_LAUNCH_CHECK();
+  return GW_OK;
+}
+
+// Z = K~ Q = -1/2 (I - 1 w^T) C (I - w 1^T) Q
+int apply_kernel(const float* x, int64_t n, int d, const float* w, CostParams cp, LiftBufs& B,
+                 cudaStream_t st) {
+  const int RP = B.RP;
+  const int64_t nr = n * RP;
+  const float wu = 1.0f / static_cast<float>(n);
+  GW_TRY(weighted_colsum(B.Q, nullptr, 1.0, n, RP, B, st));            // 1^T Q
+  center_right_kernel<<<ceil_div(nr, 256), 256, 0, st>>>(B.Q, w, wu, B.cs, n, RP, B.P);
+  GW_LAUNCH_CHECK();
+  const int64_t cps =
+      (static_cast<int64_t>(ceil_div(n, B.splits)) + kLiftTile - 1) / kLiftTile * kLiftTile;
+  const int splits = ceil_div(n, cps);
+  dim3 grid(ceil_div(n, kLiftThreads), splits);
+  float* dst = splits > 1 ? B.Zp : B.Z;
+  switch (RP) {
+    case 16: cost_matvec_kernel<16><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
+    case 32: cost_matvec_kernel<32><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
+    case 48: cost_matvec_kernel<48><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
+    case 64: cost_matvec_kernel<64><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
+    case 80: cost_matvec_kernel<80><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
+    case 96: cost_matvec_kernel<96><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
+    default: cost_matvec_kernel<128><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
+  }
+  GW_LAUNCH_CHECK();
+  if (splits > 1) {
+    reduce_splits_f32_kernel<<<ceil_div(nr, 256), 256, 0, st>>>(B.Zp, splits, nr, B.Z);
+    GW_LAUNCH_CHECK();
+  }
+  GW_TRY(weighted_colsum(B.Z, w, 1.0 / static_cast<double>(n), n, RP, B, st));   // w^T Z
+  center_left_kernel<<<ceil_div(nr, 256), 256, 0, st>>>(B.Z, B.cs, n, RP);
+  GW_LAUNCH_CHECK();
+  return GW_OK;
+}
+
+int gram(const float* U, const float* Z, int64_t n, int RP, LiftBufs& B, std::vector<double>& G,
+         cudaStream_t st) {
+  const size_t shb = sizeof(float) * 2 * 32 * RP;
+  gram_partial_kernel<<<kGramBlocks, 256, shb, st>>>(U, Z, n, RP, B.g_part);
+  GW_LAUNCH_CHECK();
+  gram_final_kernel<<<ceil_div(RP * RP, 256), 256, 0, st>>>(B.g_part, kGramBlocks, RP * RP, B.G);
+  GW_LAUNCH_CHECK();
+  G.resize(static_cast<size_t>(RP) * RP);
+  GW_CUDA_TRY(cudaMemcpyAsync(G.data(), B.G, sizeof(double) * RP * RP, cudaMemcpyDeviceToHost, st));
+  GW_CUDA_TRY(cudaStreamSynchronize(st));
+  return GW_OK;
+}
+
+// Q <- Z R^{-1} with Z^T Z = R^T R (Cholesky QR)
+int orthonormalize(int64_t n, LiftBufs& B, cudaStream_t st) {
+  const int RP = B.RP;
+  std::vector<double> G;
+  GW_TRY(gram(B.Z, B.Z, n, RP, B, G, st));
+  // tiny diagonal shift keeps the factorisation defined when a direction vanishes
+  double tr = 0.0;
+  for (int i = 0; i < RP; ++i) tr += G[i * RP + i];
+  GW_REQUIRE(tr > 0.0 && isfinite(tr), GW_ENONFINITE, "Kernel PCA: degenerate block (trace %g)", tr);
+  for (int i = 0; i < RP; ++i) G[i * RP + i] += 1e-13 * tr / RP;
+  GW_REQUIRE(cholesky_upper(G, RP), GW_ENONFINITE,
+             "Kernel PCA: Gram matrix is not positive definite");
+  std::vector<double> W = inv_upper(G, RP);
+  GW_CUDA_TRY(cudaMemcpyAsync(B.M, W.data(), sizeof(double) * RP * RP, cudaMemcpyHostToDevice, st));
+  right_mult_kernel<<<ceil_div(n * RP, 256), 256, 0, st>>>(B.Z, n, RP, B.M, RP, RP, B.Q);
+  GW_LAUNCH_CHECK();
+  GW_CUDA_TRY(cudaStreamSynchronize(st));   // W (host) must outlive the copy
+  return GW_OK;
+}
+
+}  // namespace
+
+size_t lift_ws_bytes(int64_t n, int D) {
+  Carver c(nullptr, ~size_t(0));
+  carve_lift(c, n, D);
+  return c.used();
+}
+
+int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float param, int D,
+             int n_iter, uint64_t seed, float* X, float* sqn, float* basis, float* eigvals,
+             void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (kind == GW_PEN_SQEUCLID && D == d && basis == nullptr && eigvals == nullptr) {
+    center_points_kernel<<<1, 256, 0, st>>>(x, w, n, d, X, sqn);
+    GW_LAUNCH_CHECK();
+    GW_CUDA_TRY(cudaStreamSynchronize(st));
+    return GW_OK;
+  }
+  Carver c(ws, ws_bytes);
+  LiftBufs B = carve_lift(c, n, D);
+  GW_TRY(check_ws(c, ws));
+  const int RP = B.RP;
+  GW_REQUIRE(n > RP, GW_EINVAL, "Kernel PCA with D=%d needs more than %d points (n=%lld)", D, RP,
+             static_cast<long long>(n));
+  CostParams cp{kind, param};
+  const int iters = n_iter > 0 ? n_iter : 40;
+  random_block_kernel<<<ceil_div(n * RP, 256), 256, 0, st>>>(B.Q, n * RP, seed);
+  GW_LAUNCH_CHECK();
+  for (int it = 0; it < iters; ++it) {
+    GW_TRY(apply_kernel(x, n, d, w, cp, B, st));
+    GW_TRY(orthonormalize(n, B, st));
+  }
+  // Rayleigh-Ritz: T = Q^T K~ Q, eigenpairs of T, V = Q U_{1:D}
+  GW_TRY(apply_kernel(x, n, d, w, cp, B, st));
+  std::vector<double> T;
+  GW_TRY(gram(B.Q, B.Z, n, RP, B, T, st));
+  for (int i = 0; i < RP; ++i)
+    for (int j = i + 1; j < RP; ++j) {
+      const double v = 0.5 * (T[i * RP + j] + T[j * RP + i]);
+      T[i * RP + j] = T[j * RP + i] = v;
+    }
+  std::vector<double> U;
+  jacobi_eig(T, U, RP);
+  std::vector<int> order(RP);
+  for (int i = 0; i < RP; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b) { return T[a * RP + a] > T[b * RP + b]; });
+  std::vector<double> Msel(static_cast<size_t>(RP) * D);
+  std::vector<float> lam(D), sl(D);
+  for (int c2 = 0; c2 < D; ++c2) {
+    const int k = order[c2];
+    lam[c2] = static_cast<float>(T[k * RP + k]);
+    sl[c2] = static_cast<float>(sqrt(std::max(0.0, T[k * RP + k])));
+    for (int r = 0; r < RP; ++r) Msel[r * D + c2] = U[r * RP + k];
+  }
+  GW_CUDA_TRY(cudaMemcpyAsync(B.M, Msel.data(), sizeof(double) * RP * D, cudaMemcpyHostToDevice, st));
+  GW_CUDA_TRY(cudaMemcpyAsync(B.sl, sl.data(), sizeof(float) * D, cudaMemcpyHostToDevice, st));
+  right_mult_kernel<<<ceil_div(n * D, 256), 256, 0, st>>>(B.Q, n, RP, B.M, D, D, B.V);
+  GW_LAUNCH_CHECK();
+  sign_fix_kernel<<<1, 256, 0, st>>>(B.V, n, D, X, sqn, B.sl);
+  GW_LAUNCH_CHECK();
+  if (basis) {
+    GW_CUDA_TRY(cudaMemcpyAsync(basis, B.V, sizeof(float) * n * D, cudaMemcpyDeviceToDevice, st));
+  }
+  if (eigvals) {
+    GW_CUDA_TRY(cudaMemcpyAsync(eigvals, lam.data(), sizeof(float) * D, cudaMemcpyHostToDevice, st));
+  }
+  GW_CUDA_TRY(cudaStreamSynchronize(st));
+  return GW_OK;
+}
+
+}  // namespace gw

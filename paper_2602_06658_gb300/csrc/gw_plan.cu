@@ -515,8 +515,7 @@ size_t cross_cov_ws_bytes(int64_t n, int64_t m, int D, int E, int prec) {
 // Enqueue everything up to the Gamma partials; the caller finalizes.
 static int cross_cov_stage(const PlanArgs& p, int prec, double* W_user, Carver& ws,
                            cudaStream_t st, CrossCovLayout* out) {
-  GW_REQUIRE(prec == GW_PREC_FP32 || prec == GW_PREC_BF16 || prec == GW_PREC_BF16X3,
-             GW_EUNSUPPORTED, "precision %d", prec);
+  GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_F16X3, GW_EUNSUPPORTED, "precision %d", prec);
   CrossCovLayout L = carve_cross_cov(ws, p.n, p.m, p.D, p.E, W_user == nullptr);
   GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for cross-covariance");
   if (W_user) L.W = W_user;
