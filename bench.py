@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=list(PREC))
+    ap.add_argument("--prec", default="f16x3", choices=list(PREC),
+                    help="cost-tile precision; f16x3 meets the FP32 accuracy bar")
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--D", type=int, default=32)
     ap.add_argument("--n-inner", type=int, default=100)
@@ -275,6 +276,10 @@ def run_gw(args, rank, world, local):
 
     # dominant kernel: the fused softmin, timed alone on the same stream
     rf = roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush)
+    if prec != 0:
+        rf32 = roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, 0, flush, reps=3)
+        rf["fp32_cells_per_s"] = rf32["cells_per_s"]
+        rf["speedup_vs_fp32"] = rf["cells_per_s"] / rf32["cells_per_s"]
     e2e = None if args.no_e2e else run_e2e(args, gw, torch, dev, X, Y, s, t, a, b, prec, ws)
     if world > 1:
         e2e_t, e2e_u = aggregate(e2e["seconds"], e2e["cells"], world, dev) if e2e else (None, None)

@@ -203,6 +203,41 @@ __device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
+// Fold 32 base-2 exponents into the running (max, sum of exp2): a 3-input
+// max tree, a branch-free rescale (exp2(0) = 1 when the max did not move),
+// and the shift and the sum as packed FP32x2 adds.
+__device__ __forceinline__ void lse_chunk(const uint32_t (&r)[32], float& mrun, float& srun) {
+  float v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+  float a[11];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) a[k] = tc::max3(v[3 * k], v[3 * k + 1], v[3 * k + 2]);
+  a[10] = fmaxf(v[30], v[31]);
+  const float b0 = tc::max3(a[0], a[1], a[2]);
+  const float b1 = tc::max3(a[3], a[4], a[5]);
+  const float b2 = tc::max3(a[6], a[7], a[8]);
+  const float b3 = tc::max3(a[9], a[10], mrun);
+  const float mnew = fmaxf(tc::max3(b0, b1, b2), b3);
+  srun *= ex2(mrun - mnew);
+  mrun = mnew;
+  const uint64_t neg = tc::pack2(-mnew, -mnew);
+  uint64_t acc0 = tc::pack2(0.f, 0.f), acc1 = acc0;
+#pragma unroll
+  for (int k = 0; k < 32; k += 4) {
+    float d0, d1, d2, d3;
+    tc::unpack2(tc::add2(tc::pack2(v[k], v[k + 1]), neg), d0, d1);
+    tc::unpack2(tc::add2(tc::pack2(v[k + 2], v[k + 3]), neg), d2, d3);
+    acc0 = tc::add2(acc0, tc::pack2(ex2(d0), ex2(d1)));
+    acc1 = tc::add2(acc1, tc::pack2(ex2(d2), ex2(d3)));
+  }
+  float s0, s1, s2, s3;
+  tc::unpack2(tc::add2(acc0, acc1), s0, s1);
+  (void)s2;
+  (void)s3;
+  srun += s0 + s1;
+}
+
 template <int KP, int S, bool BF16>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     softmin_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mB0,
@@ -338,25 +373,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       }
       tc::tc_fence_after();
       const uint32_t tcol = tbase + (static_cast<uint32_t>(q * 32) << 16) + (b * 2 + h) * 128;
-#pragma unroll 1
-      for (int c = 0; c < kBN / 32; ++c) {
-        float v[32];
-        tc::tmem_ld32(tcol + c * 32, v);
-        float cm = v[0];
-#pragma unroll
-        for (int k = 1; k < 32; ++k) cm = fmaxf(cm, v[k]);
-        if (cm > mrun) {
-          srun *= ex2(mrun - cm);
-          mrun = cm;
-        }
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 32; k += 2) {
-          s0 += ex2(v[k] - mrun);
-          s1 += ex2(v[k + 1] - mrun);
-        }
-        srun += s0 + s1;
-      }
+      // four chunks of 32 columns, the next chunk's TMEM load in flight
+      // while the current one is reduced
+      uint32_t ra[32], rb[32];
+      tc::tmem_ld32_issue(tcol, ra);
+      tc::tmem_ld_wait(ra);
+      tc::tmem_ld32_issue(tcol + 32, rb);
+      lse_chunk(ra, mrun, srun);
+      tc::tmem_ld_wait(rb);
+      tc::tmem_ld32_issue(tcol + 64, ra);
+      lse_chunk(rb, mrun, srun);
+      tc::tmem_ld_wait(ra);
+      tc::tmem_ld32_issue(tcol + 96, rb);
+      lse_chunk(ra, mrun, srun);
+      tc::tmem_ld_wait(rb);
+      lse_chunk(rb, mrun, srun);
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
