@@ -203,25 +203,10 @@ __device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
-// Fold 32 base-2 exponents into the running (max, sum of exp2): a 3-input
-// max tree, a branch-free rescale (exp2(0) = 1 when the max did not move),
-// and the shift and the sum as packed FP32x2 adds.
-__device__ __forceinline__ void lse_chunk(const uint32_t (&r)[32], float& mrun, float& srun) {
-  float v[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
-  float a[11];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) a[k] = tc::max3(v[3 * k], v[3 * k + 1], v[3 * k + 2]);
-  a[10] = fmaxf(v[30], v[31]);
-  const float b0 = tc::max3(a[0], a[1], a[2]);
-  const float b1 = tc::max3(a[3], a[4], a[5]);
-  const float b2 = tc::max3(a[6], a[7], a[8]);
-  const float b3 = tc::max3(a[9], a[10], mrun);
-  const float mnew = fmaxf(tc::max3(b0, b1, b2), b3);
-  srun *= ex2(mrun - mnew);
-  mrun = mnew;
-  const uint64_t neg = tc::pack2(-mnew, -mnew);
+// Sum of exp2(v_k - shift) over 32 values, with the shift and the sum as
+// packed FP32x2 adds.
+__device__ __forceinline__ float exp2_sum32(const float (&v)[32], float shift) {
+  const uint64_t neg = tc::pack2(-shift, -shift);
   uint64_t acc0 = tc::pack2(0.f, 0.f), acc1 = acc0;
 #pragma unroll
   for (int k = 0; k < 32; k += 4) {
@@ -231,11 +216,38 @@ __device__ __forceinline__ void lse_chunk(const uint32_t (&r)[32], float& mrun, 
     acc0 = tc::add2(acc0, tc::pack2(ex2(d0), ex2(d1)));
     acc1 = tc::add2(acc1, tc::pack2(ex2(d2), ex2(d3)));
   }
-  float s0, s1, s2, s3;
+  float s0, s1;
   tc::unpack2(tc::add2(acc0, acc1), s0, s1);
-  (void)s2;
-  (void)s3;
-  srun += s0 + s1;
+  return s0 + s1;
+}
+
+// Fold 32 base-2 exponents into the running (shift, sum): lse = shift +
+// log2(sum) holds for any shift, so the common path exponentiates against
+// the current shift with no max in the dependency chain.  Only when a value
+// lies more than ~43 above the shift (the partial sum reaches 2^48, or is
+// inf/NaN after an overflow) is the chunk redone against its own maximum,
+// which then becomes the shift.  The shift only ever takes values of real
+// exponents, so nothing that matters underflows.
+__device__ __forceinline__ void lse_chunk(const uint32_t (&r)[32], float& shift, float& sum) {
+  float v[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+  float acc = exp2_sum32(v, shift);
+  if (!(acc < 281474976710656.0f)) {   // 2^48
+    float a[11];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) a[k] = tc::max3(v[3 * k], v[3 * k + 1], v[3 * k + 2]);
+    a[10] = fmaxf(v[30], v[31]);
+    const float b0 = tc::max3(a[0], a[1], a[2]);
+    const float b1 = tc::max3(a[3], a[4], a[5]);
+    const float b2 = tc::max3(a[6], a[7], a[8]);
+    const float b3 = tc::max3(a[9], a[10], shift);
+    const float mnew = fmaxf(tc::max3(b0, b1, b2), b3);
+    sum *= ex2(shift - mnew);
+    shift = mnew;
+    acc = exp2_sum32(v, shift);
+  }
+  sum += acc;
 }
 
 template <int KP, int S, bool BF16>
