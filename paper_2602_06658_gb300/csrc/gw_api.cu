@@ -150,6 +150,8 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
       row.sB = p.t;
       row.h = B.g[gc];
       row.logw = B.logb;
+      row.est = B.f[fc];      // the row log-sum-exp is close to -f / eps
+
       row.n = p.n;
       row.m = p.m;
       row.K = p.D;
@@ -159,6 +161,7 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
       col.sA = p.t;
       col.sB = p.s;
       col.logw = B.loga;
+      col.est = B.g[gc];
       col.n = p.m;
       col.m = p.n;
       col.K = p.D;
@@ -281,6 +284,7 @@ int gw_sinkhorn_softmin(const float* A, const float* B, const float* sA, const f
   T.h = h;
   T.logw = logw;
   T.avg_with = avg_with;
+  T.est = avg_with;   // the previous potential doubles as the shift estimate
   T.out = out;
   T.n = n;
   T.m = m;

@@ -113,6 +113,7 @@ struct SoftminTask {
   const float* h;
   const float* logw;
   const float* avg_with;
+  const float* est; // previous potential of the output side (shift estimate) or null
   float* out;
   float* pm;        // partial maxima  [splits][n] (base 2), used when splits > 1
   float* ps;        // partial sums    [splits][n]

@@ -82,6 +82,7 @@ extern "C" int gw_sinkhorn_softmin_noalloc(const float* A, const float* B, const
   T.h = h;
   T.logw = logw;
   T.avg_with = avg_with;
+  T.est = nullptr;
   T.out = out;
   T.n = n;
   T.m = m;

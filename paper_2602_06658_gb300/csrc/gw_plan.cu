@@ -644,6 +644,7 @@ int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* lo
   T.h = p.g;
   T.logw = logb_pre ? logb_pre : logb;
   T.avg_with = nullptr;
+  T.est = p.f;   // at convergence S_b(g) is close to f
   T.out = fhat;
   T.n = p.n;
   T.m = p.m;

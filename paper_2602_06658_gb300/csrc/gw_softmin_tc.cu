@@ -14,8 +14,15 @@
 //                              two-way split product;
 //   3 columns                  the column bias w_j = (h_j/eps + logw_j) log2(e),
 //                              a three-way split times a power-of-two constant;
+//   3 columns                  minus a per-row shift estimate e_i (three-way split),
+//                              when an estimate is given;
 //   zero padding to KP (a multiple of 64).
-// So the epilogue only keeps a running (max, sum of exp2) per row.
+// With an estimate (the previous potential of the output side, which the
+// row's log-sum-exp equals at convergence) the epilogue only sums exp2 of
+// what the MMA wrote: no subtraction, no max.  A row whose sum over- or
+// underflows marks its CTA, and a second launch recomputes exactly those
+// CTAs with the safe epilogue (running shift, a chunk redone against its
+// own maximum when a value jumps above the shift).
 //
 // CTA layout (one CTA per SM): 256 rows as two M = 128 accumulators, column
 // tiles of BN = 128 streamed by TMA through a ring of S stages (128-byte
@@ -52,7 +59,9 @@ struct TcOperandShape {
   int mult;     // 1 or 3 products in the dot
   int KP;       // padded operand width
   int col_u;    // first rank-one column
-  int col_w;    // first bias column
+  int col_w;    // first column-bias column
+  int col_e;    // first row-estimate column
+  int used;     // non-zero columns
 };
 
 TcOperandShape tc_shape(int K, int prec) {
@@ -61,8 +70,9 @@ TcOperandShape tc_shape(int K, int prec) {
   s.mult = prec == GW_PREC_BF16 ? 1 : 3;
   s.col_u = s.mult * K;
   s.col_w = s.col_u + 3;
-  const int need = s.col_w + 3;
-  s.KP = ((need + 63) / 64) * 64;
+  s.col_e = s.col_w + 3;
+  s.used = s.col_e + 3;
+  s.KP = ((s.used + 63) / 64) * 64;
   return s;
 }
 
@@ -82,6 +92,15 @@ __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) {
 }
 __device__ __forceinline__ float from16(__half x) { return __half2float(x); }
 __device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Part `part` (0, 1, 2) of a three-way 16-bit split of x (hi + mid + lo).
+template <class T>
+__device__ __forceinline__ float split3(float x, int part) {
+  const float x0 = from16(to16<T>(x));
+  const float r1 = x - x0;
+  const float x1 = from16(to16<T>(r1));
+  return part == 0 ? x0 : (part == 1 ? x1 : r1 - x1);
+}
 
 // max |x| of four arrays -> mx[0..3] (non-negative floats compare as ints)
 __global__ void tc_absmax_kernel(const float* A, int64_t nA, const float* B, int64_t nB,
@@ -119,8 +138,9 @@ __device__ __forceinline__ void balance(float prod, float mxa, float mxb, float*
 // and for the B side a bias of -65504 * kBiasConst so they add nothing.
 template <class T>
 __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, const float* logw,
-                               int64_t rows_valid, int64_t rows_pad, TcOperandShape shp, int role,
-                               float alpha, float beta, float inv_eps, const unsigned* mx, T* op) {
+                               const float* est, int64_t rows_valid, int64_t rows_pad,
+                               TcOperandShape shp, int role, float alpha, float beta,
+                               float inv_eps, const unsigned* mx, T* op) {
   const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
   if (r >= rows_pad) return;
   const float mA = __uint_as_float(mx[0]), mB = __uint_as_float(mx[1]);
@@ -149,18 +169,21 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
         const float hi = from16(to16<T>(x));
         if (role == 0) v = part < 2 ? hi : x - hi;   // [hi, hi, lo]
         else v = part == 1 ? x - hi : hi;            // [hi, lo, hi]
-      } else if (k < shp.col_w + 3) {
+      } else if (k < shp.col_e) {
         if (role == 0) {
           v = kBiasConst;
         } else {
           float w = (h[r] * inv_eps + logw[r]) * kLog2e / kBiasConst;
           w = fmaxf(w, -kHalfMax);             // zero weights: effectively -inf
-          const float w0 = from16(to16<T>(w));
-          const float r1 = w - w0;
-          const float w1 = from16(to16<T>(r1));
-          const float w2 = r1 - w1;
-          const int part = k - shp.col_w;
-          v = part == 0 ? w0 : (part == 1 ? w1 : w2);
+          v = split3<T>(w, k - shp.col_w);
+        }
+      } else if (k < shp.used) {
+        if (role == 1) {
+          v = kBiasConst;
+        } else if (est) {
+          // shift estimate e_i = -est_i log2(e) / eps; the columns hold -e_i / c
+          const float e = est[r] * inv_eps * kLog2e / kBiasConst;
+          v = split3<T>(e, k - shp.col_e);
         }
       }
     } else if (role == 1 && k == shp.col_w) {
@@ -172,6 +195,9 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
 
 struct TcTask {
   int64_t n, m;           // real rows / columns
+  int ksteps;             // MMA K-steps of 16 that hold non-zero operand columns
+  const float* est;       // per-row shift estimate (fast pass), or null
+  int* flags;             // per-CTA "recompute" flags shared by the two passes
   int row_tiles;          // ceil(n / 256)
   int col_tiles;          // m_pad / 128
   int splits;
@@ -250,7 +276,34 @@ __device__ __forceinline__ void lse_chunk(const uint32_t (&r)[32], float& shift,
   sum += acc;
 }
 
-template <int KP, int S, bool BF16>
+// Fast pass: the 32 values are already shifted; just sum their exp2.
+__device__ __forceinline__ float exp2_sum32_noshift(const float (&v)[32]) {
+  uint64_t acc0 = tc::pack2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
+#pragma unroll
+  for (int k = 0; k < 32; k += 8) {
+    acc0 = tc::add2(acc0, tc::pack2(ex2(v[k]), ex2(v[k + 1])));
+    acc1 = tc::add2(acc1, tc::pack2(ex2(v[k + 2]), ex2(v[k + 3])));
+    acc2 = tc::add2(acc2, tc::pack2(ex2(v[k + 4]), ex2(v[k + 5])));
+    acc3 = tc::add2(acc3, tc::pack2(ex2(v[k + 6]), ex2(v[k + 7])));
+  }
+  float s0, s1;
+  tc::unpack2(tc::add2(tc::add2(acc0, acc1), tc::add2(acc2, acc3)), s0, s1);
+  return s0 + s1;
+}
+
+template <bool FAST>
+__device__ __forceinline__ void chunk(const uint32_t (&r)[32], float& shift, float& sum) {
+  if (FAST) {
+    float v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+    sum += exp2_sum32_noshift(v);
+  } else {
+    lse_chunk(r, shift, sum);
+  }
+}
+
+template <int KP, int S, bool BF16, bool FAST>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     softmin_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mB0,
                       const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mB1,
@@ -284,6 +337,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const int tile0 = sp * T.tiles_per_split;
   const int ntiles = min(T.tiles_per_split, T.col_tiles - tile0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the safe pass only recomputes the CTAs the fast pass marked
+  if (!FAST && T.flags != nullptr && T.flags[bid] == 0) return;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -347,10 +402,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (!tc::mbar_wait(&full[s], (t / S) & 1, ab)) break;
         tc::tc_fence_after();
         const unsigned char* Bst = Bs + s * L::kStageBytes;
+        const int nks = T.ksteps;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
 #pragma unroll
           for (int ks = 0; ks < KP / 16; ++ks) {
+            if (ks >= nks) break;   // the rest of the operand row is zero padding
             const uint32_t aaddr = tc::smem_u32(As + (h * KB + ks / 4) * 16384 + (ks % 4) * 32);
             const uint32_t baddr = tc::smem_u32(Bst + (ks / 4) * 16384 + (ks % 4) * 32);
             tc::mma_f16(tbase + (b * 2 + h) * 128, tc::sw128_desc(aaddr), tc::sw128_desc(baddr),
@@ -371,7 +428,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     const int h = e >> 2;
     const int q = warp & 3;
     const int64_t row = static_cast<int64_t>(row0) + h * 128 + q * 32 + lane;
-    float mrun = kRunInit, srun = 0.0f;
+    // fast pass: the MMA already subtracted the shift e_i, the sum starts at 0
+    float mrun = FAST ? 0.0f : kRunInit, srun = 0.0f;
     bool ok = true;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
@@ -391,34 +449,42 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       tc::tmem_ld32_issue(tcol, ra);
       tc::tmem_ld_wait(ra);
       tc::tmem_ld32_issue(tcol + 32, rb);
-      lse_chunk(ra, mrun, srun);
+      chunk<FAST>(ra, mrun, srun);
       tc::tmem_ld_wait(rb);
       tc::tmem_ld32_issue(tcol + 64, ra);
-      lse_chunk(rb, mrun, srun);
+      chunk<FAST>(rb, mrun, srun);
       tc::tmem_ld_wait(ra);
       tc::tmem_ld32_issue(tcol + 96, rb);
-      lse_chunk(ra, mrun, srun);
+      chunk<FAST>(ra, mrun, srun);
       tc::tmem_ld_wait(rb);
-      lse_chunk(rb, mrun, srun);
+      chunk<FAST>(rb, mrun, srun);
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
     }
     if (row < T.n) {
+      bool write = true;
       if (!ok || *ab) {
-        const float nan = __int_as_float(0x7fc00000);
-        if (T.splits == 1) T.out[row] = nan;
-        else {
-          T.pm[static_cast<int64_t>(sp) * T.n + row] = nan;
-          T.ps[static_cast<int64_t>(sp) * T.n + row] = nan;
+        mrun = srun = __int_as_float(0x7fc00000);   // NaN: the wait gave up
+      } else if (FAST) {
+        // the estimate was usable iff the sum stayed in a safe range;
+        // otherwise the safe pass recomputes every row of this CTA
+        if (srun > 8.673617e-19f && srun < 1.3292280e36f) {   // (2^-60, 2^120)
+          mrun = -T.est[row] * (kLog2e / T.eps);
+        } else {
+          T.flags[bid] = 1;
+          write = false;
         }
-      } else if (T.splits == 1) {
-        float v = -T.eps * kLn2 * (mrun + log2f(srun));
-        if (T.avg_with) v = 0.5f * (T.avg_with[row] + v);
-        T.out[row] = v;
-      } else {
-        T.pm[static_cast<int64_t>(sp) * T.n + row] = mrun;
-        T.ps[static_cast<int64_t>(sp) * T.n + row] = srun;
+      }
+      if (write) {
+        if (T.splits == 1) {
+          float v = -T.eps * kLn2 * (mrun + log2f(srun));
+          if (T.avg_with) v = 0.5f * (T.avg_with[row] + v);
+          T.out[row] = v;
+        } else {
+          T.pm[static_cast<int64_t>(sp) * T.n + row] = mrun;
+          T.ps[static_cast<int64_t>(sp) * T.n + row] = srun;
+        }
       }
     }
   }
@@ -481,10 +547,10 @@ int tc_splits(int row_tiles, int col_tiles, int other_blocks) {
   return best;
 }
 
-template <int KP, int S, bool BF16>
+template <int KP, int S, bool BF16, bool FAST>
 int launch_tc_kernel(const CUtensorMap* maps, const TcTask& a, const TcTask& b, cudaStream_t st) {
   using L = TcSmem<KP, S>;
-  auto kern = softmin_tc_kernel<KP, S, BF16>;
+  auto kern = softmin_tc_kernel<KP, S, BF16, FAST>;
   static bool attr_set = false;  // set once per process (same value every time)
   if (!attr_set) {
     GW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
@@ -495,16 +561,24 @@ int launch_tc_kernel(const CUtensorMap* maps, const TcTask& a, const TcTask& b, 
   return GW_OK;
 }
 
-template <bool BF16>
+template <bool BF16, bool FAST>
 int dispatch_tc(int KP, const CUtensorMap* maps, const TcTask& a, const TcTask& b, cudaStream_t st) {
   switch (KP) {
-    case 64: return launch_tc_kernel<64, 4, BF16>(maps, a, b, st);
-    case 128: return launch_tc_kernel<128, 3, BF16>(maps, a, b, st);
-    case 192: return launch_tc_kernel<192, 2, BF16>(maps, a, b, st);
+    case 64: return launch_tc_kernel<64, 4, BF16, FAST>(maps, a, b, st);
+    case 128: return launch_tc_kernel<128, 3, BF16, FAST>(maps, a, b, st);
+    case 192: return launch_tc_kernel<192, 2, BF16, FAST>(maps, a, b, st);
     default: break;
   }
   set_error("tensor-core softmin: operand width %d (K too large for this precision)", KP);
   return GW_EUNSUPPORTED;
+}
+
+int run_tc(bool bf16, bool fast, int KP, const CUtensorMap* maps, const TcTask& a, const TcTask& b,
+           cudaStream_t st) {
+  if (bf16) return fast ? dispatch_tc<true, true>(KP, maps, a, b, st)
+                        : dispatch_tc<true, false>(KP, maps, a, b, st);
+  return fast ? dispatch_tc<false, true>(KP, maps, a, b, st)
+              : dispatch_tc<false, false>(KP, maps, a, b, st);
 }
 
 }  // namespace
@@ -526,6 +600,7 @@ size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
   const int s = max_splits(static_cast<int>(m_pad / kBN));
   c.take<float>(static_cast<size_t>(s) * n);
   c.take<float>(static_cast<size_t>(s) * n);
+  c.take<int>(static_cast<size_t>(n_pad / kBM) * s);   // recompute flags
   return c.used();
 }
 
@@ -544,6 +619,7 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     row_tiles[q] = ceil_div(tasks[q].n, kBM);
     col_tiles[q] = ceil_div(tasks[q].m, kBN);
   }
+  bool any_est = false, all_est = true;
   // one split count for the launch, chosen from both tasks' tiles
   const int splits = tc_splits(row_tiles[0], col_tiles[0], ntasks == 2 ? row_tiles[1] : 0);
   for (int q = 0; q < ntasks; ++q) {
@@ -563,8 +639,11 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
       T.pm = ws.take<float>(static_cast<size_t>(s) * T.n);
       T.ps = ws.take<float>(static_cast<size_t>(s) * T.n);
     }
+    const bool use_est = T.est != nullptr && T.est != T.out;
+    int* flags = ws.take<int>(static_cast<size_t>(row_tiles[q]) * s);
     GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
     GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned), st));
+    GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q] * s, st));
     tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
                                                    T.sB, T.m, mx);
     GW_LAUNCH_CHECK();
@@ -574,20 +653,20 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     dim3 blk(64, 4);
     if (bf16) {
       tc_prep_kernel<__nv_bfloat16><<<ceil_div(n_pad, 4), blk, 0, st>>>(
-          T.A, T.sA, nullptr, nullptr, T.n, n_pad, shp, 0, alpha, beta, inv_eps, mx,
-          reinterpret_cast<__nv_bfloat16*>(opA));
+          T.A, T.sA, nullptr, nullptr, use_est ? T.est : nullptr, T.n, n_pad, shp, 0, alpha, beta,
+          inv_eps, mx, reinterpret_cast<__nv_bfloat16*>(opA));
       GW_LAUNCH_CHECK();
       tc_prep_kernel<__nv_bfloat16><<<ceil_div(m_pad, 4), blk, 0, st>>>(
-          T.B, T.sB, T.h, T.logw, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
+          T.B, T.sB, T.h, T.logw, nullptr, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
           reinterpret_cast<__nv_bfloat16*>(opB));
       GW_LAUNCH_CHECK();
     } else {
       tc_prep_kernel<__half><<<ceil_div(n_pad, 4), blk, 0, st>>>(
-          T.A, T.sA, nullptr, nullptr, T.n, n_pad, shp, 0, alpha, beta, inv_eps, mx,
-          reinterpret_cast<__half*>(opA));
+          T.A, T.sA, nullptr, nullptr, use_est ? T.est : nullptr, T.n, n_pad, shp, 0, alpha, beta,
+          inv_eps, mx, reinterpret_cast<__half*>(opA));
       GW_LAUNCH_CHECK();
       tc_prep_kernel<__half><<<ceil_div(m_pad, 4), blk, 0, st>>>(
-          T.B, T.sB, T.h, T.logw, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
+          T.B, T.sB, T.h, T.logw, nullptr, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
           reinterpret_cast<__half*>(opB));
       GW_LAUNCH_CHECK();
     }
@@ -596,6 +675,11 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     TcTask& K = tt[q];
     K.n = T.n;
     K.m = T.m;
+    K.ksteps = (shp.used + 15) / 16;
+    K.est = use_est ? T.est : nullptr;
+    K.flags = flags;
+    any_est = any_est || use_est;
+    all_est = all_est && use_est;
     K.row_tiles = row_tiles[q];
     K.col_tiles = col_tiles[q];
     K.splits = s;
@@ -613,8 +697,14 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     tt[1] = tt[0];
     tt[1].blocks = 0;
   }
-  return bf16 ? dispatch_tc<true>(shp.KP, maps, tt[0], tt[1], st)
-              : dispatch_tc<false>(shp.KP, maps, tt[0], tt[1], st);
+  if (!all_est) {
+    // no usable estimate for some task: one safe pass over every CTA
+    tt[0].flags = tt[1].flags = nullptr;
+    return run_tc(bf16, false, shp.KP, maps, tt[0], tt[1], st);
+  }
+  (void)any_est;
+  GW_TRY(run_tc(bf16, true, shp.KP, maps, tt[0], tt[1], st));
+  return run_tc(bf16, false, shp.KP, maps, tt[0], tt[1], st);
 }
 
 }  // namespace gw

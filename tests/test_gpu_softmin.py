@@ -145,3 +145,30 @@ def test_tensor_core_average_alias_and_determinism(gw):
     prev = o1.clone()
     gw.gw_sinkhorn_softmin(*args, 0.07, prec=3, avg_with=prev, out=prev)
     assert bool((prev == o1).all())   # (x + x) / 2 == x exactly
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("quality", ["good", "far", "mixed"])
+def test_tensor_core_shift_estimate_paths(gw, prec, quality):
+    """avg_with (not aliased to out) doubles as the per-row shift estimate of
+    the fast pass.  Good estimates take the fast path; estimates off by more
+    than the safe range (some or all rows) send their CTAs through the safe
+    pass.  Every case must match the oracle."""
+    from helpers import softmin_tolerance_prec
+    n, m, K, eps = 3000, 2000, 16, 0.05
+    A, B, sA, sB, h, logw = make_inputs(n, m, K, seed=31)
+    ref = oracle_softmin(A, B, sA, sB, h, logw, eps)
+    g = W.rng(77)
+    if quality == "good":
+        prev = ref + 1e-3 * eps * g.standard_normal(n)
+    elif quality == "far":
+        prev = ref + 300.0 * eps * np.sign(g.standard_normal(n))   # 2^+-430: out of range
+    else:
+        prev = ref + np.where(g.random(n) < 0.02, 300.0 * eps, 0.01 * eps)
+    prev = np.asarray(prev, np.float32).astype(np.float64)
+    out = gw.gw_sinkhorn_softmin(f32(A), f32(B), f32(sA), f32(sB), f32(h), f32(logw), eps,
+                                 prec=prec, avg_with=f32(prev))
+    want = 0.5 * (prev + ref)
+    tol = 0.5 * softmin_tolerance_prec(A, B, sA, sB, h, logw, eps, prec) + 1e-7 * np.abs(want)
+    err = np.abs(host(out) - want)
+    assert np.all(err <= tol), (quality, err.max())
