@@ -212,7 +212,7 @@ int launch_softmin(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cudaStr
   for (int q = 0; q < ntasks; ++q) t[q] = tasks[q];
   GW_REQUIRE(ntasks == 1 || t[0].K == t[1].K, GW_EINVAL, "fused softmin tasks need the same K");
   if (prec != GW_PREC_FP32) {
-    GW_TRY(launch_softmin_tc(t, ntasks, prec, ws, st));
+    return launch_softmin_tc(t, ntasks, prec, ws, st);   // merges its own split partials
   } else {
     int blocks[2] = {0, 0};
     for (int q = 0; q < ntasks; ++q) {

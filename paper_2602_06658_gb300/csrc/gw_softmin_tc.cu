@@ -53,6 +53,9 @@ constexpr int kThreadsTc = 320;
 constexpr float kBiasConst = 32768.0f;       // A-side multiplier of the bias columns
 constexpr float kHalfMax = 65504.0f;
 constexpr float kRunInit = -1.0e9f;          // running max start (below every real exponent)
+constexpr float kShiftBias = 30.0f;          // fast-pass shift sits this far below the estimate
+constexpr float kSumLo = 8.673617e-19f;      // 2^-60: a total below this underflowed
+constexpr float kSumHi = 1.3292280e36f;      // 2^120: a sum above this (or inf/NaN) overflowed
 
 struct TcOperandShape {
   int K;        // feature dimension
@@ -181,8 +184,8 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
         if (role == 1) {
           v = kBiasConst;
         } else if (est) {
-          // shift estimate e_i = -est_i log2(e) / eps; the columns hold -e_i / c
-          const float e = est[r] * inv_eps * kLog2e / kBiasConst;
+          // shift e_i = -est_i log2(e) / eps - kShiftBias; the columns hold -e_i / c
+          const float e = (est[r] * inv_eps * kLog2e + kShiftBias) / kBiasConst;
           v = split3<T>(e, k - shp.col_e);
         }
       }
@@ -337,8 +340,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const int tile0 = sp * T.tiles_per_split;
   const int ntiles = min(T.tiles_per_split, T.col_tiles - tile0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the safe pass only recomputes the CTAs the fast pass marked
-  if (!FAST && T.flags != nullptr && T.flags[bid] == 0) return;
+  // the safe pass only recomputes the row tiles the fast pass marked
+  if (!FAST && T.flags != nullptr && T.flags[rt] == 0) return;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -463,28 +466,38 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
     }
     if (row < T.n) {
-      bool write = true;
+      // z' = z - shift_i came out of the MMA when an estimate was folded in
+      const float shift_i = T.est ? -T.est[row] * (kLog2e / T.eps) - kShiftBias : 0.0f;
+      const int64_t po = static_cast<int64_t>(sp) * T.n + row;
       if (!ok || *ab) {
-        mrun = srun = __int_as_float(0x7fc00000);   // NaN: the wait gave up
+        const float nan = __int_as_float(0x7fc00000);   // a wait gave up
+        if (T.splits == 1) T.out[row] = nan;
+        else T.pm[po] = T.ps[po] = nan;
       } else if (FAST) {
-        // the estimate was usable iff the sum stayed in a safe range;
-        // otherwise the safe pass recomputes every row of this CTA
-        if (srun > 8.673617e-19f && srun < 1.3292280e36f) {   // (2^-60, 2^120)
-          mrun = -T.est[row] * (kLog2e / T.eps);
-        } else {
-          T.flags[bid] = 1;
-          write = false;
-        }
-      }
-      if (write) {
+        // a split may hold none of the row's mass (its sum underflows
+        // harmlessly); only overflow, or a total out of range, needs the
+        // safe pass, which then recomputes the whole row tile
         if (T.splits == 1) {
-          float v = -T.eps * kLn2 * (mrun + log2f(srun));
-          if (T.avg_with) v = 0.5f * (T.avg_with[row] + v);
-          T.out[row] = v;
+          if (srun > kSumLo && srun < kSumHi) {
+            float v = -T.eps * kLn2 * (shift_i + log2f(srun));
+            if (T.avg_with) v = 0.5f * (T.avg_with[row] + v);
+            T.out[row] = v;
+          } else {
+            T.flags[rt] = 1;
+          }
+        } else if (srun < kSumHi) {
+          T.pm[po] = shift_i;
+          T.ps[po] = srun;
         } else {
-          T.pm[static_cast<int64_t>(sp) * T.n + row] = mrun;
-          T.ps[static_cast<int64_t>(sp) * T.n + row] = srun;
+          T.flags[rt] = 1;
         }
+      } else if (T.splits == 1) {
+        float v = -T.eps * kLn2 * (shift_i + mrun + log2f(srun));
+        if (T.avg_with) v = 0.5f * (T.avg_with[row] + v);
+        T.out[row] = v;
+      } else {
+        T.pm[po] = shift_i + mrun;
+        T.ps[po] = srun;
       }
     }
   }
@@ -495,6 +508,42 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     tc::tc_fence_after();
     tc::tmem_dealloc(tbase, 512);
   }
+}
+
+// Merge split partials.  mode 0: every row; mode 1 (after the fast pass):
+// rows of unflagged tiles whose total is in range are written, the others
+// flag their tile; mode 2 (after the safe pass): rows of flagged tiles only.
+__global__ void tc_combine_kernel(TcTask t0, TcTask t1, int64_t n0, int mode) {
+  const int64_t gi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool second = gi >= n0;
+  const TcTask& T = second ? t1 : t0;
+  const int64_t i = second ? gi - n0 : gi;
+  if (i >= T.n || T.splits == 1) return;
+  const int rt = static_cast<int>(i / kBM);
+  if (mode == 1 && T.flags[rt] != 0) return;
+  if (mode == 2 && T.flags[rt] == 0) return;
+  float M = kNegBig;
+  for (int s = 0; s < T.splits; ++s) M = fmaxf(M, T.pm[static_cast<int64_t>(s) * T.n + i]);
+  float S = 0.0f;
+  for (int s = 0; s < T.splits; ++s) {
+    const int64_t o = static_cast<int64_t>(s) * T.n + i;
+    S += T.ps[o] * ex2(T.pm[o] - M);
+  }
+  if (mode == 1 && !(S > kSumLo && S < kSumHi)) {
+    T.flags[rt] = 1;
+    return;
+  }
+  float v = -T.eps * kLn2 * (M + log2f(S));
+  if (T.avg_with) v = 0.5f * (T.avg_with[i] + v);
+  T.out[i] = v;
+}
+
+int run_combine(const TcTask& a, const TcTask& b, int mode, cudaStream_t st) {
+  if (a.splits == 1 && (b.blocks == 0 || b.splits == 1)) return GW_OK;
+  const int64_t nn = a.n + (b.blocks ? b.n : 0);
+  tc_combine_kernel<<<ceil_div(nn, 256), 256, 0, st>>>(a, b, a.n, mode);
+  GW_LAUNCH_CHECK();
+  return GW_OK;
 }
 
 // ------------------------------------------------------------ host side
@@ -600,7 +649,7 @@ size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
   const int s = max_splits(static_cast<int>(m_pad / kBN));
   c.take<float>(static_cast<size_t>(s) * n);
   c.take<float>(static_cast<size_t>(s) * n);
-  c.take<int>(static_cast<size_t>(n_pad / kBM) * s);   // recompute flags
+  c.take<int>(static_cast<size_t>(n_pad / kBM));       // recompute flags per row tile
   return c.used();
 }
 
@@ -619,7 +668,10 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     row_tiles[q] = ceil_div(tasks[q].n, kBM);
     col_tiles[q] = ceil_div(tasks[q].m, kBN);
   }
-  bool any_est = false, all_est = true;
+  // the fast pass needs an estimate for every task (not aliased to the output)
+  bool all_est = true;
+  for (int q = 0; q < ntasks; ++q)
+    all_est = all_est && tasks[q].est != nullptr && tasks[q].est != tasks[q].out;
   // one split count for the launch, chosen from both tasks' tiles
   const int splits = tc_splits(row_tiles[0], col_tiles[0], ntasks == 2 ? row_tiles[1] : 0);
   for (int q = 0; q < ntasks; ++q) {
@@ -639,11 +691,11 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
       T.pm = ws.take<float>(static_cast<size_t>(s) * T.n);
       T.ps = ws.take<float>(static_cast<size_t>(s) * T.n);
     }
-    const bool use_est = T.est != nullptr && T.est != T.out;
-    int* flags = ws.take<int>(static_cast<size_t>(row_tiles[q]) * s);
+    const bool use_est = all_est;
+    int* flags = ws.take<int>(static_cast<size_t>(row_tiles[q]));
     GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
     GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned), st));
-    GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q] * s, st));
+    GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q], st));
     tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
                                                    T.sB, T.m, mx);
     GW_LAUNCH_CHECK();
@@ -678,8 +730,6 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     K.ksteps = (shp.used + 15) / 16;
     K.est = use_est ? T.est : nullptr;
     K.flags = flags;
-    any_est = any_est || use_est;
-    all_est = all_est && use_est;
     K.row_tiles = row_tiles[q];
     K.col_tiles = col_tiles[q];
     K.splits = s;
@@ -698,13 +748,15 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     tt[1].blocks = 0;
   }
   if (!all_est) {
-    // no usable estimate for some task: one safe pass over every CTA
+    // no usable estimate: one safe pass over every CTA
     tt[0].flags = tt[1].flags = nullptr;
-    return run_tc(bf16, false, shp.KP, maps, tt[0], tt[1], st);
+    GW_TRY(run_tc(bf16, false, shp.KP, maps, tt[0], tt[1], st));
+    return run_combine(tt[0], tt[1], 0, st);
   }
-  (void)any_est;
   GW_TRY(run_tc(bf16, true, shp.KP, maps, tt[0], tt[1], st));
-  return run_tc(bf16, false, shp.KP, maps, tt[0], tt[1], st);
+  GW_TRY(run_combine(tt[0], tt[1], 1, st));
+  GW_TRY(run_tc(bf16, false, shp.KP, maps, tt[0], tt[1], st));
+  return run_combine(tt[0], tt[1], 2, st);
 }
 
 }  // namespace gw
