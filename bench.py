@@ -354,8 +354,11 @@ def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps
     out = torch.empty(n, dtype=torch.float32, device=X.device)
     ws = gw.workspace(gw.gw_workspace_size(gw.OP_SOFTMIN, n, m, D, 1, prec), X.device)
     eps = eps_at(args, args.n_outer - 1)
+    # as in the solve: the current f is averaged in and serves as the shift estimate
+    f_prev = state["f"]
     for _ in range(3):
-        gw.gw_sinkhorn_softmin(X, V, s, t, state["g"], logb, eps, prec=prec, out=out, ws=ws)
+        gw.gw_sinkhorn_softmin(X, V, s, t, state["g"], logb, eps, prec=prec, avg_with=f_prev,
+                               out=out, ws=ws)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     times = []
@@ -363,7 +366,8 @@ def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps
         flush.random_(0, 255)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        gw.gw_sinkhorn_softmin(X, V, s, t, state["g"], logb, eps, prec=prec, out=out, ws=ws)
+        gw.gw_sinkhorn_softmin(X, V, s, t, state["g"], logb, eps, prec=prec, avg_with=f_prev,
+                               out=out, ws=ws)
         e1.record(st)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)

@@ -49,7 +49,8 @@ namespace {
 
 constexpr int kBM = 256;       // rows per CTA (two M = 128 halves)
 constexpr int kBN = 128;       // columns per tile
-constexpr int kThreadsTc = 320;
+constexpr int kEpiWarps = 16;  // 4 per scheduler: 2 per (half, lane quarter), one per column half
+constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 constexpr float kBiasConst = 32768.0f;       // A-side multiplier of the bias columns
 constexpr float kHalfMax = 65504.0f;
 constexpr float kRunInit = -1.0e9f;          // running max start (below every real exponent)
@@ -219,9 +220,11 @@ struct TcSmem {
   static constexpr int kABytes = 2 * KB * 16384;          // 256 rows
   static constexpr int kStageBytes = KB * 16384;          // 128 rows
   static constexpr int kBarOff = kABytes + S * kStageBytes;
-  // + barriers + alignment slack; at least 120 KB so that one CTA owns the
-  // SM (it allocates all 512 TMEM columns)
-  static constexpr int kBytes = kBarOff + 1280 > 122880 ? kBarOff + 1280 : 122880;
+  // + barriers and the row-merge buffers (3 x 256 words) + alignment slack;
+  // at least 120 KB so that one CTA owns the SM (it allocates all 512 TMEM
+  // columns)
+  static constexpr int kTail = 256 + 3 * 1024 + 1024;
+  static constexpr int kBytes = kBarOff + kTail > 122880 ? kBarOff + kTail : 122880;
 };
 
 __device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&tfull[b], 1);
-      tc::mbar_init(&tempty[b], 8);
+      tc::mbar_init(&tempty[b], kEpiWarps);
     }
     tc::mbar_init(afull, 1);
     tc::mbar_init(drain, 1);
@@ -427,8 +430,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // warp -> (half h, lane quarter q = warp % 4, column half ch): each row's
+    // 128 columns per tile are shared by two warps, merged at the end
     const int e = warp - 2;
-    const int h = e >> 2;
+    const int g = e >> 2;
+    const int h = g & 1;
+    const int ch = g >> 1;
     const int q = warp & 3;
     const int64_t row = static_cast<int64_t>(row0) + h * 128 + q * 32 + lane;
     // fast pass: the MMA already subtracted the shift e_i, the sum starts at 0
@@ -445,25 +452,44 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         break;
       }
       tc::tc_fence_after();
-      const uint32_t tcol = tbase + (static_cast<uint32_t>(q * 32) << 16) + (b * 2 + h) * 128;
-      // four chunks of 32 columns, the next chunk's TMEM load in flight
-      // while the current one is reduced
+      const uint32_t tcol =
+          tbase + (static_cast<uint32_t>(q * 32) << 16) + (b * 2 + h) * 128 + ch * 64;
+      // two chunks of 32 columns, the second load in flight while the first
+      // is reduced
       uint32_t ra[32], rb[32];
       tc::tmem_ld32_issue(tcol, ra);
       tc::tmem_ld_wait(ra);
       tc::tmem_ld32_issue(tcol + 32, rb);
       chunk<FAST>(ra, mrun, srun);
       tc::tmem_ld_wait(rb);
-      tc::tmem_ld32_issue(tcol + 64, ra);
-      chunk<FAST>(rb, mrun, srun);
-      tc::tmem_ld_wait(ra);
-      tc::tmem_ld32_issue(tcol + 96, rb);
-      chunk<FAST>(ra, mrun, srun);
-      tc::tmem_ld_wait(rb);
       chunk<FAST>(rb, mrun, srun);
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
+    }
+    // merge the two column halves of each row (named barrier of the epilogue
+    // warps only); the ch = 0 warp writes the row
+    {
+      float* xm = reinterpret_cast<float*>(bars + 2 * S + 8);   // [256] shifts
+      float* xs = xm + 256;                                     // [256] sums
+      int* xo = reinterpret_cast<int*>(xs + 256);               // [256] ok
+      const int slot = h * 128 + q * 32 + lane;
+      if (ch == 1) {
+        xm[slot] = mrun;
+        xs[slot] = srun;
+        xo[slot] = ok ? 1 : 0;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+      if (ch == 1) goto epilogue_done;
+      const float m2 = xm[slot], s2 = xs[slot];
+      ok = ok && xo[slot] != 0;
+      if (FAST) {
+        srun += s2;   // both halves sum against the same shift
+      } else {
+        const float M = fmaxf(mrun, m2);
+        srun = srun * ex2(mrun - M) + s2 * ex2(m2 - M);
+        mrun = M;
+      }
     }
     if (row < T.n) {
       // z' = z - shift_i came out of the MMA when an estimate was folded in
@@ -500,6 +526,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         T.ps[po] = srun;
       }
     }
+  epilogue_done:;
   }
   tc::tc_fence_before();
   __syncthreads();
