@@ -353,7 +353,7 @@ def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps
     logb = torch.log(b)
     out = torch.empty(n, dtype=torch.float32, device=X.device)
     ws = gw.workspace(gw.gw_workspace_size(gw.OP_SOFTMIN, n, m, D, 1, prec), X.device)
-    eps = eps_at(args, args.n_outer - 1)
+    eps = eps_at(args, args.warmup + args.steps - 1)   # the state's step
     # as in the solve: the current f is averaged in and serves as the shift estimate
     f_prev = state["f"]
     for _ in range(3):

@@ -65,6 +65,7 @@ struct TcOperandShape {
   int col_u;    // first rank-one column
   int col_w;    // first column-bias column
   int col_e;    // first row-estimate column
+  int col_k;    // mask column (-inf for padded and zero-weight target columns)
   int used;     // non-zero columns
 };
 
@@ -75,7 +76,8 @@ TcOperandShape tc_shape(int K, int prec) {
   s.col_u = s.mult * K;
   s.col_w = s.col_u + 3;
   s.col_e = s.col_w + 3;
-  s.used = s.col_e + 3;
+  s.col_k = s.col_e + 3;
+  s.used = s.col_k + 1;
   s.KP = ((s.used + 63) / 64) * 64;
   return s;
 }
@@ -106,23 +108,41 @@ __device__ __forceinline__ float split3(float x, int part) {
   return part == 0 ? x0 : (part == 1 ? x1 : r1 - x1);
 }
 
-// max |x| of four arrays -> mx[0..3] (non-negative floats compare as ints)
+// Largest magnitudes that set the operand scales -> mx[0..5] (non-negative
+// floats compare as unsigned ints): |A|, |B|, |sA|, |sB|, the finite column
+// biases |w_j| and the row shifts |e_i| (when an estimate is given).
 __global__ void tc_absmax_kernel(const float* A, int64_t nA, const float* B, int64_t nB,
                                  const float* sA, int64_t n, const float* sB, int64_t m,
-                                 unsigned* mx) {
-  float v[4] = {0.f, 0.f, 0.f, 0.f};
+                                 const float* h, const float* logw, const float* est,
+                                 float inv_eps, unsigned* mx) {
+  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   for (int64_t i = t0; i < nA; i += stride) v[0] = fmaxf(v[0], fabsf(A[i]));
   for (int64_t i = t0; i < nB; i += stride) v[1] = fmaxf(v[1], fabsf(B[i]));
   for (int64_t i = t0; i < n; i += stride) v[2] = fmaxf(v[2], fabsf(sA[i]));
-  for (int64_t i = t0; i < m; i += stride) v[3] = fmaxf(v[3], fabsf(sB[i]));
+  for (int64_t i = t0; i < m; i += stride) {
+    v[3] = fmaxf(v[3], fabsf(sB[i]));
+    const float w = (h[i] * inv_eps + logw[i]) * kLog2e;
+    if (isfinite(w)) v[4] = fmaxf(v[4], fabsf(w));
+  }
+  if (est)
+    for (int64_t i = t0; i < n; i += stride)
+      v[5] = fmaxf(v[5], fabsf(est[i] * inv_eps * kLog2e + kShiftBias));
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 6; ++k) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
     if ((threadIdx.x & 31) == 0) atomicMax(&mx[k], __float_as_uint(v[k]));
   }
+}
+
+// Power-of-two scale that brings max |x| / c to at most 2^14 (so a three-way
+// 16-bit split keeps all three parts normal), within [2^-14, 2^15].
+__device__ __forceinline__ float pow2_scale(float mxv) {
+  float c = 6.103515625e-05f;   // 2^-14
+  while (c < 32768.0f && mxv > 16384.0f * c) c *= 2.0f;
+  return c;
 }
 
 // Scale pair (sa, sb) with sa * sb = prod that balances max|x sa| and max|y sb|.
@@ -149,6 +169,8 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
   if (r >= rows_pad) return;
   const float mA = __uint_as_float(mx[0]), mB = __uint_as_float(mx[1]);
   const float msA = __uint_as_float(mx[2]), msB = __uint_as_float(mx[3]);
+  const float cw = pow2_scale(__uint_as_float(mx[4]));
+  const float ce = pow2_scale(__uint_as_float(mx[5]));
   float sa, sb, ua, ub;
   balance(alpha, mA, mB, &sa, &sb);
   balance(beta, msA, msB, &ua, &ub);
@@ -174,24 +196,27 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
         if (role == 0) v = part < 2 ? hi : x - hi;   // [hi, hi, lo]
         else v = part == 1 ? x - hi : hi;            // [hi, lo, hi]
       } else if (k < shp.col_e) {
+        // column bias w_j = (h_j/eps + logw_j) log2(e) as c_w * split(w_j / c_w)
         if (role == 0) {
-          v = kBiasConst;
+          v = cw;
         } else {
-          float w = (h[r] * inv_eps + logw[r]) * kLog2e / kBiasConst;
-          w = fmaxf(w, -kHalfMax);             // zero weights: effectively -inf
-          v = split3<T>(w, k - shp.col_w);
+          const float w = (h[r] * inv_eps + logw[r]) * kLog2e;
+          v = isfinite(w) ? split3<T>(w / cw, k - shp.col_w) : 0.0f;
         }
-      } else if (k < shp.used) {
+      } else if (k < shp.col_k) {
+        // row shift e_i = -est_i log2(e) / eps - kShiftBias as -c_e * split(-e_i / c_e)
         if (role == 1) {
-          v = kBiasConst;
+          v = ce;
         } else if (est) {
-          // shift e_i = -est_i log2(e) / eps - kShiftBias; the columns hold -e_i / c
-          const float e = (est[r] * inv_eps * kLog2e + kShiftBias) / kBiasConst;
-          v = split3<T>(e, k - shp.col_e);
+          v = split3<T>((est[r] * inv_eps * kLog2e + kShiftBias) / ce, k - shp.col_e);
         }
+      } else if (k == shp.col_k) {
+        // mask: zero-weight target columns never contribute
+        if (role == 0) v = kBiasConst;
+        else v = isfinite(logw[r]) ? 0.0f : -kHalfMax;
       }
-    } else if (role == 1 && k == shp.col_w) {
-      v = -kHalfMax;
+    } else if (role == 1 && k == shp.col_k) {
+      v = -kHalfMax;   // padding columns never contribute
     }
     row[k] = to16<T>(v);
   }
@@ -671,7 +696,7 @@ size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
   Carver c(nullptr, ~size_t(0));
   c.take<uint16_t>(static_cast<size_t>(n_pad) * shp.KP);
   c.take<uint16_t>(static_cast<size_t>(m_pad) * shp.KP);
-  c.take<unsigned>(4);
+  c.take<unsigned>(8);
   // partials for the largest split count any launch may pick
   const int s = max_splits(static_cast<int>(m_pad / kBN));
   c.take<float>(static_cast<size_t>(s) * n);
@@ -707,7 +732,7 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     const int64_t m_pad = static_cast<int64_t>(col_tiles[q]) * kBN;
     uint16_t* opA = ws.take<uint16_t>(static_cast<size_t>(n_pad) * shp.KP);
     uint16_t* opB = ws.take<uint16_t>(static_cast<size_t>(m_pad) * shp.KP);
-    unsigned* mx = ws.take<unsigned>(4);
+    unsigned* mx = ws.take<unsigned>(8);
     int s = splits < col_tiles[q] ? splits : col_tiles[q];
     const int tps = ceil_div(col_tiles[q], s);
     s = ceil_div(col_tiles[q], tps);
@@ -721,12 +746,13 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     const bool use_est = all_est;
     int* flags = ws.take<int>(static_cast<size_t>(row_tiles[q]));
     GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
-    GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned), st));
+    GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 8 * sizeof(unsigned), st));
     GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q], st));
-    tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
-                                                   T.sB, T.m, mx);
-    GW_LAUNCH_CHECK();
     const float inv_eps = 1.0f / T.eps;
+    tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
+                                                   T.sB, T.m, T.h, T.logw,
+                                                   use_est ? T.est : nullptr, inv_eps, mx);
+    GW_LAUNCH_CHECK();
     const float alpha = 16.0f * kLog2e * inv_eps;
     const float beta = 4.0f * kLog2e * inv_eps;
     dim3 blk(64, 4);
