@@ -255,6 +255,7 @@ size_t gw_workspace_size(int op, int64_t n, int64_t m, int D, int E, int prec) {
     case GW_OP_ENERGY: return energy_ws_bytes(n, m, D, E, prec) + 256;
     case GW_OP_SOLVE: return solve_ws_bytes(n, m, D, E, prec);
     case GW_OP_LIFT: return lift_ws_bytes(n, D) + 256;   /* (n points, D features) */
+    case GW_OP_GRAD: return grad_ws_bytes(n, m, D, E, 4, prec) + 256;
     default: return 0;
   }
 }
@@ -430,11 +431,37 @@ int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double*
               const double* Gamma_pi, float eps, int prec, const float* x, int dx_dim, int kind,
               float param, const float* basis, const float* eigvals, float* dX, float* dx,
               void* ws, size_t ws_bytes, gw_stream_t stream) {
-  (void)p; (void)f; (void)g; (void)Gamma_t; (void)Gamma_pi; (void)eps; (void)prec; (void)x;
-  (void)dx_dim; (void)kind; (void)param; (void)basis; (void)eigvals; (void)dX; (void)dx; (void)ws;
-  (void)ws_bytes; (void)stream;
-  gw::set_error("gw_grad_x is not available in this build");
-  return GW_EUNSUPPORTED;
+  gw::set_error("");
+  NONNULL(p);
+  GW_TRY(check_dims(p->n, p->m, p->D, p->E));
+  GW_REQUIRE(p->n >= 1, GW_EINVAL, "n must be >= 1");
+  GW_TRY(check_eps(eps));
+  GW_TRY(check_prec(prec));
+  NONNULL(p->X);
+  NONNULL(p->Y);
+  NONNULL(p->s);
+  NONNULL(p->t);
+  NONNULL(p->a);
+  NONNULL(p->b);
+  NONNULL(f);
+  NONNULL(g);
+  NONNULL(Gamma_t);
+  NONNULL(dX);
+  if (x != nullptr) {
+    GW_REQUIRE(dx_dim >= 1 && dx_dim <= 4, GW_EUNSUPPORTED, "points of dimension 1..4 (got %d)", dx_dim);
+    NONNULL(dx);
+    NONNULL(basis);
+    NONNULL(eigvals);
+    GW_REQUIRE(kind == GW_PEN_SQEUCLID || kind == GW_PEN_POWER || kind == GW_PEN_GAUSS, GW_EINVAL,
+               "unknown penalty %d", kind);
+  } else {
+    dx_dim = 0;
+  }
+  const size_t need = grad_ws_bytes(p->n, p->m, p->D, p->E, dx_dim, prec);
+  GW_REQUIRE(ws != nullptr && ws_bytes >= need, GW_ENOMEM,
+             "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
+  return run_grad(*p, f, g, Gamma_t, Gamma_pi, eps, prec, x, dx_dim, kind, param, basis, eigvals,
+                  dX, dx, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

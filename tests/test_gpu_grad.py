@@ -1,0 +1,122 @@
+"""Adjoint (gw_grad_x) against the FP64 oracle gradient and FP64 finite
+differences, on identical converged states; autograd wrapper."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import f32, f64, host
+
+pytestmark = pytest.mark.gpu
+
+r32 = lambda x: np.asarray(x, np.float32).astype(np.float64)
+
+
+def converged_state(X, Y, a, b, eps, G0, n_outer=60):
+    """Oracle solve to a tight fixed point; returns the state that encodes the
+    final plan (f, g on c_{Gamma_t}) and that plan."""
+    res = O.cnt_gw(a, b, X, Y, eps, n_outer, 300, Gamma0=G0, symmetric=False, record=False)
+    Gt = res["Gamma"]
+    C = O.cost_gamma(X, Y, Gt)
+    f, g = O.sinkhorn(a, b, C, eps, 2000, res["f"], res["g"], symmetric=False)
+    f, g = r32(f), r32(g)
+    pi = O.plan(a, b, f, g, C, eps)
+    return Gt, f, g, pi
+
+
+def grad_tolerance(pi, X, Y, a, eps):
+    """FP32 evaluation of the closed form: each plan entry carries a relative
+    error of ~(D+4) 2^-24 |C|/eps from its exponent, each sum over N or M
+    terms ~sqrt(N) 2^-24; scaled by the largest gradient term."""
+    scale = 16 * np.abs(X).max() * np.abs(Y).max() + 8 * (X * X).sum(1).max() * (Y * Y).sum(1).max()
+    rel = (X.shape[1] + 4) * 2.0 ** -24 * scale / eps + np.sqrt(max(X.shape[0], Y.shape[0])) * 2.0 ** -22
+    return 8.0 * rel
+
+
+@pytest.mark.parametrize("n,m,d,eps", [(200, 200, 2, 0.05), (300, 250, 3, 0.1)])
+def test_adjoint_squared_matches_oracle(gw, n, m, d, eps):
+    g = W.rng(n + d)
+    x, y = r32(g.standard_normal((n, d)) * 0.5), r32(g.standard_normal((m, d)) * 0.5)
+    a, b = r32(W.random_weights(n, 1, 0.3)), r32(W.random_weights(m, 2, 0.3))
+    X, Y = r32(O.center(x, a)), r32(O.center(y, b))
+    Gt, f, gg, pi = converged_state(X, Y, a, b, eps, 0.1 * g.standard_normal((d, d)))
+    ref = O.grad_x_squared(pi, O.cross_covariance(pi, X, Y), X, Y, a, b)
+    s, t = r32((X * X).sum(1)), r32((Y * Y).sum(1))
+    dX, _ = gw.gw_grad_x(f32(X), f32(Y), f32(s), f32(t), f32(a), f32(b), f32(f), f32(gg), f64(Gt),
+                         None, eps)
+    gmax = np.abs(ref).max()
+    assert np.abs(host(dX) - ref).max() <= max(grad_tolerance(pi, X, Y, a, eps), 1e-6) * gmax
+    # translation invariance: the centering adjoint makes the gradients sum to zero
+    assert np.abs(host(dX).sum(0)).max() <= 1e-5 * np.abs(host(dX)).sum(0).max()
+
+
+def test_adjoint_squared_matches_finite_differences(gw):
+    """N = M = 200 (the size the paper's gradient check runs at): the GPU
+    adjoint against central differences of the re-solved FP64 energy."""
+    n = 200
+    g = W.rng(7)
+    x, y = g.standard_normal((n, 2)) * 0.5, g.standard_normal((n, 2)) * 0.5
+    a = b = W.uniform_weights(n)
+    eps = 0.1
+    X, Y = O.center(x, a), O.center(y, b)
+    Gt, f, gg, pi = converged_state(X, Y, a, b, eps, 0.1 * g.standard_normal((2, 2)))
+    s, t = (X * X).sum(1), (Y * Y).sum(1)
+    dX, _ = gw.gw_grad_x(f32(X), f32(Y), f32(s), f32(t), f32(a), f32(b), f32(f), f32(gg), f64(Gt),
+                         None, eps)
+    dX = host(dX)
+    h = 1e-5
+    for (i, c) in [(0, 0), (57, 1), (199, 0)]:
+        xp, xm = x.copy(), x.copy()
+        xp[i, c] += h
+        xm[i, c] -= h
+        Ep = O.cnt_gw(a, b, O.center(xp, a), Y, eps, 30, 200, Gamma0=Gt, f0=f, g0=gg,
+                      symmetric=False)["history"][-1]["E"]
+        Em = O.cnt_gw(a, b, O.center(xm, a), Y, eps, 30, 200, Gamma0=Gt, f0=f, g0=gg,
+                      symmetric=False)["history"][-1]["E"]
+        fd = (Ep - Em) / (2 * h)
+        assert abs(dX[i, c] - fd) <= 1e-3 * np.abs(dX).max() + 1e-7, (i, c, dX[i, c], fd)
+
+
+@pytest.mark.parametrize("kind,param,D", [(1, 1.0, 8), (2, 0.8, 6)])
+def test_adjoint_lifted_matches_oracle(gw, kind, param, D):
+    n, m = 220, 200
+    w = W.gmm_rigid(n, seed=D, m=m)
+    x, y = r32(w["x"]), r32(w["y"])
+    a, b = r32(w["a"]), r32(w["b"])
+    kname = {1: "power", 2: "gauss"}[kind]
+    LX = O.lift(x, a, kname, param, D=D)
+    LY = O.lift(y, b, kname, param, D=D)
+    X, Y = r32(LX["X"]), r32(LY["X"])
+    V, lam = r32(LX["V"]), r32(LX["lam"])
+    eps = 0.05
+    Gt, f, gg, pi = converged_state(X, Y, a, b, eps, 0.1 * W.rng(3).standard_normal((D, D)))
+    ref = O.grad_x_lifted(pi, O.cross_covariance(pi, X, Y), X, Y, a, b, x, V, lam, kname, param)
+    s, t = r32((X * X).sum(1)), r32((Y * Y).sum(1))
+    dX, dx = gw.gw_grad_x(f32(X), f32(Y), f32(s), f32(t), f32(a), f32(b), f32(f), f32(gg), f64(Gt),
+                          None, eps, x=f32(x), kind=kind, param=param, basis=f32(V), eigvals=f32(lam))
+    gmax = np.abs(ref).max()
+    assert np.abs(host(dx) - ref).max() <= 2e-3 * gmax
+
+
+def test_autograd_wrapper_gives_the_adjoint(gw):
+    import torch
+    from paper_2602_06658_gb300.autograd import gw_energy_fn
+    w = W.square_rotated(300, seed=5)
+    x = torch.tensor(w["x"], dtype=torch.float32, device="cuda", requires_grad=True)
+    y = torch.tensor(w["y"], dtype=torch.float32, device="cuda")
+    a = torch.tensor(w["a"], dtype=torch.float32, device="cuda")
+    b = torch.tensor(w["b"], dtype=torch.float32, device="cuda")
+    E = gw_energy_fn(x, y, a, b, float(w["eps"]), 10, 50)
+    (gx,) = torch.autograd.grad(E, x)
+    assert gx.shape == x.shape and torch.isfinite(gx).all()
+    # rotation equivariance of the gradient (squared cost): grad(Qx) = Q grad(x)
+    th = 0.7
+    Q = torch.tensor([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]], dtype=torch.float32,
+                     device="cuda")
+    x2 = (x.detach() @ Q.T).requires_grad_(True)
+    G0 = None
+    E2 = gw_energy_fn(x2, y, a, b, float(w["eps"]), 10, 50, Gamma0=G0)
+    (gx2,) = torch.autograd.grad(E2, x2)
+    assert abs(E2.item() - E.item()) <= 1e-4 * abs(E.item())
+    assert torch.allclose(gx2, gx @ Q.T, atol=2e-3 * gx.abs().max().item())
