@@ -166,6 +166,9 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
       col.m = p.n;
       col.K = p.D;
       col.eps = eps;
+      // within an outer step only the potentials change: the tensor-core
+      // form keeps its 16-bit operands and refreshes the bias columns
+      row.reuse_ops = col.reuse_ops = it > 0 ? 1 : 0;
       if (o.symmetric) {
         // Algorithm 3: both halves read iterate n, then average.
         row.avg_with = B.f[fc];
@@ -183,7 +186,9 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
         row.out = B.f[fc ^ 1];
         GW_TRY(launch_softmin(&row, 1, o.prec, sub, st));
         fc ^= 1;
-        Carver sub2(base + mark, ws_bytes - mark);
+        // the column task keeps its own operands beside the row task's
+        const size_t off = (softmin_ws_bytes(p.n, p.m, p.D, o.prec) + 255) & ~size_t(255);
+        Carver sub2(base + mark + off, ws_bytes - mark - off);
         col.h = B.f[fc];
         col.avg_with = nullptr;
         col.out = B.g[gc ^ 1];

@@ -122,6 +122,10 @@ struct SoftminTask {
   int splits;       // column splits
   int cols_per_split;
   float eps;
+  // tensor-core form: the 16-bit operands already in the workspace (same
+  // carve position, same A, B, sA, sB, eps and precision) are still valid
+  // apart from the bias and shift columns, which are refreshed
+  int reuse_ops;
 };
 
 // Shape decisions of the softmin kernels (identical for sizing and launch).

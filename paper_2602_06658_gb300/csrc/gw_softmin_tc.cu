@@ -222,6 +222,58 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
   }
 }
 
+// Per-iteration refresh: largest |w_j| (finite) and |e_i| -> mx[4], mx[5]
+__global__ void tc_bias_absmax_kernel(const float* h, const float* logw, int64_t m,
+                                      const float* est, int64_t n, float inv_eps, unsigned* mx) {
+  float vw = 0.f, ve = 0.f;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < m; i += stride) {
+    const float w = (h[i] * inv_eps + logw[i]) * kLog2e;
+    if (isfinite(w)) vw = fmaxf(vw, fabsf(w));
+  }
+  if (est)
+    for (int64_t i = t0; i < n; i += stride)
+      ve = fmaxf(ve, fabsf(est[i] * inv_eps * kLog2e + kShiftBias));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vw = fmaxf(vw, __shfl_xor_sync(0xffffffffu, vw, o));
+    ve = fmaxf(ve, __shfl_xor_sync(0xffffffffu, ve, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&mx[4], __float_as_uint(vw));
+    atomicMax(&mx[5], __float_as_uint(ve));
+  }
+}
+
+// Rewrite only the columns that change between Sinkhorn iterations: for the
+// A side the bias constants c_w and the split shift; for the B side the split
+// bias and the shift constants c_e.
+template <class T>
+__global__ void tc_refresh_kernel(const float* h, const float* logw, const float* est,
+                                  int64_t rows_valid, TcOperandShape shp, int role, float inv_eps,
+                                  const unsigned* mx, T* op) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows_valid) return;
+  const float cw = pow2_scale(__uint_as_float(mx[4]));
+  const float ce = pow2_scale(__uint_as_float(mx[5]));
+  T* row = op + r * shp.KP;
+  if (role == 0) {
+    const float e = est ? (est[r] * inv_eps * kLog2e + kShiftBias) / ce : 0.0f;
+    for (int k = 0; k < 3; ++k) {
+      row[shp.col_w + k] = to16<T>(cw);
+      row[shp.col_e + k] = to16<T>(est ? split3<T>(e, k) : 0.0f);
+    }
+  } else {
+    const float w = (h[r] * inv_eps + logw[r]) * kLog2e;
+    const bool fin = isfinite(w);
+    for (int k = 0; k < 3; ++k) {
+      row[shp.col_w + k] = to16<T>(fin ? split3<T>(w / cw, k) : 0.0f);
+      row[shp.col_e + k] = to16<T>(ce);
+    }
+  }
+}
+
 struct TcTask {
   int64_t n, m;           // real rows / columns
   int ksteps;             // MMA K-steps of 16 that hold non-zero operand columns
@@ -746,9 +798,33 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     const bool use_est = all_est;
     int* flags = ws.take<int>(static_cast<size_t>(row_tiles[q]));
     GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
-    GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 8 * sizeof(unsigned), st));
     GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q], st));
     const float inv_eps = 1.0f / T.eps;
+    if (T.reuse_ops) {
+      // main, rank-one and mask columns are unchanged: refresh the rest
+      GW_CUDA_TRY(cudaMemsetAsync(mx + 4, 0, 2 * sizeof(unsigned), st));
+      tc_bias_absmax_kernel<<<kSmCount, 256, 0, st>>>(T.h, T.logw, T.m, use_est ? T.est : nullptr,
+                                                      T.n, inv_eps, mx);
+      GW_LAUNCH_CHECK();
+      if (bf16) {
+        tc_refresh_kernel<__nv_bfloat16><<<ceil_div(T.n, 256), 256, 0, st>>>(
+            nullptr, nullptr, use_est ? T.est : nullptr, T.n, shp, 0, inv_eps, mx,
+            reinterpret_cast<__nv_bfloat16*>(opA));
+        GW_LAUNCH_CHECK();
+        tc_refresh_kernel<__nv_bfloat16><<<ceil_div(T.m, 256), 256, 0, st>>>(
+            T.h, T.logw, nullptr, T.m, shp, 1, inv_eps, mx, reinterpret_cast<__nv_bfloat16*>(opB));
+        GW_LAUNCH_CHECK();
+      } else {
+        tc_refresh_kernel<__half><<<ceil_div(T.n, 256), 256, 0, st>>>(
+            nullptr, nullptr, use_est ? T.est : nullptr, T.n, shp, 0, inv_eps, mx,
+            reinterpret_cast<__half*>(opA));
+        GW_LAUNCH_CHECK();
+        tc_refresh_kernel<__half><<<ceil_div(T.m, 256), 256, 0, st>>>(
+            T.h, T.logw, nullptr, T.m, shp, 1, inv_eps, mx, reinterpret_cast<__half*>(opB));
+        GW_LAUNCH_CHECK();
+      }
+    } else {
+    GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 8 * sizeof(unsigned), st));
     tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
                                                    T.sB, T.m, T.h, T.logw,
                                                    use_est ? T.est : nullptr, inv_eps, mx);
@@ -774,6 +850,7 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
           T.B, T.sB, T.h, T.logw, nullptr, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
           reinterpret_cast<__half*>(opB));
       GW_LAUNCH_CHECK();
+    }
     }
     GW_TRY(make_map(&maps[2 * q], opA, n_pad, shp.KP, bf16, 128));
     GW_TRY(make_map(&maps[2 * q + 1], opB, m_pad, shp.KP, bf16, kBN));
