@@ -264,8 +264,8 @@ int gw_lift(const float* x, int64_t n, int d, const float* w, int kind, float pa
  *          - 16 Gamma_pi w_i - 8 q_i X_i,
  *   w_i = sum_j pi_ij Y_j, q_i = sum_j pi_ij t_j (pi from f, g on c_{Gamma_t}),
  *   then the adjoint of the centering, dX_i <- dX_i - a_i sum_k dX_k.
- *   If x != NULL (lifted features, Algorithm 11), additionally
- *   dx_i = sum_d dX_id grad_x Pi_d(x_i) with Kernel-Proj (Algorithm 12)
+ *   If x != NULL (lifted features, Algorithm 12), additionally
+ *   dx_i = sum_d dX_id grad_x Pi_d(x_i) with Kernel-Proj (Algorithm 13)
  *   frozen at the training points x (n x dx_dim), basis V (n x D) and
  *   eigvals Lambda (D), for the penalty (kind, param).
  *   For squared features (x == NULL) dx may equal NULL and dX is the answer.

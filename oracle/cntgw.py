@@ -176,7 +176,7 @@ def _centered_kernel_row(xq, x, a, kind, param):
 
 
 def kernel_proj(xq, x, a, V, lam, kind="power", param=1.0):
-    """Algorithm 12 (Kernel-Proj): Pi_X(xq)_d = Lambda_d^{-1/2}
+    """Algorithm 13 (Kernel-Proj): Pi_X(xq)_d = Lambda_d^{-1/2}
     sum_i k(xq, x_i) V_{id}, with k the centered kernel (the centering of a
     moving point is our reading: the paper is silent)."""
     k = _centered_kernel_row(xq, x, a, kind, param)
@@ -539,7 +539,7 @@ def grad_x_squared(pi, Gamma, X, Y, a, b):
 
 
 def grad_x_lifted(pi, Gamma, X, Y, a, b, x, V, lam, kind, param):
-    """Algorithm 11 (EGW-Grad with Kernel PCA): features X = center(Pi_X(x))
+    """Algorithm 12 (EGW-Grad with Kernel PCA): features X = center(Pi_X(x))
     with Kernel-Proj frozen at the training points, so
     grad_x = Pi_X'^T center^T grad_features.  X must be the re-centered
     Kernel-Proj features of x (equal to the Kernel PCA features at the

@@ -16,7 +16,7 @@ class GWEnergy(torch.autograd.Function):
 
     penalty = PEN_SQEUCLID: features are the centered points (D = d).
     Otherwise the features are Kernel PCA features of dimension D and the
-    gradient goes through Kernel-Proj (Algorithms 11-12)."""
+    gradient goes through Kernel-Proj (Algorithms 12-13)."""
 
     @staticmethod
     def forward(ctx, x, y, a, b, eps, n_outer, n_inner, penalty=PEN_SQEUCLID, param=2.0, D=None,

@@ -1,5 +1,5 @@
 // Gradient of the EGW energy with respect to the source points through the
-// converged plan (Appendix B.5, envelope theorem; Algorithms 10-12).
+// converged plan (Appendix B.5, envelope theorem; Algorithms 9-13).
 //
 // With pi held at the plan encoded by (f, g) on c_{Gamma_t} and Gamma_pi =
 // sum_ij pi_ij X_i Y_j^T, the Lemma (Appendix D) gives, per feature row,
@@ -8,8 +8,8 @@
 //   w_i = sum_j pi_ij Y_j,  q_i = sum_j pi_ij t_j,  mu3_X = sum_k a_k s_k X_k,
 // then the adjoint of the centering X = x - sum a x:
 //   dX_i <- dX_i - a_i sum_k dX_k.
-// For lifted features (Algorithm 11) the features of a moving point come
-// from Kernel-Proj (Algorithm 12) frozen at the training points, and
+// For lifted features (Algorithm 12) the features of a moving point come
+// from Kernel-Proj (Algorithm 13) frozen at the training points, and
 //   dx_i = sum_d dX_id grad_x Pi_d(x_i)
 //        = 1/2 [ -sum_k P_ik grad_1 c(x_i, x_k) + (sum_k P_ik) sum_l a_l grad_1 c(x_i, x_l) ],
 //   P_ik = sum_d dX_id V_kd / sqrt(Lambda_d),

@@ -432,7 +432,7 @@ def test_gradient_matches_finite_differences_of_resolved_energy():
 
 
 def test_lifted_gradient_matches_finite_differences():
-    """Algorithm 11: with Kernel-Proj frozen at the training points, the
+    """Algorithm 12: with Kernel-Proj frozen at the training points, the
     chained gradient equals the finite-difference derivative of
     x -> E(center(Pi(x)), Y)."""
     g = W.rng(95)
