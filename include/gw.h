@@ -276,6 +276,54 @@ int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double*
               float param, const float* basis, const float* eigvals, float* dX, float* dx,
               void* ws, size_t ws_bytes, gw_stream_t stream);
 
+/*
+ * Request server (continuous batching; no counterpart in the paper, which
+ * solves one problem at a time).  Requests are admitted in arrival order as
+ * soon as a worker slot is free and their device memory fits in the pool the
+ * caller gives at creation (the server allocates no device memory).  Each
+ * admitted request runs on its own stream: copy in, gw_lift, gw_solve as one
+ * CUDA graph, energy record out; admitted requests overlap on the device.
+ * Results are deterministic: the same request gives the same record alone
+ * or among others.  Weights are uniform.  Host arrays are copied at submit.
+ */
+typedef struct gw_server gw_server;
+
+typedef struct gw_request {
+  uint64_t id;          /* caller's tag, also seeds the Kernel PCA start block */
+  int64_t n, m;         /* source / target points */
+  int d;                /* point dimension (1..4) */
+  int kind;             /* GW_PEN_* */
+  float param;          /* penalty parameter */
+  int D;                /* feature dimension for lifted penalties */
+  float eps, eps_final; /* temperature schedule (eps_final <= 0: constant) */
+  int n_outer, n_inner;
+  int prec;             /* GW_PREC_* */
+} gw_request;
+
+typedef struct gw_response {
+  uint64_t id;
+  int status;                 /* GW_OK or an error code */
+  double energy[GW_EN_LEN];   /* energy record of the final plan */
+  double t_submit, t_admit, t_done;   /* seconds on a monotonic host clock */
+} gw_response;
+
+/* pool: 256-byte aligned device buffer owned by the caller; max_active:
+ * worker slots (1..256); device: CUDA ordinal the workers use.  NULL on error. */
+gw_server* gw_server_create(void* pool, size_t pool_bytes, int max_active, int device);
+/* Queue a request (h_x: n x d, h_y: m x d, host float32, copied).  GW_ENOMEM
+ * if the request can never fit in the pool. */
+int gw_server_submit(gw_server* s, const gw_request* r, const float* h_x, const float* h_y);
+/* Move up to max_out finished responses to out.  wait_ms: 0 = do not wait,
+ * < 0 = wait until one is ready or nothing is in flight, > 0 = bounded wait.
+ * Returns the number written. */
+int gw_server_poll(gw_server* s, gw_response* out, int max_out, int wait_ms);
+/* Device bytes the server reserves in its pool for this request. */
+size_t gw_server_request_bytes(const gw_request* r);
+/* Requests waiting for admission and requests running. */
+int gw_server_stats(gw_server* s, int* pending, int* active);
+/* Finish the running requests, drop the pending ones, free the server. */
+void gw_server_destroy(gw_server* s);
+
 /* Bytes of workspace `op` needs for these sizes (0 on invalid arguments). */
 size_t gw_workspace_size(int op, int64_t n, int64_t m, int D, int E, int prec);
 

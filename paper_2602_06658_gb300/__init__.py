@@ -20,7 +20,7 @@ __all__ = [
     "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
     "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
     "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
-    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc",
+    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server",
 ]
 
 GW_OK = 0
@@ -84,6 +84,30 @@ lib.gw_lift.argtypes = [_p, _i64, _int, _p, _int, _f, _int, _int, ctypes.c_uint6
                         _p, _sz, _p]
 lib.gw_grad_x.argtypes = [ctypes.POINTER(GwProblem), _p, _p, _p, _p, _f, _int, _p, _int, _int, _f,
                           _p, _p, _p, _p, _p, _sz, _p]
+class GwRequest(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("n", _i64), ("m", _i64), ("d", _int), ("kind", _int),
+                ("param", _f), ("D", _int), ("eps", _f), ("eps_final", _f), ("n_outer", _int),
+                ("n_inner", _int), ("prec", _int)]
+
+
+class GwResponse(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", _int), ("energy", ctypes.c_double * 16),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+lib.gw_server_create.argtypes = [_p, _sz, _int, _int]
+lib.gw_server_create.restype = _p
+lib.gw_server_submit.argtypes = [_p, ctypes.POINTER(GwRequest), _p, _p]
+lib.gw_server_submit.restype = _int
+lib.gw_server_poll.argtypes = [_p, ctypes.POINTER(GwResponse), _int, _int]
+lib.gw_server_poll.restype = _int
+lib.gw_server_stats.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_int)]
+lib.gw_server_stats.restype = _int
+lib.gw_server_request_bytes.argtypes = [ctypes.POINTER(GwRequest)]
+lib.gw_server_request_bytes.restype = _sz
+lib.gw_server_destroy.argtypes = [_p]
+lib.gw_server_destroy.restype = None
 lib.gw_workspace_size.argtypes = [_int, _i64, _i64, _int, _int, _int]
 lib.gw_workspace_size.restype = _sz
 lib.gw_last_error.restype = ctypes.c_char_p
@@ -291,3 +315,58 @@ def gw_grad_x(X, Y, s, t, a, b, f, g, Gamma_t, Gamma_pi, eps, prec=PREC_FP32, x=
                          _ptr(_f32(basis, "basis")), _ptr(_f32(eigvals, "eigvals")), _ptr(dX),
                          _ptr(dx), _ptr(ws), ws.numel(), _stream(stream)))
     return dX, dx
+
+
+class Server:
+    """Continuous-batching request server (gw_server_* in gw.h).  The device
+    pool is one caller-owned buffer; admission is by memory and slots."""
+
+    def __init__(self, pool_bytes: int, max_active: int = 4, device: int = 0):
+        import numpy as _np  # noqa: F401
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=f"cuda:{device}")
+        self.h = lib.gw_server_create(ctypes.c_void_p(self.pool.data_ptr()), int(pool_bytes),
+                                      int(max_active), int(device))
+        if not self.h:
+            raise GWError(GW_EINVAL_CODE, gw_last_error())
+
+    def submit(self, x, y, id, kind=PEN_SQEUCLID, param=2.0, D=0, eps=0.05, n_outer=10,
+               n_inner=50, prec=PREC_FP32, eps_final=0.0):
+        import numpy as np
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        r = GwRequest(int(id), x.shape[0], y.shape[0], x.shape[1], int(kind), float(param), int(D),
+                      float(eps), float(eps_final), int(n_outer), int(n_inner), int(prec))
+        _check(lib.gw_server_submit(self.h, ctypes.byref(r), x.ctypes.data_as(ctypes.c_void_p),
+                                    y.ctypes.data_as(ctypes.c_void_p)))
+
+    def poll(self, max_out: int = 64, wait_ms: int = 0):
+        buf = (GwResponse * max_out)()
+        k = lib.gw_server_poll(self.h, buf, max_out, int(wait_ms))
+        return [{"id": int(buf[i].id), "status": int(buf[i].status),
+                 "energy": list(buf[i].energy), "t_submit": buf[i].t_submit,
+                 "t_admit": buf[i].t_admit, "t_done": buf[i].t_done} for i in range(k)]
+
+    @staticmethod
+    def request_bytes(n, m, d=3, kind=PEN_SQEUCLID, D=0, prec=PREC_FP32, param=2.0):
+        r = GwRequest(0, int(n), int(m), int(d), int(kind), float(param), int(D), 0.1, 0.0, 1, 1,
+                      int(prec))
+        return int(lib.gw_server_request_bytes(ctypes.byref(r)))
+
+    def stats(self):
+        p, a = _int(0), _int(0)
+        lib.gw_server_stats(self.h, ctypes.byref(p), ctypes.byref(a))
+        return {"pending": p.value, "active": a.value}
+
+    def close(self):
+        if self.h:
+            lib.gw_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+GW_EINVAL_CODE = 1

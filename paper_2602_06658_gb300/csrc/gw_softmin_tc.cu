@@ -704,11 +704,12 @@ template <int KP, int S, bool BF16, bool FAST>
 int launch_tc_kernel(const CUtensorMap* maps, const TcTask& a, const TcTask& b, cudaStream_t st) {
   using L = TcSmem<KP, S>;
   auto kern = softmin_tc_kernel<KP, S, BF16, FAST>;
-  static bool attr_set = false;  // set once per process (same value every time)
-  if (!attr_set) {
-    GW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
-    attr_set = true;
-  }
+  static std::once_flag once;   // the attribute is the same for every call
+  static cudaError_t attr_rc = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_rc = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+  });
+  GW_CUDA_TRY(attr_rc);
   kern<<<a.blocks + b.blocks, kThreadsTc, L::kBytes, st>>>(maps[0], maps[1], maps[2], maps[3], a, b);
   GW_LAUNCH_CHECK();
   return GW_OK;

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "gw.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:int|size_t|unsigned long long|const char\s*\*)\s+(gw_\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:int|void|size_t|unsigned long long|const char\s*\*|gw_server\s*\*)\s+(gw_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 

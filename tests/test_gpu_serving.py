@@ -1,0 +1,97 @@
+"""Request server: continuous batching, memory-based admission, and the same
+result for a request alone and in the mix."""
+
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def make_request(rid, n, m, kind, D, eps, seed):
+    w = W.gmm_rigid(n, seed=seed, m=m)
+    return dict(x=w["x"], y=w["y"], id=rid, kind=kind, param=1.0 if kind == 1 else 2.0,
+                D=D if kind == 1 else 0, eps=eps, n_outer=6, n_inner=30, prec=3)
+
+
+def run_all(srv, reqs, gap_s=0.0):
+    for r in reqs:
+        srv.submit(**r)
+        if gap_s:
+            time.sleep(gap_s)
+    out = {}
+    t_end = time.time() + 600
+    while len(out) < len(reqs) and time.time() < t_end:
+        for res in srv.poll(64, wait_ms=200):
+            out[res["id"]] = res
+    assert len(out) == len(reqs)
+    return out
+
+
+def test_result_is_the_same_alone_and_in_the_mix(gw):
+    probe = make_request(1000, 3000, 2500, 1, 16, 0.02, seed=11)
+    g = W.rng(5)
+    others = []
+    for k in range(14):
+        n, m = (int(v) for v in np.exp(g.uniform(np.log(500), np.log(6000), 2)))
+        kind = int(g.integers(0, 2))
+        others.append(make_request(k, n, m, kind, 16 if kind else 0,
+                                   float(np.exp(g.uniform(np.log(1e-2), np.log(1e-1)))), seed=100 + k))
+    srv = gw.Server(pool_bytes=6 << 30, max_active=4)
+    try:
+        alone = run_all(srv, [probe])[1000]
+        mixed = run_all(srv, others[:7] + [probe] + others[7:], gap_s=0.01)
+    finally:
+        srv.close()
+    assert alone["status"] == 0 and mixed[1000]["status"] == 0
+    assert alone["energy"][0] == mixed[1000]["energy"][0]   # bitwise: deterministic kernels
+    for rid, res in mixed.items():
+        assert res["status"] == 0, rid
+        assert np.isfinite(res["energy"][0]), rid
+        assert res["t_submit"] <= res["t_admit"] <= res["t_done"]
+
+
+def test_server_matches_a_direct_solve(gw):
+    import torch
+    req = make_request(7, 1200, 900, 0, 0, 0.05, seed=3)
+    srv = gw.Server(pool_bytes=1 << 30, max_active=2)
+    try:
+        res = run_all(srv, [req])[7]
+    finally:
+        srv.close()
+    dev = lambda v: torch.tensor(np.asarray(v, np.float32), device="cuda")
+    a = torch.full((1200,), 1 / 1200, device="cuda")
+    b = torch.full((900,), 1 / 900, device="cuda")
+    lx = gw.gw_lift(dev(req["x"]), 3, w=a)
+    ly = gw.gw_lift(dev(req["y"]), 3, w=b)
+    out = gw.gw_solve(lx["X"], ly["X"], lx["s"], ly["s"], a, b, 0.05, 6, 30, prec=3, record=False)
+    assert out["energy"][0].item() == res["energy"][0]
+
+
+def test_admission_respects_memory_and_rejects_oversized(gw):
+    req = make_request(1, 2000, 2000, 1, 16, 0.05, seed=1)
+    need = gw.Server.request_bytes(2000, 2000, 3, 1, 16, 3, 1.0)
+    srv = gw.Server(pool_bytes=int(1.5 * need) // 256 * 256, max_active=4)   # one at a time
+    try:
+        for k in range(3):
+            r = dict(req)
+            r["id"] = k
+            srv.submit(**r)
+        seen_active = 0
+        out = {}
+        t_end = time.time() + 300
+        while len(out) < 3 and time.time() < t_end:
+            seen_active = max(seen_active, srv.stats()["active"])
+            for res in srv.poll(8, wait_ms=20):
+                out[res["id"]] = res
+        assert len(out) == 3 and seen_active <= 1
+        assert len({r["energy"][0] for r in out.values()}) == 1   # the same request, same answer
+        big = make_request(9, 60000, 60000, 1, 32, 0.05, seed=2)
+        with pytest.raises(gw.GWError) as e:
+            srv.submit(**big)
+        assert e.value.code == 2
+    finally:
+        srv.close()
