@@ -88,7 +88,10 @@ def test_admission_respects_memory_and_rejects_oversized(gw):
             for res in srv.poll(8, wait_ms=20):
                 out[res["id"]] = res
         assert len(out) == 3 and seen_active <= 1
-        assert len({r["energy"][0] for r in out.values()}) == 1   # the same request, same answer
+        # the same clouds under different ids (the id seeds the Kernel PCA start
+        # block): equal within the stated 1e-4 energy tolerance
+        E = [r["energy"][0] for r in out.values()]
+        assert max(E) - min(E) <= 1e-4 * abs(E[0])
         big = make_request(9, 60000, 60000, 1, 32, 0.05, seed=2)
         with pytest.raises(gw.GWError) as e:
             srv.submit(**big)
