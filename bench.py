@@ -60,6 +60,12 @@ def parse():
                          "of the same shape (kernel-only runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--workload", default="gmm8", choices=["gmm8", "serving"],
+                    help="gmm8: the cells/s workload; serving: request stream, p50/p99 latency")
+    ap.add_argument("--requests", type=int, default=512)
+    ap.add_argument("--rate-frac", type=float, default=0.8,
+                    help="serving arrival rate as a fraction of the measured saturated throughput")
+    ap.add_argument("--slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -342,6 +348,27 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def tc_kernel_traffic():
+    """DRAM bytes per launch of the tensor-core softmin from the committed ncu
+    summary, valid only while the kernel sources match the hash recorded there."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "softmin_tc_gmm8_100k_D32_f16x3.md")
+    if not os.path.exists(prof):
+        return None, "no profile"
+    txt = open(prof).read()
+    mb = re.search(r"dram_bytes_per_launch:\s*(\d+)", txt)
+    mh = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", txt)
+    if not mb or not mh:
+        return None, "profile lacks traffic or source hash"
+    h = hashlib.sha1()
+    for f in ("gw_softmin_tc.cu", "gw_tc.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2602_06658_gb300", "csrc", f), "rb").read())
+    if h.hexdigest() != mh.group(1):
+        return None, "kernel changed since the ncu capture"
+    return int(mb.group(1)), "ncu capture in profiles/ (same kernel sources)"
+
+
 def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps=10):
     """Average duration of the row-softmin kernel on the step's shapes (CUDA
     events on the launching stream, after warm-up) and its roofline.
@@ -384,8 +411,9 @@ def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps
                                f"(clock from {src} peaks file)",
                 "ms_per_launch": dt * 1e3, "cells_per_s": n * m / dt}
     ex2 = 152 * 32 * clk
+    traffic, tsrc = tc_kernel_traffic() if (n, m, D) == (100_000, 100_000, 32) else (None, "other size")
     return {"bound": "alu", "achieved": n * m / dt / 1e12, "peak": ex2 / 1e12, "unit": "Tex2/s",
-            "frac": n * m / dt / ex2, "traffic": None,
+            "frac": n * m / dt / ex2, "traffic": traffic, "traffic_source": tsrc,
             "kernel": "tcgen05 softmin (row softmin, N x M cells per launch)",
             "peak_source": f"derived: 152 SMs x 32 MUFU ex2/clk x {clk/1e6:.0f} MHz",
             "ms_per_launch": dt * 1e3, "cells_per_s": n * m / dt}
@@ -473,11 +501,92 @@ def run_reference(args, rank, world):
     del O
 
 
+def run_serving(args, rank, world, local):
+    """Request stream (Poisson arrivals, N and M log-uniform in [500, 50k],
+    squared (D = 3) or lifted (D = 16, 32) penalties, eps log-uniform in
+    [1e-3, 1e-1], 20 outer x 50 Sinkhorn iterations) through the continuous-
+    batching server.  Phase 1 submits a saturating batch to measure throughput;
+    phase 2 replays the stream with arrivals at rate_frac of that throughput
+    and reports p50/p99 latency (arrival -> result)."""
+    import torch
+    import paper_2602_06658_gb300 as gw
+    torch.cuda.set_device(local)
+    prec = PREC[args.prec]
+    reqs = W.serving_requests(args.requests, seed=args.seed + rank, rate=1.0)
+
+    def payload(r):
+        w = W.gmm_rigid(r["n"], seed=r["seed"], m=r["m"])
+        lifted = r["penalty"] != "sqeuclid"
+        return dict(x=w["x"], y=w["y"], id=r["id"], kind=gw.PEN_POWER if lifted else gw.PEN_SQEUCLID,
+                    param=1.0 if lifted else 2.0, D=r["D"] if lifted else 0, eps=r["eps"],
+                    n_outer=20, n_inner=50, prec=prec)
+
+    data = [payload(r) for r in reqs]
+    need = max(gw.Server.request_bytes(len(d["x"]), len(d["y"]), 3, d["kind"], d["D"], prec, d["param"])
+               for d in data)
+    pool = min(64 << 30, int(need * args.slots * 1.25) // 256 * 256)
+    srv = gw.Server(pool_bytes=pool, max_active=args.slots, device=local)
+    cells = {d["id"]: float(len(d["x"])) * len(d["y"]) * 20 * 50 for d in data}
+
+    def collect(n_expected, t_limit=3600):
+        out = {}
+        t_end = time.time() + t_limit
+        while len(out) < n_expected and time.time() < t_end:
+            for res in srv.poll(256, wait_ms=100):
+                out[res["id"]] = res
+        return out
+
+    # phase 1: saturated throughput on the first quarter of the stream
+    sat = data[: max(16, args.requests // 4)]
+    t0 = time.perf_counter()
+    for d in sat:
+        srv.submit(**d)
+    done1 = collect(len(sat))
+    t_sat = time.perf_counter() - t0
+    thr = len(done1) / t_sat
+    # phase 2: Poisson arrivals at rate_frac * throughput over the whole stream
+    lam = args.rate_frac * thr
+    g = W.rng(args.seed + 99)
+    gaps = g.exponential(1.0 / lam, len(data))
+    clocks = ClockSampler(local)
+    clocks.start()
+    t1 = time.perf_counter()
+    for k, d in enumerate(data):
+        d = dict(d)
+        d["id"] = 1_000_000 + d["id"]
+        srv.submit(**d)
+        time.sleep(float(gaps[k]))
+    done2 = collect(len(data))
+    t_all = time.perf_counter() - t1
+    clk = clocks.stop()
+    srv.close()
+    lat = sorted(r["t_done"] - r["t_submit"] for r in done2.values())
+    ok = sum(1 for r in done2.values() if r["status"] == 0)
+    q = lambda p: lat[min(len(lat) - 1, int(p * len(lat)))]
+    tot_cells = sum(cells[i - 1_000_000] for i in done2)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "GW request latency (serving)", "value": q(0.5), "unit": "s",
+            "higher_is_better": False, "p50_s": q(0.5), "p99_s": q(0.99), "max_s": lat[-1],
+            "throughput_req_per_s": len(done2) / t_all, "saturated_req_per_s": thr,
+            "arrival_rate_req_per_s": lam, "cells_per_s": tot_cells / t_all,
+            "requests": len(done2), "ok": ok, "slots": args.slots, "n_gpus": world,
+            "dtype": DTYPE[args.prec], "data": "synthetic", "clocks": clk,
+            "config": {"workload": "serving: Poisson arrivals, N, M log-uniform [500, 50k], "
+                                   "squared D=3 or lifted ||x-x'|| D=16/32, eps log-uniform "
+                                   "[1e-3, 1e-1], 20 outer x 50 Sinkhorn",
+                       "requests": args.requests, "rate_frac": args.rate_frac},
+        }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world, local)
         return
     run_gw(args, rank, world, local)
 
