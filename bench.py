@@ -60,8 +60,10 @@ def parse():
                          "of the same shape (kernel-only runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
-    ap.add_argument("--workload", default="gmm8", choices=["gmm8", "serving"],
-                    help="gmm8: the cells/s workload; serving: request stream, p50/p99 latency")
+    ap.add_argument("--workload", default="gmm8", choices=["gmm8", "sphere", "serving"],
+                    help="gmm8: the cells/s workload; sphere: unit sphere vs a smooth warp "
+                         "(use with --n 250000 --D 64 --eps1 5e-4); serving: request stream, "
+                         "p50/p99 latency")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate-frac", type=float, default=0.8,
                     help="serving arrival rate as a fraction of the measured saturated throughput")
@@ -77,7 +79,8 @@ def eps_at(args, t):
 
 
 def workload_name(args):
-    return (f"gmm8-3d N=M={args.n} ||x-x'|| Kernel-PCA D=E={args.D}, eps {args.eps0:g}->{args.eps1:g} "
+    shape = "sphere-vs-warp" if args.workload == "sphere" else "gmm8-3d"
+    return (f"{shape} N=M={args.n} ||x-x'|| Kernel-PCA D=E={args.D}, eps {args.eps0:g}->{args.eps1:g} "
             f"geometric over {args.n_outer} outer x {args.n_inner} symmetric Sinkhorn")
 
 
@@ -199,7 +202,7 @@ def run_cpu_baseline(X, Y, a, b, eps, target_s=12.0, seed=0):
 
 # ---------------------------------------------------------------- workload
 def make_features(args, gw, torch, dev, seed):
-    w = W.gmm_rigid(args.n, seed)
+    w = W.sphere_warp(args.n, seed) if args.workload == "sphere" else W.gmm_rigid(args.n, seed)
     a = torch.tensor(w["a"], dtype=torch.float32, device=dev)
     b = torch.tensor(w["b"], dtype=torch.float32, device=dev)
     if args.features == "random":

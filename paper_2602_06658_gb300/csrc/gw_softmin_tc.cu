@@ -48,7 +48,9 @@ namespace gw {
 namespace {
 
 constexpr int kBM = 256;       // rows per CTA (two M = 128 halves)
-constexpr int kBN = 128;       // columns per tile
+// columns per tile: 128, or 64 for the widest operands (KP = 256) so that the
+// ring still fits in shared memory
+__host__ __device__ constexpr int tile_cols(int KP) { return KP >= 256 ? 64 : 128; }
 constexpr int kEpiWarps = 16;  // 4 per scheduler: 2 per (half, lane quarter), one per column half
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 constexpr float kBiasConst = 32768.0f;       // A-side multiplier of the bias columns
@@ -291,11 +293,12 @@ struct TcTask {
   float* ps;
 };
 
-template <int KP, int S>
+template <int KP, int S, int BN>
 struct TcSmem {
   static constexpr int KB = KP / 64;
   static constexpr int kABytes = 2 * KB * 16384;          // 256 rows
-  static constexpr int kStageBytes = KB * 16384;          // 128 rows
+  static constexpr int kBBlock = BN * 128;                // one 64-wide K-block of a B tile
+  static constexpr int kStageBytes = KB * kBBlock;
   static constexpr int kBarOff = kABytes + S * kStageBytes;
   // + barriers and the row-merge buffers (3 x 256 words) + alignment slack;
   // at least 120 KB so that one CTA owns the SM (it allocates all 512 TMEM
@@ -386,13 +389,14 @@ __device__ __forceinline__ void chunk(const uint32_t (&r)[32], float& shift, flo
   }
 }
 
-template <int KP, int S, bool BF16, bool FAST>
+template <int KP, int S, int BN, bool BF16, bool FAST>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     softmin_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mB0,
                       const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mB1,
                       TcTask t0, TcTask t1) {
-  using L = TcSmem<KP, S>;
+  using L = TcSmem<KP, S, BN>;
   constexpr int KB = L::KB;
+  constexpr int kTmemCols = 4 * BN;   // 2 buffers x 2 halves
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     tc::fence_mbar_init();
   }
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 512);
+    tc::tmem_alloc(&tmem_base, kTmemCols);
     tc::tmem_relinquish();
   }
   tc::tc_fence_before();
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (!tc::mbar_wait(&empty[s], ((t / S) & 1) ^ 1, ab)) break;
         tc::mbar_arrive_expect_tx(&full[s], L::kStageBytes);
         for (int kb = 0; kb < KB; ++kb)
-          tc::tma_load_2d(Bs + s * L::kStageBytes + kb * 16384, mB, kb * 64, (tile0 + t) * kBN,
+          tc::tma_load_2d(Bs + s * L::kStageBytes + kb * L::kBBlock, mB, kb * 64, (tile0 + t) * BN,
                           &full[s]);
         issued = t + 1;
       }
@@ -477,7 +481,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------------- MMA issuer
-      const uint32_t idesc = tc::f16_idesc(128, kBN, BF16);
+      const uint32_t idesc = tc::f16_idesc(128, BN, BF16);
       bool ok = tc::mbar_wait(afull, 0, ab);
       for (int t = 0; ok && t < ntiles; ++t) {
         const int s = t % S, b = t & 1;
@@ -492,8 +496,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           for (int ks = 0; ks < KP / 16; ++ks) {
             if (ks >= nks) break;   // the rest of the operand row is zero padding
             const uint32_t aaddr = tc::smem_u32(As + (h * KB + ks / 4) * 16384 + (ks % 4) * 32);
-            const uint32_t baddr = tc::smem_u32(Bst + (ks / 4) * 16384 + (ks % 4) * 32);
-            tc::mma_f16(tbase + (b * 2 + h) * 128, tc::sw128_desc(aaddr), tc::sw128_desc(baddr),
+            const uint32_t baddr = tc::smem_u32(Bst + (ks / 4) * L::kBBlock + (ks % 4) * 32);
+            tc::mma_f16(tbase + (b * 2 + h) * BN, tc::sw128_desc(aaddr), tc::sw128_desc(baddr),
                         idesc, ks > 0 ? 1u : 0u);
           }
         }
@@ -530,16 +534,23 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       }
       tc::tc_fence_after();
       const uint32_t tcol =
-          tbase + (static_cast<uint32_t>(q * 32) << 16) + (b * 2 + h) * 128 + ch * 64;
-      // two chunks of 32 columns, the second load in flight while the first
-      // is reduced
-      uint32_t ra[32], rb[32];
-      tc::tmem_ld32_issue(tcol, ra);
-      tc::tmem_ld_wait(ra);
-      tc::tmem_ld32_issue(tcol + 32, rb);
-      chunk<FAST>(ra, mrun, srun);
-      tc::tmem_ld_wait(rb);
-      chunk<FAST>(rb, mrun, srun);
+          tbase + (static_cast<uint32_t>(q * 32) << 16) + (b * 2 + h) * BN + ch * (BN / 2);
+      uint32_t ra[32];
+      if constexpr (BN == 128) {
+        // two chunks of 32 columns, the second load in flight while the first
+        // is reduced
+        uint32_t rb[32];
+        tc::tmem_ld32_issue(tcol, ra);
+        tc::tmem_ld_wait(ra);
+        tc::tmem_ld32_issue(tcol + 32, rb);
+        chunk<FAST>(ra, mrun, srun);
+        tc::tmem_ld_wait(rb);
+        chunk<FAST>(rb, mrun, srun);
+      } else {
+        tc::tmem_ld32_issue(tcol, ra);
+        tc::tmem_ld_wait(ra);
+        chunk<FAST>(ra, mrun, srun);
+      }
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
@@ -610,7 +621,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   if (warp == 0) {
     __syncwarp();
     tc::tc_fence_after();
-    tc::tmem_dealloc(tbase, 512);
+    tc::tmem_dealloc(tbase, kTmemCols);
   }
 }
 
@@ -702,8 +713,9 @@ int tc_splits(int row_tiles, int col_tiles, int other_blocks) {
 
 template <int KP, int S, bool BF16, bool FAST>
 int launch_tc_kernel(const CUtensorMap* maps, const TcTask& a, const TcTask& b, cudaStream_t st) {
-  using L = TcSmem<KP, S>;
-  auto kern = softmin_tc_kernel<KP, S, BF16, FAST>;
+  constexpr int BN = tile_cols(KP);
+  using L = TcSmem<KP, S, BN>;
+  auto kern = softmin_tc_kernel<KP, S, BN, BF16, FAST>;
   static std::once_flag once;   // the attribute is the same for every call
   static cudaError_t attr_rc = cudaSuccess;
   std::call_once(once, [&] {
@@ -721,6 +733,7 @@ int dispatch_tc(int KP, const CUtensorMap* maps, const TcTask& a, const TcTask& 
     case 64: return launch_tc_kernel<64, 4, BF16, FAST>(maps, a, b, st);
     case 128: return launch_tc_kernel<128, 3, BF16, FAST>(maps, a, b, st);
     case 192: return launch_tc_kernel<192, 2, BF16, FAST>(maps, a, b, st);
+    case 256: return launch_tc_kernel<256, 2, BF16, FAST>(maps, a, b, st);
     default: break;
   }
   set_error("tensor-core softmin: operand width %d (K too large for this precision)", KP);
@@ -739,19 +752,20 @@ int run_tc(bool bf16, bool fast, int KP, const CUtensorMap* maps, const TcTask& 
 
 bool softmin_tc_supported(int K, int prec) {
   if (prec != GW_PREC_BF16 && prec != GW_PREC_BF16X3 && prec != GW_PREC_F16X3) return false;
-  return tc_shape(K, prec).KP <= 192;
+  return tc_shape(K, prec).KP <= 256;
 }
 
 size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
   const TcOperandShape shp = tc_shape(K, prec);
   const int64_t n_pad = ((n + kBM - 1) / kBM) * kBM;
-  const int64_t m_pad = ((m + kBN - 1) / kBN) * kBN;
+  const int bn = tile_cols(shp.KP);
+  const int64_t m_pad = ((m + bn - 1) / bn) * bn;
   Carver c(nullptr, ~size_t(0));
   c.take<uint16_t>(static_cast<size_t>(n_pad) * shp.KP);
   c.take<uint16_t>(static_cast<size_t>(m_pad) * shp.KP);
   c.take<unsigned>(8);
   // partials for the largest split count any launch may pick
-  const int s = max_splits(static_cast<int>(m_pad / kBN));
+  const int s = max_splits(static_cast<int>(m_pad / bn));
   c.take<float>(static_cast<size_t>(s) * n);
   c.take<float>(static_cast<size_t>(s) * n);
   c.take<int>(static_cast<size_t>(n_pad / kBM));       // recompute flags per row tile
@@ -771,7 +785,7 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
   int row_tiles[2] = {0, 0}, col_tiles[2] = {0, 0};
   for (int q = 0; q < ntasks; ++q) {
     row_tiles[q] = ceil_div(tasks[q].n, kBM);
-    col_tiles[q] = ceil_div(tasks[q].m, kBN);
+    col_tiles[q] = ceil_div(tasks[q].m, tile_cols(shp.KP));
   }
   // the fast pass needs an estimate for every task (not aliased to the output)
   bool all_est = true;
@@ -782,7 +796,7 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
   for (int q = 0; q < ntasks; ++q) {
     SoftminTask& T = tasks[q];
     const int64_t n_pad = static_cast<int64_t>(row_tiles[q]) * kBM;
-    const int64_t m_pad = static_cast<int64_t>(col_tiles[q]) * kBN;
+    const int64_t m_pad = static_cast<int64_t>(col_tiles[q]) * tile_cols(shp.KP);
     uint16_t* opA = ws.take<uint16_t>(static_cast<size_t>(n_pad) * shp.KP);
     uint16_t* opB = ws.take<uint16_t>(static_cast<size_t>(m_pad) * shp.KP);
     unsigned* mx = ws.take<unsigned>(8);
@@ -790,7 +804,7 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     const int tps = ceil_div(col_tiles[q], s);
     s = ceil_div(col_tiles[q], tps);
     T.splits = s;
-    T.cols_per_split = tps * kBN;
+    T.cols_per_split = tps * tile_cols(shp.KP);
     T.pm = T.ps = nullptr;
     if (s > 1) {
       T.pm = ws.take<float>(static_cast<size_t>(s) * T.n);
@@ -854,7 +868,7 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     }
     }
     GW_TRY(make_map(&maps[2 * q], opA, n_pad, shp.KP, bf16, 128));
-    GW_TRY(make_map(&maps[2 * q + 1], opB, m_pad, shp.KP, bf16, kBN));
+    GW_TRY(make_map(&maps[2 * q + 1], opB, m_pad, shp.KP, bf16, tile_cols(shp.KP)));
     TcTask& K = tt[q];
     K.n = T.n;
     K.m = T.m;

@@ -130,3 +130,23 @@ def test_config1_end_to_end_tensor_core(gw, cfg1_oracle, prec):
     row, col = gpu_marginals(gw, P, out)
     assert np.max(np.abs(row - last["row"]) / P["a"]) <= 1e-3
     assert np.max(np.abs(col - last["col"]) / P["b"]) <= 1e-3
+
+
+@pytest.mark.parametrize("D,prec", [(64, 3), (64, 0), (32, 2)])
+def test_solve_wide_features_tensor_core(gw, D, prec):
+    """D = 64 (the widest configuration: 64-column tiles, K' = 256 in the
+    split modes) and BF16X3 at D = 32, against the oracle step by step."""
+    g = W.rng(321 + D)
+    n, m = 700, 650
+    a, b = r32(W.uniform_weights(n)), r32(W.uniform_weights(m))
+    X = g.standard_normal((n, D)) * (0.6 / np.sqrt(D))
+    Y = g.standard_normal((m, D)) * (0.6 / np.sqrt(D))
+    X, Y = r32(X - a @ X), r32(Y - b @ Y)
+    s, t = r32((X * X).sum(1)), r32((Y * Y).sum(1))
+    G0 = 0.2 * g.standard_normal((D, D)) / D
+    res = O.cnt_gw(a, b, X, Y, 0.05, 4, 40, Gamma0=G0, eps_final=0.01, symmetric=True)
+    out = gw.gw_solve(f32(X), f32(Y), f32(s), f32(t), f32(a), f32(b), 0.05, 4, 40, eps_final=0.01,
+                      Gamma0=f64(G0), prec=prec)
+    hist = host(out["history"])
+    for k, h in enumerate(res["history"]):
+        assert abs(hist[k, gw.EN["E"]] - h["E"]) <= 1e-4 * abs(h["E"]), (k, hist[k, 0], h["E"])
