@@ -362,37 +362,7 @@ __device__ __forceinline__ void lse_chunk(const uint32_t (&r)[32], float& shift,
   sum += acc;
 }
 
-// exp2 of a pair on the FMA pipe instead of MUFU (the coefficients and the
-// method are in exp2_poly.py): n = round(x) by the 1.5 * 2^23 shift,
-// f = x - n in [-1/2, 1/2], the degree-5 Chebyshev interpolant of 2^f in
-// packed FP32x2 Horner steps, then n added to the exponent field.  x is
-// clamped to [-126, 126]; the fast pass already rejects any row whose sum
-// leaves (2^-60, 2^120), so the clamp never changes a kept result.
-__device__ __forceinline__ uint64_t exp2_fma_pair(float x0, float x1) {
-  x0 = fminf(fmaxf(x0, -126.0f), 126.0f);
-  x1 = fminf(fmaxf(x1, -126.0f), 126.0f);
-  const float kShift = 12582912.0f;   // 1.5 * 2^23: x + kShift rounds x to an integer
-  const uint64_t X = tc::pack2(x0, x1);
-  const uint64_t Tt = tc::add2(X, tc::pack2(kShift, kShift));
-  const uint64_t Nn = tc::add2(Tt, tc::pack2(-kShift, -kShift));
-  const uint64_t F = tc::fma2(Nn, tc::pack2(-1.0f, -1.0f), X);
-  uint64_t P = tc::pack2(0.0013390863f, 0.0013390863f);
-  P = tc::fma2(P, F, tc::pack2(0.009676032f, 0.009676032f));
-  P = tc::fma2(P, F, tc::pack2(0.05550357f, 0.05550357f));
-  P = tc::fma2(P, F, tc::pack2(0.24022107f, 0.24022107f));
-  P = tc::fma2(P, F, tc::pack2(0.6931472f, 0.6931472f));
-  P = tc::fma2(P, F, tc::pack2(1.0000001f, 1.0000001f));
-  float p0, p1, t0, t1;
-  tc::unpack2(P, p0, p1);
-  tc::unpack2(Tt, t0, t1);
-  const int n0 = __float_as_int(t0) - 0x4B400000;
-  const int n1 = __float_as_int(t1) - 0x4B400000;
-  return tc::pack2(__int_as_float(__float_as_int(p0) + (n0 << 23)),
-                   __int_as_float(__float_as_int(p1) + (n1 << 23)));
-}
-
-// Fast pass: the 32 values are already shifted; just sum their exp2.  One
-// value in four goes to the FMA pipe, which relieves the MUFU/MIO queue.
+// Fast pass: the 32 values are already shifted; just sum their exp2.
 __device__ __forceinline__ float exp2_sum32_noshift(const float (&v)[32]) {
   uint64_t acc0 = tc::pack2(0.f, 0.f), acc1 = acc0, acc2 = acc0, acc3 = acc0;
 #pragma unroll
@@ -400,7 +370,7 @@ __device__ __forceinline__ float exp2_sum32_noshift(const float (&v)[32]) {
     acc0 = tc::add2(acc0, tc::pack2(ex2(v[k]), ex2(v[k + 1])));
     acc1 = tc::add2(acc1, tc::pack2(ex2(v[k + 2]), ex2(v[k + 3])));
     acc2 = tc::add2(acc2, tc::pack2(ex2(v[k + 4]), ex2(v[k + 5])));
-    acc3 = tc::add2(acc3, exp2_fma_pair(v[k + 6], v[k + 7]));
+    acc3 = tc::add2(acc3, tc::pack2(ex2(v[k + 6]), ex2(v[k + 7])));
   }
   float s0, s1;
   tc::unpack2(tc::add2(tc::add2(acc0, acc1), tc::add2(acc2, acc3)), s0, s1);
