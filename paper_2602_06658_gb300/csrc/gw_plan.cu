@@ -28,6 +28,20 @@ int dpad(int D) {
   return 128;
 }
 
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+  uint64_t p;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(lo), "f"(hi));
+  return p;
+}
+__device__ __forceinline__ void upk2(uint64_t p, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+__device__ __forceinline__ uint64_t fm2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 struct ColSumArgs {
   const float* X;  // n x D
   const float* s;
@@ -66,9 +80,9 @@ __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
   const float tj = colok ? P.t[j] : 0.0f;
   const float cb = colok ? P.g[j] * hs + log2f(P.b[j]) : kNegBig;
 
-  float acc[DP];
+  uint64_t acc2[DP / 2];
 #pragma unroll
-  for (int k = 0; k < DP; ++k) acc[k] = 0.0f;
+  for (int k = 0; k < DP / 2; ++k) acc2[k] = pk2(0.0f, 0.0f);
   float acc_s = 0.0f, acc_1 = 0.0f;
 
   const int64_t r_begin = static_cast<int64_t>(blockIdx.y) * P.rows_per_split;
@@ -93,26 +107,27 @@ __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
       }
     }
     __syncthreads();
+    // packed FP32x2 arithmetic: the dot product and the accumulation both
+    // run as fma.rn.f32x2 on feature pairs
 #pragma unroll 2
     for (int ii = 0; ii < kBR; ++ii) {
       const float4* xr = reinterpret_cast<const float4*>(&Xs[ii][0]);
-      float z = fmaf(us[ii], tj, rb[ii] + cb);
+      uint64_t z2 = pk2(fmaf(us[ii], tj, rb[ii] + cb), 0.0f);
 #pragma unroll
       for (int k4 = 0; k4 < DP / 4; ++k4) {
         const float4 xv = xr[k4];
-        z = fmaf(v[4 * k4 + 0], xv.x, z);
-        z = fmaf(v[4 * k4 + 1], xv.y, z);
-        z = fmaf(v[4 * k4 + 2], xv.z, z);
-        z = fmaf(v[4 * k4 + 3], xv.w, z);
+        z2 = fm2(pk2(v[4 * k4 + 0], v[4 * k4 + 1]), pk2(xv.x, xv.y), z2);
+        z2 = fm2(pk2(v[4 * k4 + 2], v[4 * k4 + 3]), pk2(xv.z, xv.w), z2);
       }
-      const float p = ex2(fminf(z, 126.0f));
+      float z0, z1;
+      upk2(z2, z0, z1);
+      const float p = ex2(fminf(z0 + z1, 126.0f));
+      const uint64_t pp = pk2(p, p);
 #pragma unroll
       for (int k4 = 0; k4 < DP / 4; ++k4) {
         const float4 xv = xr[k4];
-        acc[4 * k4 + 0] = fmaf(p, xv.x, acc[4 * k4 + 0]);
-        acc[4 * k4 + 1] = fmaf(p, xv.y, acc[4 * k4 + 1]);
-        acc[4 * k4 + 2] = fmaf(p, xv.z, acc[4 * k4 + 2]);
-        acc[4 * k4 + 3] = fmaf(p, xv.w, acc[4 * k4 + 3]);
+        acc2[2 * k4 + 0] = fm2(pp, pk2(xv.x, xv.y), acc2[2 * k4 + 0]);
+        acc2[2 * k4 + 1] = fm2(pp, pk2(xv.z, xv.w), acc2[2 * k4 + 1]);
       }
       acc_s = fmaf(p, ss[ii], acc_s);
       acc_1 += p;
@@ -121,8 +136,12 @@ __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
   if (!colok) return;
   float* out = P.Wp + (static_cast<int64_t>(blockIdx.y) * P.m + j) * (P.D + 2);
 #pragma unroll
-  for (int k = 0; k < DP; ++k)
-    if (k < P.D) out[k] = acc[k];
+  for (int k = 0; k < DP / 2; ++k) {
+    float lo, hi;
+    upk2(acc2[k], lo, hi);
+    if (2 * k < P.D) out[2 * k] = lo;
+    if (2 * k + 1 < P.D) out[2 * k + 1] = hi;
+  }
   out[P.D] = acc_s;
   out[P.D + 1] = acc_1;
 }
