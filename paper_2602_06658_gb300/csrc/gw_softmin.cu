@@ -22,20 +22,6 @@ constexpr int kThreads = 128;
 constexpr int kBN = 32;      // columns per shared-memory tile
 constexpr int kChunk = 8;    // columns per online-max update
 
-__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
-  uint64_t p;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(lo), "f"(hi));
-  return p;
-}
-__device__ __forceinline__ void upk2(uint64_t p, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
-}
-__device__ __forceinline__ uint64_t fm2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
 template <int KP>
 struct RowsPerThread {
   static constexpr int value = KP <= 32 ? 2 : 1;
@@ -102,26 +88,22 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int c = 0; c < kChunk; ++c) {
         const float4* brow = reinterpret_cast<const float4*>(&Bs[jc + c][0]);
-        // the dot product as packed FP32x2 multiply-adds over feature pairs
-        uint64_t acc[R];
+        float acc[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = pk2(fmaf(u[r], ct[jc + c], cw[jc + c]), 0.0f);
+        for (int r = 0; r < R; ++r) acc[r] = fmaf(u[r], ct[jc + c], cw[jc + c]);
 #pragma unroll
         for (int k4 = 0; k4 < KP / 4; ++k4) {
           const float4 bv = brow[k4];
-          const uint64_t b01 = pk2(bv.x, bv.y), b23 = pk2(bv.z, bv.w);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            acc[r] = fm2(pk2(a[r][4 * k4 + 0], a[r][4 * k4 + 1]), b01, acc[r]);
-            acc[r] = fm2(pk2(a[r][4 * k4 + 2], a[r][4 * k4 + 3]), b23, acc[r]);
+            acc[r] = fmaf(a[r][4 * k4 + 0], bv.x, acc[r]);
+            acc[r] = fmaf(a[r][4 * k4 + 1], bv.y, acc[r]);
+            acc[r] = fmaf(a[r][4 * k4 + 2], bv.z, acc[r]);
+            acc[r] = fmaf(a[r][4 * k4 + 3], bv.w, acc[r]);
           }
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          float lo, hi;
-          upk2(acc[r], lo, hi);
-          z[r][c] = lo + hi;
-        }
+        for (int r = 0; r < R; ++r) z[r][c] = acc[r];
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
