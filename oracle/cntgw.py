@@ -36,6 +36,7 @@ __all__ = [
     "entropic_gw_step", "kernel_gw",
     "grad_features", "center_vjp", "grad_x_squared", "grad_x_lifted",
     "grad_x_bruteforce", "permutation_ot",
+    "kmeans_coarsen", "kmeans_objective", "interpolate", "multiscale_gw",
 ]
 
 F64 = np.float64
@@ -567,3 +568,69 @@ def grad_x_bruteforce(pi, x, y, a, b, kind="sqeuclid", param=2.0):
             coef += pi[i, j] * (Dkl * pi).sum(1)
         out[i] = 4.0 * coef @ dc
     return out
+
+
+# --------------------------------------------------------------------------
+# Multiscale-GW (Algorithms 7 and 8, Appendix B.4)
+# --------------------------------------------------------------------------
+
+def kmeans_coarsen(X, a, init_idx, n_iter):
+    """Coarsen (Appendix B.4): K-Means centroids of the features with the
+    aggregated weights a^c_i = sum_{j in C_i} a_j.  Lloyd's iterations (the
+    paper does not say which K-Means): assign every point to its nearest
+    centroid (ties to the lowest index), then move each centroid to the
+    a-weighted mean of its points; the centroids start at X[init_idx] (the
+    caller draws the indices).  A last assignment follows the last update, and
+    the final centroids are the weighted means of that assignment.  Empty
+    clusters are dropped.  Returns (Xc, ac, assign) with assign indexing Xc."""
+    X = np.asarray(X, F64)
+    a = np.asarray(a, F64)
+    C = X[np.asarray(init_idx)].copy()
+    for _ in range(n_iter + 1):
+        d2 = pairwise_sqdist(X, C)
+        assign = np.argmin(d2, axis=1)          # first minimum
+        k = C.shape[0]
+        wsum = np.bincount(assign, weights=a, minlength=k)
+        for d in range(X.shape[1]):
+            num = np.bincount(assign, weights=a * X[:, d], minlength=k)
+            C[:, d] = np.where(wsum > 0, num / np.where(wsum > 0, wsum, 1.0), C[:, d])
+    keep = np.flatnonzero(wsum > 0)
+    remap = -np.ones(C.shape[0], dtype=np.int64)
+    remap[keep] = np.arange(len(keep))
+    return C[keep], wsum[keep], remap[assign]
+
+
+def kmeans_objective(X, a, C, assign):
+    """sum_j a_j ||X_j - C_{assign(j)}||^2"""
+    X = np.asarray(X, F64)
+    return float(np.asarray(a, F64) @ np.sum((X - np.asarray(C, F64)[assign]) ** 2, axis=1))
+
+
+def interpolate(g_c, X, Yc, b_c, Gamma, eps):
+    """Algorithm 8 (Interpolate): f_i = -eps log sum_j exp(log b^c_j +
+    (g^c_j - C_ij)/eps) with C_ij = -4 ||X_i||^2 ||Y^c_j||^2 - 16 X_i^T Gamma Y^c_j
+    (Gamma the coarse linear map: our reading of the free Gamma of the listing)."""
+    C = cost_gamma(X, Yc, Gamma)
+    return softmin(eps, np.log(np.asarray(b_c, F64)), g_c, C)
+
+
+def multiscale_gw(a, b, X, Y, eps, init_x, init_y, km_iter, coarse_outer, coarse_inner,
+                  fine_outer, fine_inner, eps_final=None, symmetric=True, Gamma0=None):
+    """Algorithm 7 (Multiscale-GW): coarsen both measures by K-Means, solve
+    CNT-GW on the coarse measures, interpolate the coarse potentials to the
+    fine points (Algorithm 8), then run CNT-GW on the fine measures from
+    Gamma^c and the interpolated potentials.  The coarse solve runs at the
+    fine solve's first temperature.  Returns the fine result plus the coarse
+    one under "coarse"."""
+    Xc, ac, _ = kmeans_coarsen(X, a, init_x, km_iter)
+    Yc, bc, _ = kmeans_coarsen(Y, b, init_y, km_iter)
+    coarse = cnt_gw(ac, bc, Xc, Yc, eps, coarse_outer, coarse_inner, Gamma0=Gamma0,
+                    symmetric=symmetric)
+    Gc = coarse["Gamma"]
+    f0 = interpolate(coarse["g"], X, Yc, bc, Gc, eps)
+    g0 = interpolate(coarse["f"], Y, Xc, ac, np.asarray(Gc).T, eps)
+    fine = cnt_gw(a, b, X, Y, eps, fine_outer, fine_inner, Gamma0=Gc, f0=f0, g0=g0,
+                  symmetric=symmetric, eps_final=eps_final)
+    fine["coarse"] = coarse
+    fine["Xc"], fine["ac"], fine["Yc"], fine["bc"] = Xc, ac, Yc, bc
+    return fine

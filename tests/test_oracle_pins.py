@@ -502,3 +502,68 @@ def test_symmetric_sinkhorn_is_exchange_symmetric():
     f, gg = O.sinkhorn(a, b, C, 0.3, 2, symmetric=False)
     g2, f2 = O.sinkhorn(b, a, C.T, 0.3, 2, symmetric=False)
     assert not np.allclose(f, f2, atol=1e-6)
+
+
+# ----------------------------------------------------------- Multiscale-GW
+
+def test_kmeans_recovers_separated_blob_means():
+    """Well-separated blobs, one initial centroid in each: Lloyd's iterations
+    stop at the blobs' weighted means, and the weights aggregate exactly."""
+    g = W.rng(201)
+    centers = np.array([[0.0, 0.0], [10.0, 0.0], [0.0, 10.0], [10.0, 10.0]])
+    lab = np.repeat(np.arange(4), 30)
+    X = centers[lab] + 0.3 * g.standard_normal((120, 2))
+    a = W.random_weights(120, 202)
+    init = [0, 30, 60, 90]
+    C, ac, assign = O.kmeans_coarsen(X, a, init, 5)
+    assert np.array_equal(assign, lab)
+    for c in range(4):
+        m = lab == c
+        assert np.allclose(C[c], (a[m] @ X[m]) / a[m].sum(), atol=1e-13)
+        assert abs(ac[c] - a[m].sum()) < 1e-15
+    assert abs(ac.sum() - 1.0) < 1e-14
+
+
+def test_kmeans_objective_decreases_and_centering_is_kept():
+    g = W.rng(203)
+    X = g.standard_normal((400, 3))
+    a = W.random_weights(400, 204)
+    X = X - a @ X
+    init = g.choice(400, 25, replace=False)
+    objs = []
+    for it in range(0, 8):
+        C, ac, assign = O.kmeans_coarsen(X, a, init, it)
+        objs.append(O.kmeans_objective(X, a, C, assign))
+        # centroids are weighted means, so the coarse measure stays centered
+        assert np.abs(ac @ C).max() < 1e-13
+        # every centroid is the weighted mean of the points assigned to it
+        for c in range(len(ac)):
+            m = assign == c
+            assert np.allclose(C[c], (a[m] @ X[m]) / a[m].sum(), atol=1e-13)
+    assert all(objs[k + 1] <= objs[k] + 1e-15 for k in range(len(objs) - 1))
+
+
+def test_interpolate_with_identical_coarse_measure_is_the_softmin():
+    """Coarse = fine (every point its own cluster): Interpolate is the row
+    update S_b(g) of Algorithm 2 on c_Gamma."""
+    a, b, X, Y = small_problem(N=9, M=8, D=3, E=2, seed=205)
+    G = W.rng(206).standard_normal((3, 2)) * 0.1
+    g = W.rng(207).standard_normal(8)
+    f = O.interpolate(g, X, Y, b, G, 0.3)
+    assert np.allclose(f, O.softmin(0.3, np.log(b), g, O.cost_gamma(X, Y, G)), atol=1e-14)
+
+
+def test_multiscale_reaches_the_direct_solution():
+    """A multiscale solve (rho = 0.1) lands on the energy of the direct fine
+    solve when both converge to the same critical point."""
+    w = W.square_rotated(300, seed=4)
+    a, b = w["a"], w["b"]
+    X, Y = O.center(w["x"], a), O.center(w["y"], b)
+    eps = w["eps"]
+    g = W.rng(208)
+    ix, iy = g.choice(300, 30, replace=False), g.choice(300, 30, replace=False)
+    ms = O.multiscale_gw(a, b, X, Y, eps, ix, iy, 10, 20, 50, 20, 50)
+    direct = O.cnt_gw(a, b, X, Y, eps, 40, 50)
+    assert abs(ms["history"][-1]["E"] - direct["history"][-1]["E"]) < 1e-4 * abs(direct["history"][-1]["E"])
+    assert ms["coarse"]["history"][-1]["E"] > 0
+    assert len(ms["ac"]) <= 30 and abs(ms["ac"].sum() - 1) < 1e-12
