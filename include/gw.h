@@ -73,12 +73,13 @@ typedef struct CUstream_st* gw_stream_t;
 #define GW_OP_SOLVE 3
 #define GW_OP_LIFT 4
 #define GW_OP_GRAD 5
+#define GW_OP_COARSEN 6  /* gw_workspace_size(GW_OP_COARSEN, n points, k clusters, D, 1, 0) */
 
 #define GW_MAX_FEATURES 128 /* largest D, E (and K) the kernels accept */
 
 /* Layout of the float64 energy record written by gw_energy and gw_solve. */
 #define GW_EN_E 0          /* L + eps KL  (objective of Eq. entropic_gromov_wasserstein) */
-#define GW_EN_L 1          /* C - 8 ||Gamma_{t+1}||^2 - 4 T  (Lemma, Appendix D) */
+#define GW_EN_L 1          /* C - 8 ||Gamma_{t+1}||^2 - 4 T  (Lemma, Appendix C.1) */
 #define GW_EN_KL 2         /* KL(pi | a x b) */
 #define GW_EN_C 3          /* C(alpha, beta) of the Lemma */
 #define GW_EN_GAMMA2 4     /* ||Gamma_{t+1}||_F^2 */
@@ -91,6 +92,8 @@ typedef struct CUstream_st* gw_stream_t;
 #define GW_EN_DGAMMA 11    /* ||Gamma_{t+1} - Gamma_t||_F */
 #define GW_EN_EPS 12       /* eps used */
 #define GW_EN_STATUS 13    /* 0, or GW_ENONFINITE when a term is not finite */
+#define GW_EN_NINNER 14    /* gw_solve: Sinkhorn iterations run in this outer step */
+#define GW_EN_STOPERR 15   /* gw_solve: Err of the stop rule's last check, -1 if none */
 #define GW_EN_LEN 16
 
 /*
@@ -173,7 +176,7 @@ int gw_cross_cov(const float* X, const float* Y, const float* s, const float* t,
 
 /*
  * gw_energy -- energy terms of the plan encoded by (f, g) on c_{Gamma_t}
- * (Lemma in Appendix D; Eq. entropic_gromov_wasserstein):
+ * (Lemma in Appendix C.1; Eq. entropic_gromov_wasserstein):
  *   C(alpha,beta) from the centered moments of X and Y,
  *   L = C - 8 ||Gamma_{t+1}||^2 - 4 T,
  *   eps KL = sum_i f_i (pi 1)_i + sum_j g_j (pi^T 1)_j + 16 <Gamma_t, Gamma_{t+1}> + 4 T,
@@ -213,6 +216,19 @@ typedef struct gw_options {
   const double* Gamma0; /* D x E initial map, NULL = 0 (Algorithm 1, first line) */
   const float* f0;    /* initial potentials (warm start), NULL = 0 */
   const float* g0;
+  /* Algorithm 6 (Appendix B.4) applied to CNT-GW: 1 = n_inner is the initial
+     count, doubled (up to n_inner_max) after every outer step whose energy E
+     exceeds the previous step's by more than adapt_rtol * |E_prev|
+     (adapt_rtol = 0 is the paper's strict test). */
+  int adaptive;
+  int n_inner_max;    /* cap of the adaptive count (<= 0: n_inner) */
+  float adapt_rtol;   /* >= 0 */
+  /* Hybrid stop (Appendix D.1): > 0 = after every stop_every-th iteration,
+     end the outer step's Sinkhorn loop once Err (Appendix A) of the plan that
+     iteration measured is below stop_tol: (f^n, g^n) for Algorithm 3,
+     (f^{n+1}, g^n) for Algorithm 2.  n_inner stays the maximum. */
+  float stop_tol;
+  int stop_every;
 } gw_options;
 
 typedef struct gw_result {
@@ -231,7 +247,11 @@ typedef struct gw_result {
  *   c_{Gamma_t} at eps_t, warm-started from the previous potentials;
  *   Gamma_{t+1} = sum_ij pi_ij X_i Y_j^T; energy record of pi_{t+1}.
  * All outputs are device buffers owned by the caller; nothing is read back
- * to the host.  Asynchronous on `stream`.
+ * to the host.  Asynchronous on `stream`, except with adaptive = 1 or
+ * stop_tol > 0: those decisions are taken on the host, which waits for each
+ * outer step's energy (adaptive) or each stop check (and no CUDA graph is
+ * used).  Records carry the iterations run (GW_EN_NINNER) and the last
+ * checked Err (GW_EN_STOPERR).
  * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
  */
 int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, size_t ws_bytes,
@@ -259,7 +279,7 @@ int gw_lift(const float* x, int64_t n, int d, const float* w, int kind, float pa
 
 /*
  * gw_grad_x -- gradient of the EGW energy with respect to the source points
- * through the converged plan (envelope theorem, Appendix B.5):
+ * through the converged plan (envelope theorem, Appendix B.6):
  *   dX_i = 8 a_i [(s_i + m2_X) X_i + 2 Sigma_X X_i - mu3_X] - 8 a_i m2_Y X_i
  *          - 16 Gamma_pi w_i - 8 q_i X_i,
  *   w_i = sum_j pi_ij Y_j, q_i = sum_j pi_ij t_j (pi from f, g on c_{Gamma_t}),
@@ -275,6 +295,43 @@ int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double*
               const double* Gamma_pi, float eps, int prec, const float* x, int dx_dim, int kind,
               float param, const float* basis, const float* eigvals, float* dX, float* dx,
               void* ws, size_t ws_bytes, gw_stream_t stream);
+
+/*
+ * gw_coarsen -- Coarsen of Multiscale-GW (Appendix B.5): K-Means of the
+ * features X (n x D, weights a; NULL = uniform) by Lloyd's iterations from
+ * the k caller-given point indices init_idx (device, int64), ties to the
+ * lowest centroid index, n_iter update rounds followed by a last assignment
+ * and update.  Writes the non-empty clusters in order: centroids Xc (k x D),
+ * aggregated weights ac (k), squared norms sc (k), their count to *h_k_out
+ * (host), and, when assign (device, n) is not NULL, each point's cluster in
+ * that order (from the last assignment).  Weights must be non-negative.  An
+ * index of init_idx outside [0, n) returns GW_EINVAL (checked on the device,
+ * nothing is read out of bounds).  Workspace: GW_OP_COARSEN.  Synchronous.  Cluster sums use 64-bit fixed point with
+ * integer atomics, so the result is bitwise reproducible.
+ * Errors: GW_EINVAL, GW_ENOMEM, GW_ECUDA.
+ */
+int gw_coarsen(const float* X, const float* a, int64_t n, int D, const int64_t* init_idx,
+               int64_t k, int n_iter, float* Xc, float* ac, float* sc, int* assign,
+               int64_t* h_k_out, void* ws, size_t ws_bytes, gw_stream_t stream);
+
+/*
+ * gw_multiscale -- Multiscale-GW (Algorithm 7): coarsen both measures
+ * (gw_coarsen with init_x (kx indices) / init_y (ky indices) and km_iter
+ * rounds), CNT-GW on the coarse measures with options `coarse` (Gamma0 /
+ * f0 / g0 honoured, record ignored), Interpolate (Algorithm 8: one softmin per
+ * side at the fine solve's first eps, with the coarse Gamma), then CNT-GW on
+ * the fine measures with options `fine`, started from Gamma^c and the
+ * interpolated potentials (its Gamma0 / f0 / g0 are replaced).  Results as
+ * gw_solve; coarse_energy (device, GW_EN_LEN, may be NULL) receives the
+ * coarse solve's final record.  Synchronous up to the fine solve, which is
+ * enqueued on `stream`.  Workspace: gw_multiscale_workspace_size().
+ */
+int gw_multiscale(const gw_problem* p, const gw_options* coarse, const gw_options* fine,
+                  const int64_t* init_x, int64_t kx, const int64_t* init_y, int64_t ky,
+                  int km_iter, gw_result* r, double* coarse_energy, void* ws, size_t ws_bytes,
+                  gw_stream_t stream);
+size_t gw_multiscale_workspace_size(int64_t n, int64_t m, int D, int E, int64_t kx, int64_t ky,
+                                    int prec);
 
 /*
  * Request server (continuous batching; no counterpart in the paper, which

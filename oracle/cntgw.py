@@ -36,7 +36,7 @@ __all__ = [
     "entropic_gw_step", "kernel_gw",
     "grad_features", "center_vjp", "grad_x_squared", "grad_x_lifted",
     "grad_x_bruteforce", "permutation_ot",
-    "kmeans_coarsen", "kmeans_objective", "interpolate", "multiscale_gw",
+    "kmeans_coarsen", "kmeans_objective", "interpolate", "multiscale_gw", "sinkhorn_stop",
 ]
 
 F64 = np.float64
@@ -185,7 +185,7 @@ def kernel_proj(xq, x, a, V, lam, kind="power", param=1.0):
 
 
 def kernel_proj_vjp(G, xq, x, a, V, lam, kind="power", param=1.0):
-    """Vector-Jacobian product of Kernel-Proj at points xq (Appendix B.5,
+    """Vector-Jacobian product of Kernel-Proj at points xq (Appendix B.6,
     "Approximation with Kernel PCA"): returns sum_d G_{qd} grad_x Pi_d(xq).
 
     grad_x k~(x, x_i) = (-grad_1 c(x, x_i) + sum_l a_l grad_1 c(x, x_l)) / 2,
@@ -286,7 +286,7 @@ def row_marginal_from_potentials(a, b, f, g, C, eps):
 
 # --------------------------------------------------------------------------
 # GW loss and energy (Eq. GW_loss; Eq. entropic_gromov_wasserstein; Lemma in
-# Appendix D; Theorem 3.3)
+# Appendix C.1; Theorem 3.3)
 # --------------------------------------------------------------------------
 
 def gw_loss_bruteforce(pi, CX, CY):
@@ -345,7 +345,7 @@ def cross_covariance(pi, X, Y):
 
 def gw_loss_lemma(pi, X, Y, a, b):
     """L(pi) = C(alpha, beta) - 8 ||Gamma_pi||^2 - 4 sum_ij pi_ij ||X_i||^2 ||Y_j||^2
-    (Lemma in Appendix D; valid for pi in Pi(a, b) and centered X, Y)."""
+    (Lemma in Appendix C.1; valid for pi in Pi(a, b) and centered X, Y)."""
     G = cross_covariance(pi, X, Y)
     T = float(sqnorms(X) @ np.asarray(pi, F64) @ sqnorms(Y))
     return gw_constant_pairwise(X, Y, a, b) - 8.0 * float(np.sum(G * G)) - 4.0 * T
@@ -396,18 +396,58 @@ def eps_schedule(eps0, eps_final, n_outer):
     return [float(eps0 * (eps_final / eps0) ** (t / (n_outer - 1))) for t in range(n_outer)]
 
 
+def sinkhorn_stop(a, b, C, eps, n_max, f0=None, g0=None, symmetric=True, tol=0.0, every=1,
+                  trace=None):
+    """Sinkhorn with the hybrid stop of Appendix D.1 (a fixed maximum of
+    iterations and early stopping on the marginal error): after every
+    `every`-th iteration the error Err (Appendix A) of the last plan whose
+    marginals that iteration measured is compared with tol, and the loop ends
+    once it is below.  The measured plan is (f^n, g^n) for Algorithm 3 (its
+    row and column softmins were just evaluated) and (f^{n+1}, g^n) for
+    Algorithm 2 (exact rows; columns from S_a(f^{n+1})).  The paper prints a
+    weighted form of the error next to the plain one of Appendix A; this uses
+    the plain one.  Every check appends (iteration, Err) to `trace` when it is
+    a list.  Returns (f, g, iterations run, last measured Err or None)."""
+    a = np.asarray(a, F64)
+    b = np.asarray(b, F64)
+    C = np.asarray(C, F64)
+    f = np.zeros(C.shape[0]) if f0 is None else np.array(f0, F64)
+    g = np.zeros(C.shape[1]) if g0 is None else np.array(g0, F64)
+    err = None
+    for it in range(n_max):
+        f_new, g_new = sinkhorn(a, b, C, eps, 1, f, g, symmetric)
+        if (it + 1) % every == 0:
+            measured = (f, g) if symmetric else (f_new, g)
+            err = marginal_error(plan(a, b, measured[0], measured[1], C, eps), a, b)
+            if trace is not None:
+                trace.append((it + 1, err))
+        f, g = f_new, g_new
+        if err is not None and (it + 1) % every == 0 and err < tol:
+            return f, g, it + 1, err
+    return f, g, n_max, err
+
+
 def cnt_gw(a, b, X, Y, eps, n_outer, n_inner, Gamma0=None, f0=None, g0=None,
-           symmetric=True, eps_final=None, record=True):
+           symmetric=True, eps_final=None, record=True, adaptive=False, n_inner_max=None,
+           stop_tol=None, stop_every=1, adapt_rtol=0.0):
     """Algorithm 1 (CNT-GW) with Algorithm 3 as SinkhornOT, on c_Gamma.
 
     For t = 0 .. n_outer-1:
       1. C = c_{Gamma_t}  (Zbar_j = [Gamma_t Y_j, ||Y_j||^2 / 2] in Alg. 1);
-      2. (f, g) <- Sinkhorn(a, b, C, eps_t, n_inner), warm-started from the
-         previous (f, g) (Appendix B.1, "Warm-Start");
-      3. Xtilde_j = sum_i a_i X_i exp((f_i + g_j - C_ij)/eps_t);
+      2. (f, g) <- n_inner Sinkhorn iterations at eps_t, warm-started (App. B.1);
+      3. Xtilde_j = sum_i a_i X_i exp((f_i + g_j - C_ij) / eps_t);
       4. Gamma_{t+1} = sum_j b_j Xtilde_j Y_j^T.
     Gamma_0 = 0 unless given.  Each step records the energy of pi_{t+1}
     (E = L + eps_t KL), its marginal error and ||Gamma_{t+1} - Gamma_t||_F.
+
+    adaptive: Algorithm 6 applied to CNT-GW (Appendix B.4): n_inner is the
+    initial count; when the energy of pi_{t+1} exceeds that of pi_t the next
+    steps run twice as many iterations (capped at n_inner_max).  The loss
+    compared is E = L + eps_t KL on the lifted features; "exceeds" means
+    E(pi_{t+1}) > E(pi_t) + adapt_rtol |E(pi_t)| (0: the paper's strict test,
+    which near convergence also fires on rounding noise).
+    stop_tol: the hybrid stop of sinkhorn_stop inside every outer step, with
+    n_inner (or the adaptive count) as the maximum.
     Returns dict(Gamma, f, g, history, eps)."""
     a = np.asarray(a, F64)
     b = np.asarray(b, F64)
@@ -418,24 +458,39 @@ def cnt_gw(a, b, X, Y, eps, n_outer, n_inner, Gamma0=None, f0=None, g0=None,
     f = np.zeros(X.shape[0]) if f0 is None else np.array(f0, F64)
     g = np.zeros(Y.shape[0]) if g0 is None else np.array(g0, F64)
     sched = eps_schedule(eps, eps_final, n_outer)
+    cap = n_inner_max if n_inner_max is not None else n_inner
+    n_cur = n_inner
+    E_prev = None
     hist = []
     for t in range(n_outer):
         e = sched[t]
         C = cost_gamma(X, Y, Gamma)
-        f, g = sinkhorn(a, b, C, e, n_inner, f, g, symmetric)
+        trace = []
+        if stop_tol is not None and stop_tol > 0:
+            f, g, n_run, serr = sinkhorn_stop(a, b, C, e, n_cur, f, g, symmetric, stop_tol,
+                                              stop_every, trace)
+        else:
+            f, g = sinkhorn(a, b, C, e, n_cur, f, g, symmetric)
+            n_run, serr = n_cur, None
         K = np.exp((f[:, None] + g[None, :] - C) / e)
         Xtilde = K.T @ (a[:, None] * X)                  # (M, D): Xtilde_j
         Gamma_next = (Xtilde * b[:, None]).T @ Y         # sum_j b_j Xtilde_j Y_j^T
-        if record:
+        if record or adaptive:
             pi = plan(a, b, f, g, C, e)
             en = egw_energy(pi, X, Y, a, b, e)
+        if record:
             hist.append({
                 "eps": e, "E": en["E"], "L": en["L"], "KL": en["KL"], "C": en["C"],
                 "err": marginal_error(pi, a, b),
                 "row": pi.sum(1), "col": pi.sum(0),
                 "dGamma": float(np.linalg.norm(Gamma_next - Gamma)),
                 "Gamma": Gamma_next.copy(),
+                "n_inner": n_run, "stop_err": serr, "stop_trace": trace,
             })
+        if adaptive:
+            if E_prev is not None and en["E"] > E_prev + adapt_rtol * abs(E_prev):
+                n_cur = min(2 * n_cur, cap)
+            E_prev = en["E"]
         Gamma = Gamma_next
     return {"Gamma": Gamma, "f": f, "g": g, "history": hist, "eps": sched}
 
@@ -499,12 +554,12 @@ def permutation_ot(C):
 
 
 # --------------------------------------------------------------------------
-# Gradients (Appendix B.5, envelope theorem)
+# Gradients (Appendix B.6, envelope theorem)
 # --------------------------------------------------------------------------
 
 def grad_features(pi, Gamma, X, Y, a, b):
     """Gradient of E = L(pi) + eps KL with pi held at the converged plan
-    (envelope theorem, Appendix B.5), with respect to the centered features
+    (envelope theorem, Appendix B.6), with respect to the centered features
     X_i, from the Lemma:
       dC/dX_i     = 8 a_i [(s_i + m2_X) X_i + 2 Sigma_X X_i - mu3_X] - 8 a_i m2_Y X_i
       d(-8||G||^2) = -16 Gamma w_i,   w_i = sum_j pi_ij Y_j
@@ -571,11 +626,11 @@ def grad_x_bruteforce(pi, x, y, a, b, kind="sqeuclid", param=2.0):
 
 
 # --------------------------------------------------------------------------
-# Multiscale-GW (Algorithms 7 and 8, Appendix B.4)
+# Multiscale-GW (Algorithms 7 and 8, Appendix B.5)
 # --------------------------------------------------------------------------
 
 def kmeans_coarsen(X, a, init_idx, n_iter):
-    """Coarsen (Appendix B.4): K-Means centroids of the features with the
+    """Coarsen (Appendix B.5): K-Means centroids of the features with the
     aggregated weights a^c_i = sum_{j in C_i} a_j.  Lloyd's iterations (the
     paper does not say which K-Means): assign every point to its nearest
     centroid (ties to the lowest index), then move each centroid to the

@@ -20,17 +20,18 @@ __all__ = [
     "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
     "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
     "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
-    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server",
+    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale",
 ]
 
 GW_OK = 0
 PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 PEN_SQEUCLID, PEN_POWER, PEN_GAUSS = 0, 1, 2
-OP_SOFTMIN, OP_CROSS_COV, OP_ENERGY, OP_SOLVE, OP_LIFT, OP_GRAD = 0, 1, 2, 3, 4, 5
+OP_SOFTMIN, OP_CROSS_COV, OP_ENERGY, OP_SOLVE, OP_LIFT, OP_GRAD, OP_COARSEN = 0, 1, 2, 3, 4, 5, 6
 EN_LEN = 16
 # index of each term of the float64 energy record
 EN = {"E": 0, "L": 1, "KL": 2, "C": 3, "Gamma2": 4, "T": 5, "row_l1": 6, "col_l1": 7,
-      "row_relmax": 8, "col_relmax": 9, "mass": 10, "dGamma": 11, "eps": 12, "status": 13}
+      "row_relmax": 8, "col_relmax": 9, "mass": 10, "dGamma": 11, "eps": 12, "status": 13,
+      "n_inner": 14, "stop_err": 15}
 _STATUS = {1: "GW_EINVAL", 2: "GW_ENOMEM", 3: "GW_ECUDA", 4: "GW_ENONFINITE", 5: "GW_ETIMEOUT",
            6: "GW_EUNSUPPORTED"}
 
@@ -61,7 +62,8 @@ class GwProblem(ctypes.Structure):
 class GwOptions(ctypes.Structure):
     _fields_ = [("eps", _f), ("eps_final", _f), ("n_outer", _int), ("n_inner", _int),
                 ("symmetric", _int), ("prec", _int), ("record", _int), ("use_graph", _int),
-                ("Gamma0", _p), ("f0", _p), ("g0", _p)]
+                ("Gamma0", _p), ("f0", _p), ("g0", _p), ("adaptive", _int), ("n_inner_max", _int),
+                ("adapt_rtol", _f), ("stop_tol", _f), ("stop_every", _int)]
 
 
 class GwResult(ctypes.Structure):
@@ -84,6 +86,13 @@ lib.gw_lift.argtypes = [_p, _i64, _int, _p, _int, _f, _int, _int, ctypes.c_uint6
                         _p, _sz, _p]
 lib.gw_grad_x.argtypes = [ctypes.POINTER(GwProblem), _p, _p, _p, _p, _f, _int, _p, _int, _int, _f,
                           _p, _p, _p, _p, _p, _sz, _p]
+lib.gw_coarsen.argtypes = [_p, _p, _i64, _int, _p, _i64, _int, _p, _p, _p, _p,
+                           ctypes.POINTER(_i64), _p, _sz, _p]
+lib.gw_multiscale.argtypes = [ctypes.POINTER(GwProblem), ctypes.POINTER(GwOptions),
+                              ctypes.POINTER(GwOptions), _p, _i64, _p, _i64, _int,
+                              ctypes.POINTER(GwResult), _p, _p, _sz, _p]
+lib.gw_multiscale_workspace_size.argtypes = [_i64, _i64, _int, _int, _i64, _i64, _int]
+lib.gw_multiscale_workspace_size.restype = _sz
 class GwRequest(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("n", _i64), ("m", _i64), ("d", _int), ("kind", _int),
                 ("param", _f), ("D", _int), ("eps", _f), ("eps_final", _f), ("n_outer", _int),
@@ -114,7 +123,8 @@ lib.gw_last_error.restype = ctypes.c_char_p
 lib.gw_version.restype = _int
 lib.gw_kernel_launches.argtypes = [_int]
 lib.gw_kernel_launches.restype = ctypes.c_ulonglong
-for _name in ("gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve", "gw_lift", "gw_grad_x"):
+for _name in ("gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve", "gw_lift", "gw_grad_x",
+              "gw_coarsen", "gw_multiscale"):
     getattr(lib, _name).restype = _int
 
 
@@ -250,9 +260,12 @@ def gw_energy(X, Y, s, t, a, b, f, g, Gamma_t, eps, prec=PREC_FP32, ws=None, str
 
 def gw_solve(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=True,
              prec=PREC_FP32, record=True, use_graph=True, Gamma0=None, f0=None, g0=None, ws=None,
-             out=None, stream=None):
+             out=None, stream=None, adaptive=False, n_inner_max=0, adapt_rtol=0.0, stop_tol=0.0,
+             stop_every=1):
     """CNT-GW (Algorithm 1) on device.  Returns dict(Gamma, Gamma_plan, f, g,
-    energy, history) of device tensors; nothing is synchronised."""
+    energy, history) of device tensors; nothing is synchronised unless
+    adaptive (Algorithm 6) or stop_tol > 0 (hybrid stop) asks for host
+    decisions."""
     n, D = X.shape
     m, E = Y.shape
     dev = X.device
@@ -270,11 +283,77 @@ def gw_solve(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=T
                   _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
     O = GwOptions(float(eps), float(eps_final), int(n_outer), int(n_inner), int(bool(symmetric)),
                   int(prec), int(bool(record)), int(bool(use_graph)),
-                  _ptr(_f64(Gamma0, "Gamma0")), _ptr(_f32(f0, "f0")), _ptr(_f32(g0, "g0")))
+                  _ptr(_f64(Gamma0, "Gamma0")), _ptr(_f32(f0, "f0")), _ptr(_f32(g0, "g0")),
+                  int(bool(adaptive)), int(n_inner_max), float(adapt_rtol), float(stop_tol),
+                  int(stop_every))
     R = GwResult(_ptr(out["Gamma"]), _ptr(out.get("Gamma_plan")), _ptr(out["f"]), _ptr(out["g"]), _ptr(out["energy"]),
                  _ptr(out["history"]))
     _check(lib.gw_solve(ctypes.byref(P), ctypes.byref(O), ctypes.byref(R), _ptr(ws), ws.numel(),
                         _stream(stream)))
+    return out
+
+
+def _idx64(t, name):
+    if t.dtype != torch.int64:
+        raise TypeError(f"{name} must be int64")
+    return t
+
+
+def gw_coarsen(X, init_idx, n_iter, a=None, ws=None, stream=None):
+    """K-Means coarsening (gw.h: gw_coarsen).  Returns (Xc, ac, sc, assign)
+    of the non-empty clusters; synchronises with the stream (the cluster
+    count is read back)."""
+    n, D = X.shape
+    k = int(init_idx.numel())
+    dev = X.device
+    Xc = torch.empty(k, D, dtype=torch.float32, device=dev)
+    ac = torch.empty(k, dtype=torch.float32, device=dev)
+    sc = torch.empty(k, dtype=torch.float32, device=dev)
+    assign = torch.empty(n, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = workspace(gw_workspace_size(OP_COARSEN, n, k, D, 1, PREC_FP32), dev)
+    kout = _i64(0)
+    _check(lib.gw_coarsen(_ptr(_f32(X, "X")), _ptr(_f32(a, "a")), n, D,
+                          _ptr(_idx64(init_idx, "init_idx")), k, int(n_iter), _ptr(Xc), _ptr(ac),
+                          _ptr(sc), _ptr(assign), ctypes.byref(kout), _ptr(ws), ws.numel(),
+                          _stream(stream)))
+    k2 = int(kout.value)
+    return Xc[:k2], ac[:k2], sc[:k2], assign
+
+
+def gw_multiscale(X, Y, s, t, a, b, eps, init_x, init_y, km_iter, coarse_outer, coarse_inner,
+                  fine_outer, fine_inner, eps_final=0.0, symmetric=True, prec=PREC_FP32,
+                  record=True, use_graph=True, Gamma0=None, ws=None, stream=None):
+    """Multiscale-GW (Algorithm 7; gw.h: gw_multiscale).  The coarse solve
+    runs at the fine solve's first temperature.  Returns the gw_solve dict
+    plus "coarse_energy"."""
+    n, D = X.shape
+    m, E = Y.shape
+    dev = X.device
+    kx, ky = int(init_x.numel()), int(init_y.numel())
+    out = {"Gamma": torch.empty(D, E, dtype=torch.float64, device=dev),
+           "Gamma_plan": torch.empty(D, E, dtype=torch.float64, device=dev),
+           "f": torch.empty(n, dtype=torch.float32, device=dev),
+           "g": torch.empty(m, dtype=torch.float32, device=dev),
+           "energy": torch.empty(EN_LEN, dtype=torch.float64, device=dev),
+           "history": torch.empty(fine_outer, EN_LEN, dtype=torch.float64, device=dev)
+           if record else None,
+           "coarse_energy": torch.empty(EN_LEN, dtype=torch.float64, device=dev)}
+    if ws is None:
+        ws = workspace(lib.gw_multiscale_workspace_size(n, m, D, E, kx, ky, int(prec)), dev)
+    P = GwProblem(_ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
+                  _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
+    Oc = GwOptions(float(eps), 0.0, int(coarse_outer), int(coarse_inner), int(bool(symmetric)),
+                   int(prec), 0, int(bool(use_graph)), _ptr(_f64(Gamma0, "Gamma0")), None, None)
+    Of = GwOptions(float(eps), float(eps_final), int(fine_outer), int(fine_inner),
+                   int(bool(symmetric)), int(prec), int(bool(record)), int(bool(use_graph)),
+                   None, None, None)
+    R = GwResult(_ptr(out["Gamma"]), _ptr(out["Gamma_plan"]), _ptr(out["f"]), _ptr(out["g"]),
+                 _ptr(out["energy"]), _ptr(out["history"]))
+    _check(lib.gw_multiscale(ctypes.byref(P), ctypes.byref(Oc), ctypes.byref(Of),
+                             _ptr(_idx64(init_x, "init_x")), kx, _ptr(_idx64(init_y, "init_y")), ky,
+                             int(km_iter), ctypes.byref(R), _ptr(out["coarse_energy"]), _ptr(ws),
+                             ws.numel(), _stream(stream)))
     return out
 
 

@@ -12,7 +12,7 @@ from . import (EN, PEN_SQEUCLID, PREC_FP32, gw_grad_x, gw_lift, gw_solve)
 class GWEnergy(torch.autograd.Function):
     """E = GW_eps(alpha, beta) for alpha = sum a_i delta_{x_i}, beta = sum
     b_j delta_{y_j} (Eq. entropic_gromov_wasserstein), with the gradient with
-    respect to the source points x through the converged plan (Appendix B.5).
+    respect to the source points x through the converged plan (Appendix B.6).
 
     penalty = PEN_SQEUCLID: features are the centered points (D = d).
     Otherwise the features are Kernel PCA features of dimension D and the

@@ -73,6 +73,8 @@ size_t solve_fixed_bytes(int64_t n, int64_t m, int D, int E) {
   c.take<double>(static_cast<size_t>(D) * E); // Gamma next
   c.take<double>(4);                // C
   c.take<double>(GW_EN_LEN);        // scratch energy record
+  c.take<double>(kMargBlocks);      // stop-rule partials
+  c.take<double>(2);                // stop-rule Err
   return c.used();
 }
 
@@ -86,8 +88,15 @@ size_t solve_ws_bytes(int64_t n, int64_t m, int D, int E, int prec) {
 
 struct SolveBufs {
   float *loga, *logb, *f[2], *g[2], *V;
-  double *G[2], *C, *en;
+  double *G[2], *C, *en, *mpart, *merr;
 };
+
+// read one device double (the stream is drained first)
+int read_back(const double* d, double* h, cudaStream_t st) {
+  GW_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, st));
+  GW_CUDA_TRY(cudaStreamSynchronize(st));
+  return GW_OK;
+}
 
 int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, void* ws,
                   size_t ws_bytes, cudaStream_t st) {
@@ -104,6 +113,8 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
   B.G[1] = c.take<double>(static_cast<size_t>(p.D) * p.E);
   B.C = c.take<double>(4);
   B.en = c.take<double>(GW_EN_LEN);
+  B.mpart = c.take<double>(kMargBlocks);
+  B.merr = c.take<double>(2);
   GW_TRY(check_ws(c, ws));
   const size_t mark = c.used();
   char* base = static_cast<char*>(ws);
@@ -131,6 +142,10 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
     GW_TRY(run_moments(p.X, p.a, p.n, p.D, p.Y, p.b, p.m, p.E, B.C, sub, st));
   }
 
+  const bool stop_rule = o.stop_tol > 0.0f;
+  const int cap = o.n_inner_max > o.n_inner ? o.n_inner_max : o.n_inner;
+  int n_cur = o.n_inner;   // Algorithm 6: the count of the coming outer step
+  double E_prev = 0.0;
   int fc = 0, gc = 0, Gc = 0;
   for (int t = 0; t < o.n_outer; ++t) {
     float eps = o.eps;
@@ -141,7 +156,9 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
     }
     // Zbar_j <- Gamma_t Y_j (Algorithm 1, line 4)
     GW_TRY(launch_gamma_y(B.G[Gc], p.Y, p.m, p.D, p.E, B.V, st));
-    for (int it = 0; it < o.n_inner; ++it) {
+    int n_run = n_cur;
+    bool checked = false;
+    for (int it = 0; it < n_cur; ++it) {
       Carver sub(base + mark, ws_bytes - mark);
       SoftminTask row{}, col{};
       row.A = p.X;
@@ -195,6 +212,18 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
         GW_TRY(launch_softmin(&col, 1, o.prec, sub2, st));
         gc ^= 1;
       }
+      if (stop_rule && (it + 1) % o.stop_every == 0) {
+        // hybrid stop: Err of the plan this iteration measured
+        GW_TRY(run_marginal_error(B.f[fc ^ 1], B.f[fc], p.a, p.n, B.g[gc ^ 1], B.g[gc], p.b, p.m,
+                                  eps, o.symmetric != 0, B.mpart, B.merr, st));
+        checked = true;
+        double err = 0.0;
+        GW_TRY(read_back(B.merr, &err, st));
+        if (err < static_cast<double>(o.stop_tol)) {
+          n_run = it + 1;
+          break;
+        }
+      }
     }
     // Xtilde / Gamma_{t+1} lines of Algorithm 1, plus the energy record
     PlanArgs pa;
@@ -214,9 +243,18 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
     pa.E = p.E;
     Carver sub(base + mark, ws_bytes - mark);
     const bool last = t == o.n_outer - 1;
-    if (o.record || last) {
+    if (o.record || last || o.adaptive) {
       double* rec = (o.record && r.history) ? r.history + static_cast<size_t>(t) * GW_EN_LEN : B.en;
       GW_TRY(run_energy(pa, o.prec, B.C, B.logb, rec, B.G[Gc ^ 1], sub, st));
+      GW_TRY(launch_record_extra(rec, n_run, checked ? B.merr : nullptr, st));
+      if (o.adaptive) {
+        // Algorithm 6: an energy increase means Sinkhorn was not converged
+        double E = 0.0;
+        GW_TRY(read_back(rec + GW_EN_E, &E, st));
+        if (t > 0 && E > E_prev + static_cast<double>(o.adapt_rtol) * fabs(E_prev))
+          n_cur = 2 * n_cur < cap ? 2 * n_cur : cap;
+        E_prev = E;
+      }
       if (last) {
         GW_CUDA_TRY(cudaMemcpyAsync(r.energy, rec, sizeof(double) * GW_EN_LEN,
                                     cudaMemcpyDeviceToDevice, st));
@@ -261,6 +299,7 @@ size_t gw_workspace_size(int op, int64_t n, int64_t m, int D, int E, int prec) {
     case GW_OP_SOLVE: return solve_ws_bytes(n, m, D, E, prec);
     case GW_OP_LIFT: return lift_ws_bytes(n, D) + 256;   /* (n points, D features) */
     case GW_OP_GRAD: return grad_ws_bytes(n, m, D, E, 4, prec) + 256;
+    case GW_OP_COARSEN: return n >= 1 ? coarsen_ws_bytes(n, m, D) + 256 : 0;   /* (n points, m = k) */
     default: return 0;
   }
 }
@@ -377,11 +416,16 @@ int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, s
   NONNULL(r->g);
   NONNULL(r->energy);
   GW_REQUIRE(!o->record || r->history != nullptr, GW_EINVAL, "record = 1 needs result.history");
+  GW_REQUIRE(o->n_inner_max <= 1000000, GW_EINVAL, "n_inner_max too large");
+  GW_REQUIRE(o->adapt_rtol >= 0.0f && isfinite(o->adapt_rtol), GW_EINVAL, "adapt_rtol must be >= 0");
+  GW_REQUIRE(!(o->stop_tol > 0.0f) || (isfinite(o->stop_tol) && o->stop_every >= 1), GW_EINVAL,
+             "stop_tol > 0 needs a finite tolerance and stop_every >= 1");
   const size_t need = solve_ws_bytes(p->n, p->m, p->D, p->E, o->prec);
   GW_REQUIRE(ws != nullptr && ws_bytes >= need, GW_ENOMEM,
              "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (!o->use_graph || st == nullptr) return enqueue_solve(*p, *o, *r, ws, ws_bytes, st);
+  const bool host_driven = o->adaptive || o->stop_tol > 0.0f;
+  if (!o->use_graph || st == nullptr || host_driven) return enqueue_solve(*p, *o, *r, ws, ws_bytes, st);
 
   cudaGraph_t graph = nullptr;
   GW_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -467,6 +511,59 @@ int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double*
              "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
   return run_grad(*p, f, g, Gamma_t, Gamma_pi, eps, prec, x, dx_dim, kind, param, basis, eigvals,
                   dX, dx, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int gw_coarsen(const float* X, const float* a, int64_t n, int D, const int64_t* init_idx,
+               int64_t k, int n_iter, float* Xc, float* ac, float* sc, int* assign,
+               int64_t* h_k_out, void* ws, size_t ws_bytes, gw_stream_t stream) {
+  gw::set_error("");
+  NONNULL(X);
+  NONNULL(init_idx);
+  NONNULL(Xc);
+  NONNULL(ac);
+  NONNULL(sc);
+  NONNULL(h_k_out);
+  GW_REQUIRE(n >= 1 && k >= 1 && k <= n, GW_EINVAL, "need 1 <= k <= n");
+  GW_REQUIRE(D >= 1 && D <= GW_MAX_FEATURES, GW_EUNSUPPORTED, "D must be in [1, %d]", GW_MAX_FEATURES);
+  GW_REQUIRE(n_iter >= 0 && n_iter <= 10000, GW_EINVAL, "n_iter out of range");
+  Carver c(ws, ws_bytes);
+  GW_REQUIRE(reinterpret_cast<uintptr_t>(ws) % 256 == 0, GW_ENOMEM, "workspace must be 256-byte aligned");
+  return run_coarsen(X, a, n, D, init_idx, k, n_iter, Xc, ac, sc, assign, h_k_out, c,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t gw_multiscale_workspace_size(int64_t n, int64_t m, int D, int E, int64_t kx, int64_t ky,
+                                    int prec) {
+  if (n < 1 || m < 1 || kx < 1 || ky < 1 || D < 1 || E < 1) return 0;
+  return multiscale_ws_bytes(n, m, D, E, kx, ky, prec);
+}
+
+int gw_multiscale(const gw_problem* p, const gw_options* coarse, const gw_options* fine,
+                  const int64_t* init_x, int64_t kx, const int64_t* init_y, int64_t ky,
+                  int km_iter, gw_result* r, double* coarse_energy, void* ws, size_t ws_bytes,
+                  gw_stream_t stream) {
+  gw::set_error("");
+  NONNULL(p);
+  NONNULL(coarse);
+  NONNULL(fine);
+  NONNULL(r);
+  NONNULL(init_x);
+  NONNULL(init_y);
+  GW_TRY(check_dims(p->n, p->m, p->D, p->E));
+  GW_REQUIRE(kx >= 1 && kx <= p->n && ky >= 1 && ky <= p->m, GW_EINVAL, "need 1 <= kx <= n, 1 <= ky <= m");
+  GW_TRY(check_eps(coarse->eps));
+  GW_TRY(check_eps(fine->eps));
+  GW_TRY(check_prec(coarse->prec));
+  GW_TRY(check_prec(fine->prec));
+  GW_REQUIRE(coarse->n_outer >= 1 && coarse->n_inner >= 1 && fine->n_outer >= 1 && fine->n_inner >= 1,
+             GW_EINVAL, "iteration counts must be >= 1");
+  GW_REQUIRE(!fine->record || r->history != nullptr, GW_EINVAL, "record = 1 needs result.history");
+  const size_t need = multiscale_ws_bytes(p->n, p->m, p->D, p->E, kx, ky,
+                                          fine->prec > coarse->prec ? fine->prec : coarse->prec);
+  GW_REQUIRE(ws != nullptr && ws_bytes >= need, GW_ENOMEM,
+             "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
+  return run_multiscale(*p, *coarse, *fine, init_x, kx, init_y, ky, km_iter, *r, coarse_energy, ws,
+                        ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

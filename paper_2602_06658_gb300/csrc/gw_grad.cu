@@ -1,8 +1,8 @@
 // Gradient of the EGW energy with respect to the source points through the
-// converged plan (Appendix B.5, envelope theorem; Algorithms 9-13).
+// converged plan (Appendix B.6, envelope theorem; Algorithms 9-13).
 //
 // With pi held at the plan encoded by (f, g) on c_{Gamma_t} and Gamma_pi =
-// sum_ij pi_ij X_i Y_j^T, the Lemma (Appendix D) gives, per feature row,
+// sum_ij pi_ij X_i Y_j^T, the Lemma (Appendix C.1) gives, per feature row,
 //   dX_i = 8 a_i [(s_i + m2_X) X_i + 2 Sigma_X X_i - mu3_X] - 8 a_i m2_Y X_i
 //          - 16 Gamma_pi w_i - 8 q_i X_i,
 //   w_i = sum_j pi_ij Y_j,  q_i = sum_j pi_ij t_j,  mu3_X = sum_k a_k s_k X_k,

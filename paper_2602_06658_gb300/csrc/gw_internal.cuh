@@ -206,6 +206,26 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
              int n_iter, uint64_t seed, float* X, float* sqn, float* basis, float* eigvals,
              void* ws, size_t ws_bytes, cudaStream_t st);
 
+// Stop rule of the Sinkhorn loop: Err of the last measured plan from two
+// consecutive iterates (gw_plan.cu); `part` holds kMargBlocks doubles.
+constexpr int kMargBlocks = 152;
+int run_marginal_error(const float* f0, const float* f1, const float* a, int64_t n,
+                       const float* g0, const float* g1, const float* b, int64_t m, float eps,
+                       bool symmetric, double* part, double* out, cudaStream_t st);
+// rec[GW_EN_NINNER], rec[GW_EN_STOPERR] (err may be null: -1)
+int launch_record_extra(double* rec, int n_inner, const double* err, cudaStream_t st);
+
+// K-Means coarsening and Multiscale-GW (gw_multiscale.cu)
+size_t coarsen_ws_bytes(int64_t n, int64_t k, int D);
+int run_coarsen(const float* X, const float* a, int64_t n, int D, const int64_t* init_idx,
+                int64_t k, int n_iter, float* Xc, float* ac, float* sc, int* assign_out,
+                int64_t* k_out, Carver& ws, cudaStream_t st);
+size_t multiscale_ws_bytes(int64_t n, int64_t m, int D, int E, int64_t kx, int64_t ky, int prec);
+int run_multiscale(const gw_problem& p, const gw_options& oc, const gw_options& of,
+                   const int64_t* init_x, int64_t kx, const int64_t* init_y, int64_t ky,
+                   int km_iter, gw_result& r, double* coarse_energy, void* ws, size_t ws_bytes,
+                   cudaStream_t st);
+
 // logw_i = log(w_i)
 int launch_log(const float* w, int64_t n, float* logw, cudaStream_t st);
 

@@ -1,5 +1,5 @@
 // Plan-weighted reductions of CNT-GW (Algorithm 1's Xtilde / Gamma_{t+1}
-// lines, Theorem 3.3), the moments behind C(alpha, beta) (Lemma, Appendix D),
+// lines, Theorem 3.3), the moments behind C(alpha, beta) (Lemma, Appendix C.1),
 // the marginals and the energy record, FP32 CUDA-core form.
 //
 // The plan pi_ij = a_i b_j exp((f_i + g_j - C_ij)/eps) is rebuilt tile by tile
@@ -329,6 +329,54 @@ __global__ void __launch_bounds__(256)
     Rp[blockIdx.x * 4 + 1] = v1;
     Rp[blockIdx.x * 4 + 2] = v2;
     Rp[blockIdx.x * 4 + 3] = 0.0;
+  }
+}
+
+// Marginal error of the stop rule from consecutive potentials (no extra
+// softmin): for one side with weights w, sum_i w_i |exp(k (p0_i - p1_i) / eps) - 1|.
+// Algorithm 3 (k = 2): p1 = (p0 + S)/2, so the sums of the plan (f^n, g^n)
+// are w exp(2 (p0 - p1) / eps).  Algorithm 2 (k = 1, columns only): the
+// columns of (f^{n+1}, g^n) are b exp((g^n - g^{n+1}) / eps).  Fixed grid,
+// fixed-order sums: deterministic.
+__global__ void __launch_bounds__(256)
+    marg_err_partial_kernel(const float* f0, const float* f1, const float* a, int64_t n,
+                            const float* g0, const float* g1, const float* b, int64_t m,
+                            double kf, double kg, double* part) {
+  const int tid = threadIdx.x;
+  double acc = 0.0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * 256;
+  if (kf != 0.0) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * 256 + tid; i < n; i += stride)
+      acc += static_cast<double>(a[i]) *
+             fabs(expm1(kf * (static_cast<double>(f0[i]) - static_cast<double>(f1[i]))));
+  }
+  for (int64_t j = static_cast<int64_t>(blockIdx.x) * 256 + tid; j < m; j += stride)
+    acc += static_cast<double>(b[j]) *
+           fabs(expm1(kg * (static_cast<double>(g0[j]) - static_cast<double>(g1[j]))));
+  __shared__ double red[8];
+  acc = warp_sum(acc);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double v = 0.0;
+    for (int q = 0; q < 8; ++q) v += red[q];
+    part[blockIdx.x] = v;
+  }
+}
+
+__global__ void marg_err_final_kernel(const double* part, int nb, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double v = 0.0;
+    for (int q = 0; q < nb; ++q) v += part[q];
+    *out = v;
+  }
+}
+
+// rec[GW_EN_NINNER] = iterations run, rec[GW_EN_STOPERR] = *err (or -1)
+__global__ void record_extra_kernel(double* rec, double n_inner, const double* err) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    rec[GW_EN_NINNER] = n_inner;
+    rec[GW_EN_STOPERR] = err ? *err : -1.0;
   }
 }
 
@@ -689,6 +737,25 @@ size_t energy_ws_bytes(int64_t n, int64_t m, int D, int E, int prec) {
   c.take<float>(static_cast<size_t>(m));        // log b
   c.take<double>(static_cast<size_t>(kRedBlocks) * 4);
   return c.used() + softmin_ws_bytes(n, m, D, prec) + 256;
+}
+
+int run_marginal_error(const float* f0, const float* f1, const float* a, int64_t n,
+                       const float* g0, const float* g1, const float* b, int64_t m, float eps,
+                       bool symmetric, double* part, double* out, cudaStream_t st) {
+  const double inv = 1.0 / static_cast<double>(eps);
+  marg_err_partial_kernel<<<kMargBlocks, 256, 0, st>>>(f0, f1, a, n, g0, g1, b, m,
+                                                       symmetric ? 2.0 * inv : 0.0,
+                                                       symmetric ? 2.0 * inv : inv, part);
+  GW_LAUNCH_CHECK();
+  marg_err_final_kernel<<<1, 32, 0, st>>>(part, kMargBlocks, out);
+  GW_LAUNCH_CHECK();
+  return GW_OK;
+}
+
+int launch_record_extra(double* rec, int n_inner, const double* err, cudaStream_t st) {
+  record_extra_kernel<<<1, 32, 0, st>>>(rec, static_cast<double>(n_inner), err);
+  GW_LAUNCH_CHECK();
+  return GW_OK;
 }
 
 int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* logb_pre,

@@ -410,7 +410,7 @@ def _energy_of_points(x, y, a, b, eps, G0, f0, g0, n_outer=80):
 
 
 def test_gradient_matches_finite_differences_of_resolved_energy():
-    """Envelope theorem (Appendix B.5): the closed-form gradient equals the
+    """Envelope theorem (Appendix B.6): the closed-form gradient equals the
     derivative of the re-solved EGW value."""
     g = W.rng(91)
     N, M = 7, 6
@@ -567,3 +567,65 @@ def test_multiscale_reaches_the_direct_solution():
     assert abs(ms["history"][-1]["E"] - direct["history"][-1]["E"]) < 1e-4 * abs(direct["history"][-1]["E"])
     assert ms["coarse"]["history"][-1]["E"] > 0
     assert len(ms["ac"]) <= 30 and abs(ms["ac"].sum() - 1) < 1e-12
+
+
+# ---------------------------------------------------------------- Algorithm 6 and the hybrid stop
+
+def small_uniform_problem(seed=3, n=40, m=35):
+    g = W.rng(seed)
+    x = g.uniform(0, 1, (n, 2)) * [1.0, 0.6]
+    y = g.uniform(0, 1, (m, 2)) * [0.9, 0.7]
+    a, b = np.full(n, 1 / n), np.full(m, 1 / m)
+    return a, b, O.center(x, a), O.center(y, b)
+
+
+def test_adaptive_never_doubles_on_converged_sinkhorn_and_reaches_the_converged_energy():
+    """Algorithm 6 (Appendix B.4): with Sinkhorn converged at every step the
+    energy cannot increase (Prop. 4.4), so the count never doubles; from
+    n_inner^0 = 1 the schedule grows (doubling only after an increase) and
+    reaches the energy of the converged solver (the paper's convergence
+    guarantee; this problem has one minimum reachable from Gamma_0 = 0)."""
+    a, b, X, Y = small_uniform_problem()
+    eps = 0.05
+    ref = O.cnt_gw(a, b, X, Y, eps, 60, 500)
+    same = O.cnt_gw(a, b, X, Y, eps, 60, 500, adaptive=True, n_inner_max=4096, adapt_rtol=1e-12)
+    assert all(h["n_inner"] == 500 for h in same["history"])
+    ad = O.cnt_gw(a, b, X, Y, eps, 60, 1, adaptive=True, n_inner_max=4096)
+    n_seq = [h["n_inner"] for h in ad["history"]]
+    E_seq = [h["E"] for h in ad["history"]]
+    assert n_seq[0] == 1 and n_seq[-1] > 64
+    for t in range(1, len(n_seq)):
+        assert n_seq[t] in (n_seq[t - 1], min(2 * n_seq[t - 1], 4096))
+        if t >= 2 and n_seq[t] > n_seq[t - 1]:
+            assert E_seq[t - 1] > E_seq[t - 2]        # a doubling follows an increase
+    assert abs(ad["history"][-1]["E"] - ref["history"][-1]["E"]) <= 1e-10 * ref["history"][-1]["E"]
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_hybrid_stop_rule(symmetric):
+    """Appendix D.1 hybrid stop: below tol at the stop and not at the check
+    before; tol = 0 runs the maximum and equals plain Sinkhorn.  The measured
+    plan is the one whose marginals the last iteration evaluated: for
+    Algorithm 3 the row sums of (f^n, g^n) are a exp(2 (f^n - f^{n+1}) / eps)
+    (f^{n+1} averages f^n with S_b(g^n)); for Algorithm 2 the rows of
+    (f^{n+1}, g^n) are exact."""
+    a, b, X, Y = small_uniform_problem()
+    eps = 0.05
+    C = O.cost_gamma(X, Y, O.cnt_gw(a, b, X, Y, eps, 10, 300)["Gamma"])
+    f0, g0 = np.zeros(len(a)), np.zeros(len(b))
+    f, g, n_run, err = O.sinkhorn_stop(a, b, C, eps, 3000, f0, g0, symmetric, 1e-8, 7)
+    assert n_run % 7 == 0 and n_run < 3000 and err < 1e-8
+    _, _, n_prev, err_prev = O.sinkhorn_stop(a, b, C, eps, n_run - 7, f0, g0, symmetric, 0.0, 7)
+    assert n_prev == n_run - 7 and err_prev >= 1e-8
+    fz, gz, nz, _ = O.sinkhorn_stop(a, b, C, eps, 50, f0, g0, symmetric, 0.0, 5)
+    fs, gs = O.sinkhorn(a, b, C, eps, 50, f0, g0, symmetric)
+    assert nz == 50 and np.array_equal(fz, fs) and np.array_equal(gz, gs)
+    fn, gn = O.sinkhorn(a, b, C, eps, 12, f0, g0, symmetric)
+    f1, g1 = O.sinkhorn(a, b, C, eps, 1, fn, gn, symmetric)
+    if symmetric:
+        rows = O.plan(a, b, fn, gn, C, eps).sum(1)
+        np.testing.assert_allclose(rows, a * np.exp(2 * (fn - f1) / eps), rtol=1e-12)
+    else:
+        np.testing.assert_allclose(O.plan(a, b, f1, gn, C, eps).sum(1), a, rtol=1e-12)
+        cols = O.plan(a, b, f1, gn, C, eps).sum(0)
+        np.testing.assert_allclose(cols, b * np.exp((gn - g1) / eps), rtol=1e-12)
