@@ -37,6 +37,7 @@ __all__ = [
     "grad_features", "center_vjp", "grad_x_squared", "grad_x_lifted",
     "grad_x_bruteforce", "permutation_ot",
     "kmeans_coarsen", "kmeans_objective", "interpolate", "multiscale_gw", "sinkhorn_stop",
+    "final_plan", "sgw", "sgw_grad_features",
 ]
 
 F64 = np.float64
@@ -623,6 +624,44 @@ def grad_x_bruteforce(pi, x, y, a, b, kind="sqeuclid", param=2.0):
             coef += pi[i, j] * (Dkl * pi).sum(1)
         out[i] = 4.0 * coef @ dc
     return out
+
+
+# --------------------------------------------------------------------------
+# Sinkhorn GW divergence (Section 4.1, "Entropic Bias and Symmetric Debiasing")
+# --------------------------------------------------------------------------
+
+def final_plan(res, a, b, X, Y, Gamma0=None):
+    """The plan a cnt_gw result (record=True) ends on: its potentials on the
+    cost of the Gamma that preceded the last update."""
+    hist = res["history"]
+    if len(hist) >= 2:
+        Gt = hist[-2]["Gamma"]
+    else:
+        Gt = np.zeros((X.shape[1], Y.shape[1])) if Gamma0 is None else np.asarray(Gamma0, F64)
+    return plan(a, b, res["f"], res["g"], cost_gamma(X, Y, Gt), res["eps"][-1])
+
+
+def sgw(a, b, X, Y, eps, n_outer, n_inner, **kw):
+    """SGW_eps(alpha, beta) = GW_eps(alpha, beta) - (GW_eps(alpha, alpha)
+    + GW_eps(beta, beta)) / 2, each GW_eps the final energy E = L + eps KL of a
+    CNT-GW solve with the same options.  Returns dict(SGW, ab, aa, bb)."""
+    ab = cnt_gw(a, b, X, Y, eps, n_outer, n_inner, **kw)
+    aa = cnt_gw(a, a, X, X, eps, n_outer, n_inner, **kw)
+    bb = cnt_gw(b, b, Y, Y, eps, n_outer, n_inner, **kw)
+    E = lambda r: r["history"][-1]["E"]
+    return {"SGW": E(ab) - 0.5 * (E(aa) + E(bb)), "ab": ab, "aa": aa, "bb": bb}
+
+
+def sgw_grad_features(pi_ab, pi_aa, X, Y, a, b):
+    """Gradient of SGW with respect to the source features X with every plan
+    held at its optimum (envelope theorem, Appendix B.6).  GW_eps(alpha,
+    alpha) depends on X through both of its sides: the target side is the
+    source side of the transposed problem (plan pi^T)."""
+    g_ab = grad_features(pi_ab, cross_covariance(pi_ab, X, Y), X, Y, a, b)
+    g_src = grad_features(pi_aa, cross_covariance(pi_aa, X, X), X, X, a, a)
+    pt = np.asarray(pi_aa, F64).T
+    g_tgt = grad_features(pt, cross_covariance(pt, X, X), X, X, a, a)
+    return g_ab - 0.5 * (g_src + g_tgt)
 
 
 # --------------------------------------------------------------------------

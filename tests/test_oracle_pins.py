@@ -629,3 +629,72 @@ def test_hybrid_stop_rule(symmetric):
         np.testing.assert_allclose(O.plan(a, b, f1, gn, C, eps).sum(1), a, rtol=1e-12)
         cols = O.plan(a, b, f1, gn, C, eps).sum(0)
         np.testing.assert_allclose(cols, b * np.exp((gn - g1) / eps), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- SGW divergence (Section 4.1)
+
+def _sgw_converged(a, b, X, Y, eps, n_outer=80):
+    return O.sgw(a, b, X, Y, eps, n_outer, 300, symmetric=False)
+
+
+def test_sgw_is_nonnegative_and_vanishes_for_isometric_measures():
+    """Section 4.1 theorem on SGW: for CNT costs SGW_eps >= 0, and = 0 when
+    alpha and beta are isometric (here a rotated, reflected, translated and
+    reordered copy with the same weights)."""
+    for seed in range(4):
+        g = W.rng(200 + seed)
+        n, m = 12, 10
+        x = g.standard_normal((n, 2)) * [0.4, 0.2]       # scaled so the plans converge
+        y = g.standard_normal((m, 2)) * [0.28, 0.24]
+        a, b = W.random_weights(n, 300 + seed, 0.3), W.random_weights(m, 400 + seed, 0.3)
+        res = _sgw_converged(a, b, O.center(x, a), O.center(y, b), 0.1)
+        assert res["SGW"] >= -1e-9, (seed, res["SGW"])
+        assert res["SGW"] > 1e-4                      # these clouds are not isometric
+    g = W.rng(9)
+    n = 11
+    x = g.standard_normal((n, 3)) * [0.4, 0.24, 0.12]
+    a = W.random_weights(n, 10, 0.3)
+    Q = W.random_orthogonal(3, W.rng(11))
+    perm = g.permutation(n)
+    y = (x @ Q.T + [0.3, -1.0, 2.0])[perm]
+    res = _sgw_converged(a, a[perm], O.center(x, a), O.center(y, a[perm]), 0.1)
+    assert abs(res["SGW"]) < 1e-9
+
+
+def test_sgw_gradient_matches_finite_differences():
+    """Envelope theorem for the three solves: the closed-form SGW gradient
+    (the self term differentiated through both of its sides) equals central
+    differences of the re-solved divergence."""
+    g = W.rng(93)
+    N, M = 7, 6
+    x, y = g.standard_normal((N, 2)) * 0.4, g.standard_normal((M, 2)) * 0.32
+    a, b = W.uniform_weights(N), W.uniform_weights(M)
+    eps = 0.2
+
+    def solve(xx, warm=None):
+        X, Y = O.center(xx, a), O.center(y, b)
+        kw = dict(symmetric=False)
+        if warm is None:
+            return O.sgw(a, b, X, Y, eps, 80, 300, **kw), X, Y
+        ab = O.cnt_gw(a, b, X, Y, eps, 60, 300, Gamma0=warm["ab"]["Gamma"], f0=warm["ab"]["f"],
+                      g0=warm["ab"]["g"], **kw)
+        aa = O.cnt_gw(a, a, X, X, eps, 60, 300, Gamma0=warm["aa"]["Gamma"], f0=warm["aa"]["f"],
+                      g0=warm["aa"]["g"], **kw)
+        return ab["history"][-1]["E"] - 0.5 * (aa["history"][-1]["E"] + warm["bb"]["history"][-1]["E"])
+
+    res, X, Y = solve(x)
+    # converge the final plans tightly, then differentiate
+    Cab = O.cost_gamma(X, Y, res["ab"]["Gamma"])
+    f, gg = O.sinkhorn(a, b, Cab, eps, 3000, res["ab"]["f"], res["ab"]["g"], symmetric=False)
+    pi_ab = O.plan(a, b, f, gg, Cab, eps)
+    Caa = O.cost_gamma(X, X, res["aa"]["Gamma"])
+    f, gg = O.sinkhorn(a, a, Caa, eps, 3000, res["aa"]["f"], res["aa"]["g"], symmetric=False)
+    pi_aa = O.plan(a, a, f, gg, Caa, eps)
+    closed = O.center_vjp(O.sgw_grad_features(pi_ab, pi_aa, X, Y, a, b), a)
+    h = 1e-5
+    for (i, d) in [(0, 0), (2, 1), (5, 0)]:
+        xp, xm = x.copy(), x.copy()
+        xp[i, d] += h
+        xm[i, d] -= h
+        fd = (solve(xp, res) - solve(xm, res)) / (2 * h)
+        assert abs(fd - closed[i, d]) < 1e-6 * max(1.0, np.abs(closed).max()), (i, d, fd, closed[i, d])
