@@ -334,6 +334,50 @@ size_t gw_multiscale_workspace_size(int64_t n, int64_t m, int D, int E, int64_t 
                                     int prec);
 
 /*
+ * gw_kernel_gw -- Kernel-GW (Algorithm 5, Appendix B.3): the exact
+ * kernelised EGW scheme for small N with dense matrices.  CX (n x n) and
+ * CY (m x m): CNT cost matrices (device, FP32, row-major); a, b: weights.
+ * K^X, K^Y = Algorithm 4 (base index 0, weighted double centering); pi^0 =
+ * a b^T; each outer step: C = -4 K^X_ii K^Y_jj - 16 K^X pi K^Y, n_inner
+ * Sinkhorn iterations on C (Algorithm 3, or 2 with symmetric = 0), warm
+ * started, then pi = a b^T exp((f + g - C)/eps).  Options used: eps,
+ * eps_final, n_outer, n_inner, symmetric, record, f0, g0 (prec, Gamma0 and
+ * the adaptive / stop fields are ignored).  The two GEMMs per step run in
+ * cuBLAS with FP32-emulating BF16x9 tensor-core arithmetic (opened at first
+ * use; GW_EUNSUPPORTED if libcublas is absent).  Outputs (device): pi
+ * (n x m), f, g, energy (GW_EN_LEN record of the final plan, Lemma in kernel
+ * form), history (n_outer x GW_EN_LEN when record = 1).  Enqueued on
+ * `stream`.  Memory: O(n m + n^2 + m^2), n m <= 2^31.
+ * Workspace: gw_kernel_gw_workspace_size(n, m).
+ */
+int gw_kernel_gw(const float* CX, const float* CY, const float* a, const float* b, int64_t n,
+                 int64_t m, const gw_options* o, float* pi, float* f, float* g, double* energy,
+                 double* history, void* ws, size_t ws_bytes, gw_stream_t stream);
+size_t gw_kernel_gw_workspace_size(int64_t n, int64_t m);
+
+/*
+ * gw_sgw -- Sinkhorn GW divergence (Section 4.1):
+ *   SGW_eps(alpha, beta) = GW_eps(alpha, beta) - (GW_eps(alpha, alpha) + GW_eps(beta, beta)) / 2,
+ * each GW_eps the final energy E (GW_EN_E) of a gw_solve with options `o`
+ * (record ignored; Gamma0 / f0 / g0 apply to the alpha-beta solve only, the
+ * two self solves start from zero).  Writes sgw (device, 4 doubles): SGW,
+ * GW(alpha,beta), GW(alpha,alpha), GW(beta,beta); records (device,
+ * 3 x GW_EN_LEN, may be NULL): the three final energy records.
+ * Gradient (dX not NULL): d SGW / d X (n x D, device) with every plan held at
+ * its optimum (envelope theorem, Appendix B.6) at the schedule's last eps;
+ * the self term is differentiated through both of its sides.  With x (raw
+ * points, n x dx_dim) and the lift's basis/eigvals also d SGW / d x into dx,
+ * as gw_grad_x.  Enqueued on `stream` (the three solves in sequence).
+ * Workspace: gw_sgw_workspace_size(n, m, D, E, prec, want_grad, dx_dim).
+ * Errors: as gw_solve and gw_grad_x.
+ */
+int gw_sgw(const gw_problem* p, const gw_options* o, double* sgw, double* records, float* dX,
+           const float* x, int dx_dim, int kind, float param, const float* basis,
+           const float* eigvals, float* dx, void* ws, size_t ws_bytes, gw_stream_t stream);
+size_t gw_sgw_workspace_size(int64_t n, int64_t m, int D, int E, int prec, int want_grad,
+                             int dx_dim);
+
+/*
  * Request server (continuous batching; no counterpart in the paper, which
  * solves one problem at a time).  Requests are admitted in arrival order as
  * soon as a worker slot is free and their device memory fits in the pool the

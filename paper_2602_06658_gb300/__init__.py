@@ -20,7 +20,7 @@ __all__ = [
     "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
     "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
     "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
-    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale",
+    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw",
 ]
 
 GW_OK = 0
@@ -91,6 +91,14 @@ lib.gw_coarsen.argtypes = [_p, _p, _i64, _int, _p, _i64, _int, _p, _p, _p, _p,
 lib.gw_multiscale.argtypes = [ctypes.POINTER(GwProblem), ctypes.POINTER(GwOptions),
                               ctypes.POINTER(GwOptions), _p, _i64, _p, _i64, _int,
                               ctypes.POINTER(GwResult), _p, _p, _sz, _p]
+lib.gw_kernel_gw.argtypes = [_p, _p, _p, _p, _i64, _i64, ctypes.POINTER(GwOptions), _p, _p, _p, _p,
+                             _p, _p, _sz, _p]
+lib.gw_kernel_gw_workspace_size.argtypes = [_i64, _i64]
+lib.gw_kernel_gw_workspace_size.restype = _sz
+lib.gw_sgw.argtypes = [ctypes.POINTER(GwProblem), ctypes.POINTER(GwOptions), _p, _p, _p, _p, _int,
+                       _int, _f, _p, _p, _p, _p, _sz, _p]
+lib.gw_sgw_workspace_size.argtypes = [_i64, _i64, _int, _int, _int, _int, _int]
+lib.gw_sgw_workspace_size.restype = _sz
 lib.gw_multiscale_workspace_size.argtypes = [_i64, _i64, _int, _int, _i64, _i64, _int]
 lib.gw_multiscale_workspace_size.restype = _sz
 class GwRequest(ctypes.Structure):
@@ -124,7 +132,7 @@ lib.gw_version.restype = _int
 lib.gw_kernel_launches.argtypes = [_int]
 lib.gw_kernel_launches.restype = ctypes.c_ulonglong
 for _name in ("gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve", "gw_lift", "gw_grad_x",
-              "gw_coarsen", "gw_multiscale"):
+              "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw"):
     getattr(lib, _name).restype = _int
 
 
@@ -354,6 +362,60 @@ def gw_multiscale(X, Y, s, t, a, b, eps, init_x, init_y, km_iter, coarse_outer, 
                              _ptr(_idx64(init_x, "init_x")), kx, _ptr(_idx64(init_y, "init_y")), ky,
                              int(km_iter), ctypes.byref(R), _ptr(out["coarse_energy"]), _ptr(ws),
                              ws.numel(), _stream(stream)))
+    return out
+
+
+def gw_kernel_gw(CX, CY, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=True, record=True,
+                 f0=None, g0=None, ws=None, stream=None):
+    """Kernel-GW exact mode (Algorithm 5; gw.h: gw_kernel_gw) on dense cost
+    matrices.  Returns dict(pi, f, g, energy, history) of device tensors."""
+    n, m = CX.shape[0], CY.shape[0]
+    dev = CX.device
+    out = {"pi": torch.empty(n, m, dtype=torch.float32, device=dev),
+           "f": torch.empty(n, dtype=torch.float32, device=dev),
+           "g": torch.empty(m, dtype=torch.float32, device=dev),
+           "energy": torch.empty(EN_LEN, dtype=torch.float64, device=dev),
+           "history": torch.empty(n_outer, EN_LEN, dtype=torch.float64, device=dev)
+           if record else None}
+    if ws is None:
+        ws = workspace(lib.gw_kernel_gw_workspace_size(n, m), dev)
+    O = GwOptions(float(eps), float(eps_final), int(n_outer), int(n_inner), int(bool(symmetric)),
+                  PREC_FP32, int(bool(record)), 0, None, _ptr(_f32(f0, "f0")), _ptr(_f32(g0, "g0")),
+                  0, 0, 0.0, 0.0, 1)
+    _check(lib.gw_kernel_gw(_ptr(_f32(CX, "CX")), _ptr(_f32(CY, "CY")), _ptr(_f32(a, "a")),
+                            _ptr(_f32(b, "b")), n, m, ctypes.byref(O), _ptr(out["pi"]),
+                            _ptr(out["f"]), _ptr(out["g"]), _ptr(out["energy"]),
+                            _ptr(out["history"]), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def gw_sgw(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=True,
+           prec=PREC_FP32, use_graph=True, grad=False, x=None, kind=PEN_SQEUCLID, param=2.0,
+           basis=None, eigvals=None, ws=None, stream=None, **solve_kw):
+    """Sinkhorn GW divergence (gw.h: gw_sgw).  Returns dict(sgw (4: SGW and
+    the three GW values), records (3 x EN_LEN), dX, dx) of device tensors."""
+    n, D = X.shape
+    m, E = Y.shape
+    dev = X.device
+    out = {"sgw": torch.empty(4, dtype=torch.float64, device=dev),
+           "records": torch.empty(3, EN_LEN, dtype=torch.float64, device=dev),
+           "dX": torch.empty(n, D, dtype=torch.float32, device=dev) if grad else None,
+           "dx": torch.empty(n, x.shape[1], dtype=torch.float32, device=dev)
+           if (grad and x is not None) else None}
+    dxd = int(x.shape[1]) if (grad and x is not None) else 0
+    if ws is None:
+        ws = workspace(lib.gw_sgw_workspace_size(n, m, D, E, int(prec), int(bool(grad)), dxd), dev)
+    P = GwProblem(_ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
+                  _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
+    O = GwOptions(float(eps), float(eps_final), int(n_outer), int(n_inner), int(bool(symmetric)),
+                  int(prec), 0, int(bool(use_graph)), None, None, None,
+                  int(bool(solve_kw.get("adaptive", False))), int(solve_kw.get("n_inner_max", 0)),
+                  float(solve_kw.get("adapt_rtol", 0.0)), float(solve_kw.get("stop_tol", 0.0)),
+                  int(solve_kw.get("stop_every", 1)))
+    _check(lib.gw_sgw(ctypes.byref(P), ctypes.byref(O), _ptr(out["sgw"]), _ptr(out["records"]),
+                      _ptr(out["dX"]), _ptr(_f32(x, "x")) if grad else None, dxd, int(kind),
+                      float(param), _ptr(_f32(basis, "basis")), _ptr(_f32(eigvals, "eigvals")),
+                      _ptr(out["dx"]), _ptr(ws), ws.numel(), _stream(stream)))
     return out
 
 

@@ -532,6 +532,67 @@ int gw_coarsen(const float* X, const float* a, int64_t n, int D, const int64_t* 
                      reinterpret_cast<cudaStream_t>(stream));
 }
 
+size_t gw_kernel_gw_workspace_size(int64_t n, int64_t m) {
+  if (n < 1 || m < 1) return 0;
+  return kernel_gw_ws_bytes(n, m);
+}
+
+int gw_kernel_gw(const float* CX, const float* CY, const float* a, const float* b, int64_t n,
+                 int64_t m, const gw_options* o, float* pi, float* f, float* g, double* energy,
+                 double* history, void* ws, size_t ws_bytes, gw_stream_t stream) {
+  gw::set_error("");
+  NONNULL(CX);
+  NONNULL(CY);
+  NONNULL(a);
+  NONNULL(b);
+  NONNULL(o);
+  NONNULL(pi);
+  NONNULL(f);
+  NONNULL(g);
+  NONNULL(energy);
+  GW_REQUIRE(n >= 1 && m >= 1, GW_EINVAL, "n, m must be >= 1");
+  GW_TRY(check_eps(o->eps));
+  GW_REQUIRE(o->eps_final <= 0.0f || isfinite(o->eps_final), GW_EINVAL, "eps_final not finite");
+  GW_REQUIRE(o->n_outer >= 1 && o->n_inner >= 1, GW_EINVAL, "n_outer, n_inner must be >= 1");
+  GW_REQUIRE(!o->record || history != nullptr, GW_EINVAL, "record = 1 needs history");
+  const size_t need = kernel_gw_ws_bytes(n, m);
+  GW_REQUIRE(ws != nullptr && ws_bytes >= need, GW_ENOMEM,
+             "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
+  return run_kernel_gw(CX, CY, a, b, n, m, *o, pi, f, g, energy, history, ws, ws_bytes,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t gw_sgw_workspace_size(int64_t n, int64_t m, int D, int E, int prec, int want_grad,
+                             int dx_dim) {
+  if (n < 1 || m < 1 || D < 1 || E < 1 || D > GW_MAX_FEATURES || E > GW_MAX_FEATURES) return 0;
+  return sgw_ws_bytes(n, m, D, E, prec, want_grad != 0, want_grad ? dx_dim : 0);
+}
+
+int gw_sgw(const gw_problem* p, const gw_options* o, double* sgw, double* records, float* dX,
+           const float* x, int dx_dim, int kind, float param, const float* basis,
+           const float* eigvals, float* dx, void* ws, size_t ws_bytes, gw_stream_t stream) {
+  gw::set_error("");
+  NONNULL(p);
+  NONNULL(o);
+  NONNULL(sgw);
+  GW_TRY(check_dims(p->n, p->m, p->D, p->E));
+  GW_REQUIRE(p->n >= 1 && p->m >= 1, GW_EINVAL, "n, m must be >= 1");
+  if (dX != nullptr && x != nullptr) {
+    GW_REQUIRE(dx_dim >= 1 && dx_dim <= 4, GW_EUNSUPPORTED, "points of dimension 1..4 (got %d)", dx_dim);
+    NONNULL(dx);
+    NONNULL(basis);
+    NONNULL(eigvals);
+    GW_REQUIRE(kind == GW_PEN_SQEUCLID || kind == GW_PEN_POWER || kind == GW_PEN_GAUSS, GW_EINVAL,
+               "unknown penalty %d", kind);
+  }
+  const int dxd = (dX != nullptr && x != nullptr) ? dx_dim : 0;
+  const size_t need = sgw_ws_bytes(p->n, p->m, p->D, p->E, o->prec, dX != nullptr, dxd);
+  GW_REQUIRE(ws != nullptr && ws_bytes >= need, GW_ENOMEM,
+             "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
+  return run_sgw(*p, *o, sgw, records, dX, dxd ? x : nullptr, dxd, kind, param, basis, eigvals,
+                 dx, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
 size_t gw_multiscale_workspace_size(int64_t n, int64_t m, int D, int E, int64_t kx, int64_t ky,
                                     int prec) {
   if (n < 1 || m < 1 || kx < 1 || ky < 1 || D < 1 || E < 1) return 0;

@@ -215,6 +215,18 @@ int run_marginal_error(const float* f0, const float* f1, const float* a, int64_t
 // rec[GW_EN_NINNER], rec[GW_EN_STOPERR] (err may be null: -1)
 int launch_record_extra(double* rec, int n_inner, const double* err, cudaStream_t st);
 
+// Kernel-GW exact mode (gw_kernelgw.cu)
+size_t kernel_gw_ws_bytes(int64_t n, int64_t m);
+int run_kernel_gw(const float* CX, const float* CY, const float* a, const float* b, int64_t n,
+                  int64_t m, const gw_options& o, float* pi_out, float* f_out, float* g_out,
+                  double* energy, double* history, void* ws, size_t ws_bytes, cudaStream_t st);
+
+// SGW divergence (gw_sgw.cu)
+size_t sgw_ws_bytes(int64_t n, int64_t m, int D, int E, int prec, bool grad, int dx_dim);
+int run_sgw(const gw_problem& p, const gw_options& o, double* out, double* records, float* dX,
+            const float* x, int dx_dim, int kind, float param, const float* basis,
+            const float* eigvals, float* dx, void* ws, size_t ws_bytes, cudaStream_t st);
+
 // K-Means coarsening and Multiscale-GW (gw_multiscale.cu)
 size_t coarsen_ws_bytes(int64_t n, int64_t k, int D);
 int run_coarsen(const float* X, const float* a, int64_t n, int D, const int64_t* init_idx,
