@@ -334,6 +334,21 @@ size_t gw_multiscale_workspace_size(int64_t n, int64_t m, int D, int E, int64_t 
                                     int prec);
 
 /*
+ * gw_transfer -- color / UV transfer (Appendix E): the barycentric projection
+ *   out_j = sum_i pi_ij U_i / b_j  of source attributes U (n x k, device,
+ *   1 <= k <= 16) through the plan pi_ij = a_i b_j exp((f_i + g_j - c_ij)/eps)
+ *   on c_{Gamma_t} (the state gw_solve returns: f, g, Gamma_plan).  out (m x k,
+ *   device); mass (m, device, may be NULL) receives the column sums of pi.
+ *   Enqueued on `stream`; deterministic.
+ * Workspace: gw_transfer_workspace_size(n, m, D, k).
+ * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
+ */
+int gw_transfer(const gw_problem* p, const float* f, const float* g, const double* Gamma_t,
+                float eps, const float* U, int k, float* out, float* mass, void* ws,
+                size_t ws_bytes, gw_stream_t stream);
+size_t gw_transfer_workspace_size(int64_t n, int64_t m, int D, int k);
+
+/*
  * gw_kernel_gw -- Kernel-GW (Algorithm 5, Appendix B.3): the exact
  * kernelised EGW scheme for small N with dense matrices.  CX (n x n) and
  * CY (m x m): CNT cost matrices (device, FP32, row-major); a, b: weights.

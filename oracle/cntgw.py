@@ -37,7 +37,7 @@ __all__ = [
     "grad_features", "center_vjp", "grad_x_squared", "grad_x_lifted",
     "grad_x_bruteforce", "permutation_ot",
     "kmeans_coarsen", "kmeans_objective", "interpolate", "multiscale_gw", "sinkhorn_stop",
-    "final_plan", "sgw", "sgw_grad_features",
+    "final_plan", "sgw", "sgw_grad_features", "barycentric_transfer",
 ]
 
 F64 = np.float64
@@ -624,6 +624,16 @@ def grad_x_bruteforce(pi, x, y, a, b, kind="sqeuclid", param=2.0):
             coef += pi[i, j] * (Dkl * pi).sum(1)
         out[i] = 4.0 * coef @ dc
     return out
+
+
+# --------------------------------------------------------------------------
+# Color / UV transfer (Appendix E, "Transport plan visualizations")
+# --------------------------------------------------------------------------
+
+def barycentric_transfer(pi, U, b):
+    """C_Y(y_j) = sum_i C_X(x_i) pi_ij / (a_i b_j) a_i = (pi^T U)_j / b_j for
+    source attributes U (colors, UV coordinates; N x k)."""
+    return (np.asarray(pi, F64).T @ np.asarray(U, F64)) / np.asarray(b, F64)[:, None]
 
 
 # --------------------------------------------------------------------------

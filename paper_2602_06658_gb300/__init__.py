@@ -20,7 +20,7 @@ __all__ = [
     "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
     "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
     "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
-    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw",
+    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer",
 ]
 
 GW_OK = 0
@@ -91,6 +91,10 @@ lib.gw_coarsen.argtypes = [_p, _p, _i64, _int, _p, _i64, _int, _p, _p, _p, _p,
 lib.gw_multiscale.argtypes = [ctypes.POINTER(GwProblem), ctypes.POINTER(GwOptions),
                               ctypes.POINTER(GwOptions), _p, _i64, _p, _i64, _int,
                               ctypes.POINTER(GwResult), _p, _p, _sz, _p]
+lib.gw_transfer.argtypes = [ctypes.POINTER(GwProblem), _p, _p, _p, _f, _p, _int, _p, _p, _p, _sz,
+                            _p]
+lib.gw_transfer_workspace_size.argtypes = [_i64, _i64, _int, _int]
+lib.gw_transfer_workspace_size.restype = _sz
 lib.gw_kernel_gw.argtypes = [_p, _p, _p, _p, _i64, _i64, ctypes.POINTER(GwOptions), _p, _p, _p, _p,
                              _p, _p, _sz, _p]
 lib.gw_kernel_gw_workspace_size.argtypes = [_i64, _i64]
@@ -132,7 +136,7 @@ lib.gw_version.restype = _int
 lib.gw_kernel_launches.argtypes = [_int]
 lib.gw_kernel_launches.restype = ctypes.c_ulonglong
 for _name in ("gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve", "gw_lift", "gw_grad_x",
-              "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw"):
+              "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer", "gw_transfer"):
     getattr(lib, _name).restype = _int
 
 
@@ -363,6 +367,25 @@ def gw_multiscale(X, Y, s, t, a, b, eps, init_x, init_y, km_iter, coarse_outer, 
                              int(km_iter), ctypes.byref(R), _ptr(out["coarse_energy"]), _ptr(ws),
                              ws.numel(), _stream(stream)))
     return out
+
+
+def gw_transfer(X, Y, s, t, a, b, f, g, Gamma_t, eps, U, ws=None, stream=None):
+    """Color / UV transfer (Appendix E; gw.h: gw_transfer).  Returns (out, mass):
+    out_j = sum_i pi_ij U_i / b_j and the plan's column sums."""
+    n, D = X.shape
+    m, E = Y.shape
+    k = int(U.shape[1])
+    dev = X.device
+    out = torch.empty(m, k, dtype=torch.float32, device=dev)
+    mass = torch.empty(m, dtype=torch.float32, device=dev)
+    if ws is None:
+        ws = workspace(lib.gw_transfer_workspace_size(n, m, D, k), dev)
+    P = GwProblem(_ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
+                  _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
+    _check(lib.gw_transfer(ctypes.byref(P), _ptr(_f32(f, "f")), _ptr(_f32(g, "g")),
+                           _ptr(_f64(Gamma_t, "Gamma_t")), float(eps), _ptr(_f32(U, "U")), k,
+                           _ptr(out), _ptr(mass), _ptr(ws), ws.numel(), _stream(stream)))
+    return out, mass
 
 
 def gw_kernel_gw(CX, CY, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=True, record=True,

@@ -532,6 +532,37 @@ int gw_coarsen(const float* X, const float* a, int64_t n, int D, const int64_t* 
                      reinterpret_cast<cudaStream_t>(stream));
 }
 
+size_t gw_transfer_workspace_size(int64_t n, int64_t m, int D, int k) {
+  if (n < 1 || m < 1 || D < 1 || D > GW_MAX_FEATURES || k < 1 || k > 16) return 0;
+  return transfer_ws_bytes(n, m, D, k);
+}
+
+int gw_transfer(const gw_problem* p, const float* f, const float* g, const double* Gamma_t,
+                float eps, const float* U, int k, float* out, float* mass, void* ws,
+                size_t ws_bytes, gw_stream_t stream) {
+  gw::set_error("");
+  NONNULL(p);
+  GW_TRY(check_dims(p->n, p->m, p->D, p->E));
+  GW_REQUIRE(p->n >= 1, GW_EINVAL, "n must be >= 1");
+  GW_TRY(check_eps(eps));
+  GW_REQUIRE(k >= 1 && k <= 16, GW_EUNSUPPORTED, "k must be in [1, 16] (got %d)", k);
+  NONNULL(p->X);
+  NONNULL(p->Y);
+  NONNULL(p->s);
+  NONNULL(p->t);
+  NONNULL(p->a);
+  NONNULL(p->b);
+  NONNULL(f);
+  NONNULL(g);
+  NONNULL(Gamma_t);
+  NONNULL(U);
+  NONNULL(out);
+  GW_REQUIRE(reinterpret_cast<uintptr_t>(ws) % 256 == 0, GW_ENOMEM, "workspace must be 256-byte aligned");
+  Carver c(ws, ws_bytes);
+  return run_transfer(*p, f, g, Gamma_t, eps, U, k, out, mass, c,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
 size_t gw_kernel_gw_workspace_size(int64_t n, int64_t m) {
   if (n < 1 || m < 1) return 0;
   return kernel_gw_ws_bytes(n, m);

@@ -215,6 +215,12 @@ int run_marginal_error(const float* f0, const float* f1, const float* a, int64_t
 // rec[GW_EN_NINNER], rec[GW_EN_STOPERR] (err may be null: -1)
 int launch_record_extra(double* rec, int n_inner, const double* err, cudaStream_t st);
 
+// Color / UV transfer (gw_transfer.cu)
+size_t transfer_ws_bytes(int64_t n, int64_t m, int D, int k);
+int run_transfer(const gw_problem& p, const float* f, const float* g, const double* Gamma_t,
+                 float eps, const float* U, int k, float* out, float* mass, Carver& ws,
+                 cudaStream_t st);
+
 // Kernel-GW exact mode (gw_kernelgw.cu)
 size_t kernel_gw_ws_bytes(int64_t n, int64_t m);
 int run_kernel_gw(const float* CX, const float* CY, const float* a, const float* b, int64_t n,

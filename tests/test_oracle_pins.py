@@ -698,3 +698,21 @@ def test_sgw_gradient_matches_finite_differences():
         xm[i, d] -= h
         fd = (solve(xp, res) - solve(xm, res)) / (2 * h)
         assert abs(fd - closed[i, d]) < 1e-6 * max(1.0, np.abs(closed).max()), (i, d, fd, closed[i, d])
+
+
+def test_barycentric_transfer_closed_forms():
+    """Appendix E transfer: the identity coupling diag(a) (a = b) returns the
+    source attributes; the independent coupling a b^T returns their
+    a-weighted mean at every target point; a permutation coupling permutes."""
+    g = W.rng(61)
+    n = 9
+    a = W.random_weights(n, 62)
+    U = g.standard_normal((n, 3))
+    assert np.allclose(O.barycentric_transfer(np.diag(a), U, a), U, atol=1e-14)
+    b = W.random_weights(7, 63)
+    T = O.barycentric_transfer(np.outer(a, b), U, b)
+    assert np.allclose(T, np.tile(a @ U, (7, 1)), atol=1e-14)
+    perm = g.permutation(n)
+    P = np.zeros((n, n))
+    P[np.arange(n), perm] = a
+    assert np.allclose(O.barycentric_transfer(P, U, a[np.argsort(perm)]), U[np.argsort(perm)], atol=1e-14)
