@@ -360,7 +360,7 @@ def tc_kernel_traffic():
     if not os.path.exists(prof):
         return None, "no profile"
     txt = open(prof).read()
-    mb = re.search(r"dram_bytes_per_launch:\s*(\d+)", txt)
+    mb = re.search(r"dram_bytes_per_fused_launch:\s*(\d+)", txt)
     mh = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", txt)
     if not mb or not mh:
         return None, "profile lacks traffic or source hash"
@@ -373,22 +373,29 @@ def tc_kernel_traffic():
 
 
 def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps=10):
-    """Average duration of the row-softmin kernel on the step's shapes (CUDA
-    events on the launching stream, after warm-up) and its roofline.
-    FP32 form: the bound is the FP32 FMA pipe; algorithmic work per cell is
-    2K + 2 FLOP (K multiply-adds of the dot product, one multiply-add of the
-    rank-one term).  Peak = 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock."""
+    """Average duration of one Sinkhorn iteration as the solve runs it (CUDA
+    events on the launching stream, after warm-up, L2 flushed between
+    launches): both half-steps fused in one launch, the 16-bit operands of
+    the outer step reused, only the potential columns refreshed.  Work per
+    launch: 2 N M cells (row and column softmins).
+    Tensor-core forms: bound = MUFU ex2, one exp2 per cell; peak = 152 SMs x
+    32 ex2/clk x max SM clock.  FP32 form: bound = FP32 FMA pipe, 2K + 2 FLOP
+    per cell; peak = 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock."""
     n, m, D = X.shape[0], Y.shape[0], X.shape[1]
     V = (state["Gamma"].float() @ Y.T).T.contiguous()
-    logb = torch.log(b)
-    out = torch.empty(n, dtype=torch.float32, device=X.device)
-    ws = gw.workspace(gw.gw_workspace_size(gw.OP_SOFTMIN, n, m, D, 1, prec), X.device)
+    loga, logb = torch.log(a), torch.log(b)
+    ws = gw.workspace(gw.gw_workspace_size(gw.OP_ITERATION, n, m, D, 1, prec), X.device)
     eps = eps_at(args, args.warmup + args.steps - 1)   # the state's step
-    # as in the solve: the current f is averaged in and serves as the shift estimate
-    f_prev = state["f"]
+    f0, g0 = state["f"], state["g"]
+    f1, g1 = torch.empty_like(f0), torch.empty_like(g0)
+
+    def it(reuse):
+        gw.gw_sinkhorn_iteration(X, V, s, t, loga, logb, f0, g0, eps, prec=prec, reuse=reuse,
+                                 f_out=f1, g_out=g1, ws=ws)
+
+    it(False)                      # the outer step's operand preparation
     for _ in range(3):
-        gw.gw_sinkhorn_softmin(X, V, s, t, state["g"], logb, eps, prec=prec, avg_with=f_prev,
-                               out=out, ws=ws)
+        it(True)
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     times = []
@@ -396,30 +403,31 @@ def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps
         flush.random_(0, 255)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        gw.gw_sinkhorn_softmin(X, V, s, t, state["g"], logb, eps, prec=prec, avg_with=f_prev,
-                               out=out, ws=ws)
+        it(True)
         e1.record(st)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     dt = statistics.median(times)
+    cells = 2.0 * n * m
     peaks, src = load_peaks()
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     if prec == 0:
-        work = (2.0 * D + 2.0) * n * m
+        work = (2.0 * D + 2.0) * cells
         peak = 152 * 128 * 2 * clk
         return {"bound": "alu", "achieved": work / dt / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": work / dt / peak, "traffic": None,
-                "kernel": "softmin_fp32_kernel (row softmin, N x M cells per launch)",
+                "kernel": "softmin_fp32_kernel, one fused Sinkhorn iteration (2 N M cells per launch)",
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {clk/1e6:.0f} MHz "
                                f"(clock from {src} peaks file)",
-                "ms_per_launch": dt * 1e3, "cells_per_s": n * m / dt}
+                "ms_per_launch": dt * 1e3, "cells_per_s": cells / dt}
     ex2 = 152 * 32 * clk
     traffic, tsrc = tc_kernel_traffic() if (n, m, D) == (100_000, 100_000, 32) else (None, "other size")
-    return {"bound": "alu", "achieved": n * m / dt / 1e12, "peak": ex2 / 1e12, "unit": "Tex2/s",
-            "frac": n * m / dt / ex2, "traffic": traffic, "traffic_source": tsrc,
-            "kernel": "tcgen05 softmin (row softmin, N x M cells per launch)",
+    return {"bound": "alu", "achieved": cells / dt / 1e12, "peak": ex2 / 1e12, "unit": "Tex2/s",
+            "frac": cells / dt / ex2, "traffic": traffic, "traffic_source": tsrc,
+            "kernel": "tcgen05 softmin, one fused Sinkhorn iteration as in the solve "
+                      "(row + column half-steps, 2 N M cells per launch, operands reused)",
             "peak_source": f"derived: 152 SMs x 32 MUFU ex2/clk x {clk/1e6:.0f} MHz",
-            "ms_per_launch": dt * 1e3, "cells_per_s": n * m / dt}
+            "ms_per_launch": dt * 1e3, "cells_per_s": cells / dt}
 
 
 def run_e2e(args, gw, torch, dev, X, Y, s, t, a, b, prec, ws):

@@ -74,6 +74,7 @@ typedef struct CUstream_st* gw_stream_t;
 #define GW_OP_LIFT 4
 #define GW_OP_GRAD 5
 #define GW_OP_COARSEN 6  /* gw_workspace_size(GW_OP_COARSEN, n points, k clusters, D, 1, 0) */
+#define GW_OP_ITERATION 7 /* gw_sinkhorn_iteration(n, m, K): both half-steps */
 
 #define GW_MAX_FEATURES 128 /* largest D, E (and K) the kernels accept */
 
@@ -295,6 +296,25 @@ int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double*
               const double* Gamma_pi, float eps, int prec, const float* x, int dx_dim, int kind,
               float param, const float* basis, const float* eigvals, float* dX, float* dx,
               void* ws, size_t ws_bytes, gw_stream_t stream);
+
+/*
+ * gw_sinkhorn_iteration -- one Sinkhorn iteration on c_Gamma, both halves in
+ * one launch, as gw_solve runs it (Algorithm 3: f' = (f + S_b(g))/2,
+ * g' = (g + S_a(f))/2; Algorithm 2 with symmetric = 0: f' = S_b(g),
+ * g' = S_a(f')).  Cost c_ij = -16 <X_i, V_j> - 4 s_i t_j with V = Gamma Y
+ * (m x K); loga = log a (n), logb = log b (m); f, g in, f_out, g_out out (all
+ * device; f_out / g_out must not alias f / g).  f and g double as the shift
+ * estimates of the tensor-core forms.  reuse = 1: X, V, s, t, eps and prec
+ * are those of the previous call on the same workspace, which the caller has
+ * left untouched, so the tensor-core forms keep their 16-bit operands and
+ * refresh only the potential columns (how gw_solve runs the iterations of an
+ * outer step).  Enqueued on `stream`.  Workspace: GW_OP_ITERATION.
+ */
+int gw_sinkhorn_iteration(const float* X, const float* V, const float* s, const float* t,
+                          const float* loga, const float* logb, const float* f, const float* g,
+                          float* f_out, float* g_out, float eps, int64_t n, int64_t m, int K,
+                          int prec, int symmetric, int reuse, void* ws, size_t ws_bytes,
+                          gw_stream_t stream);
 
 /*
  * gw_coarsen -- Coarsen of Multiscale-GW (Appendix B.5): K-Means of the

@@ -20,13 +20,13 @@ __all__ = [
     "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
     "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
     "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
-    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer",
+    "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer", "gw_sinkhorn_iteration",
 ]
 
 GW_OK = 0
 PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 PEN_SQEUCLID, PEN_POWER, PEN_GAUSS = 0, 1, 2
-OP_SOFTMIN, OP_CROSS_COV, OP_ENERGY, OP_SOLVE, OP_LIFT, OP_GRAD, OP_COARSEN = 0, 1, 2, 3, 4, 5, 6
+OP_SOFTMIN, OP_CROSS_COV, OP_ENERGY, OP_SOLVE, OP_LIFT, OP_GRAD, OP_COARSEN, OP_ITERATION = range(8)
 EN_LEN = 16
 # index of each term of the float64 energy record
 EN = {"E": 0, "L": 1, "KL": 2, "C": 3, "Gamma2": 4, "T": 5, "row_l1": 6, "col_l1": 7,
@@ -91,6 +91,8 @@ lib.gw_coarsen.argtypes = [_p, _p, _i64, _int, _p, _i64, _int, _p, _p, _p, _p,
 lib.gw_multiscale.argtypes = [ctypes.POINTER(GwProblem), ctypes.POINTER(GwOptions),
                               ctypes.POINTER(GwOptions), _p, _i64, _p, _i64, _int,
                               ctypes.POINTER(GwResult), _p, _p, _sz, _p]
+lib.gw_sinkhorn_iteration.argtypes = [_p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _f, _i64, _i64, _int,
+                                      _int, _int, _int, _p, _sz, _p]
 lib.gw_transfer.argtypes = [ctypes.POINTER(GwProblem), _p, _p, _p, _f, _p, _int, _p, _p, _p, _sz,
                             _p]
 lib.gw_transfer_workspace_size.argtypes = [_i64, _i64, _int, _int]
@@ -136,7 +138,7 @@ lib.gw_version.restype = _int
 lib.gw_kernel_launches.argtypes = [_int]
 lib.gw_kernel_launches.restype = ctypes.c_ulonglong
 for _name in ("gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve", "gw_lift", "gw_grad_x",
-              "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer", "gw_transfer"):
+              "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer", "gw_sinkhorn_iteration", "gw_transfer"):
     getattr(lib, _name).restype = _int
 
 
@@ -367,6 +369,27 @@ def gw_multiscale(X, Y, s, t, a, b, eps, init_x, init_y, km_iter, coarse_outer, 
                              int(km_iter), ctypes.byref(R), _ptr(out["coarse_energy"]), _ptr(ws),
                              ws.numel(), _stream(stream)))
     return out
+
+
+def gw_sinkhorn_iteration(X, V, s, t, loga, logb, f, g, eps, prec=PREC_FP32, symmetric=True,
+                          reuse=False, f_out=None, g_out=None, ws=None, stream=None):
+    """One Sinkhorn iteration on c_Gamma, both halves in one launch (gw.h:
+    gw_sinkhorn_iteration).  reuse=True keeps the 16-bit operands already in
+    `ws` (same X, V, s, t, eps, prec as the previous call).  Returns (f', g')."""
+    n, K = X.shape
+    m = V.shape[0]
+    dev = X.device
+    f_out = torch.empty(n, dtype=torch.float32, device=dev) if f_out is None else f_out
+    g_out = torch.empty(m, dtype=torch.float32, device=dev) if g_out is None else g_out
+    if ws is None:
+        ws = workspace(gw_workspace_size(OP_ITERATION, n, m, K, 1, prec), dev)
+    _check(lib.gw_sinkhorn_iteration(_ptr(_f32(X, "X")), _ptr(_f32(V, "V")), _ptr(_f32(s, "s")),
+                                     _ptr(_f32(t, "t")), _ptr(_f32(loga, "loga")),
+                                     _ptr(_f32(logb, "logb")), _ptr(_f32(f, "f")),
+                                     _ptr(_f32(g, "g")), _ptr(f_out), _ptr(g_out), float(eps), n,
+                                     m, K, int(prec), int(bool(symmetric)), int(bool(reuse)),
+                                     _ptr(ws), ws.numel(), _stream(stream)))
+    return f_out, g_out
 
 
 def gw_transfer(X, Y, s, t, a, b, f, g, Gamma_t, eps, U, ws=None, stream=None):

@@ -78,12 +78,72 @@ size_t solve_fixed_bytes(int64_t n, int64_t m, int D, int E) {
   return c.used();
 }
 
+size_t iteration_ws_bytes(int64_t n, int64_t m, int K, int prec);
+
 size_t solve_ws_bytes(int64_t n, int64_t m, int D, int E, int prec) {
-  const size_t inner = softmin_ws_bytes(n, m, D, prec) + softmin_ws_bytes(m, n, D, prec) + 512;
+  const size_t inner = iteration_ws_bytes(n, m, D, prec);
   size_t step = energy_ws_bytes(n, m, D, E, prec);
   const size_t mom = moments_ws_bytes(n, m, D, E);
   if (mom > step) step = mom;
   return solve_fixed_bytes(n, m, D, E) + (inner > step ? inner : step) + 256;
+}
+
+size_t iteration_ws_bytes(int64_t n, int64_t m, int K, int prec) {
+  return softmin_ws_bytes(n, m, K, prec) + softmin_ws_bytes(m, n, K, prec) + 512;
+}
+
+// One iteration (both half-steps), shared by gw_solve and gw_sinkhorn_iteration.
+int launch_iteration(const float* X, const float* V, const float* s, const float* t,
+                     const float* loga, const float* logb, const float* f, const float* g,
+                     float* f_out, float* g_out, float eps, int64_t n, int64_t m, int K, int prec,
+                     bool symmetric, bool reuse, char* ws, size_t ws_bytes, cudaStream_t st) {
+  Carver sub(ws, ws_bytes);
+  SoftminTask row{}, col{};
+  row.A = X;
+  row.B = V;
+  row.sA = s;
+  row.sB = t;
+  row.h = g;
+  row.logw = logb;
+  row.est = f;      // the row log-sum-exp is close to -f / eps
+  row.n = n;
+  row.m = m;
+  row.K = K;
+  row.eps = eps;
+  col.A = V;
+  col.B = X;
+  col.sA = t;
+  col.sB = s;
+  col.logw = loga;
+  col.est = g;
+  col.n = m;
+  col.m = n;
+  col.K = K;
+  col.eps = eps;
+  // within an outer step only the potentials change: the tensor-core form
+  // keeps its 16-bit operands and refreshes the bias columns
+  row.reuse_ops = col.reuse_ops = reuse ? 1 : 0;
+  if (symmetric) {
+    // Algorithm 3: both halves read iterate n, then average.
+    row.avg_with = f;
+    row.out = f_out;
+    col.h = f;
+    col.avg_with = g;
+    col.out = g_out;
+    SoftminTask both[2] = {row, col};
+    return launch_softmin(both, 2, prec, sub, st);
+  }
+  // Algorithm 2: f from g^n, then g from f^{n+1}.
+  row.avg_with = nullptr;
+  row.out = f_out;
+  GW_TRY(launch_softmin(&row, 1, prec, sub, st));
+  // the column task keeps its own operands beside the row task's
+  const size_t off = (softmin_ws_bytes(n, m, K, prec) + 255) & ~size_t(255);
+  Carver sub2(ws + off, ws_bytes - off);
+  col.h = f_out;
+  col.avg_with = nullptr;
+  col.out = g_out;
+  return launch_softmin(&col, 1, prec, sub2, st);
 }
 
 struct SolveBufs {
@@ -159,59 +219,11 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
     int n_run = n_cur;
     bool checked = false;
     for (int it = 0; it < n_cur; ++it) {
-      Carver sub(base + mark, ws_bytes - mark);
-      SoftminTask row{}, col{};
-      row.A = p.X;
-      row.B = B.V;
-      row.sA = p.s;
-      row.sB = p.t;
-      row.h = B.g[gc];
-      row.logw = B.logb;
-      row.est = B.f[fc];      // the row log-sum-exp is close to -f / eps
-
-      row.n = p.n;
-      row.m = p.m;
-      row.K = p.D;
-      row.eps = eps;
-      col.A = B.V;
-      col.B = p.X;
-      col.sA = p.t;
-      col.sB = p.s;
-      col.logw = B.loga;
-      col.est = B.g[gc];
-      col.n = p.m;
-      col.m = p.n;
-      col.K = p.D;
-      col.eps = eps;
-      // within an outer step only the potentials change: the tensor-core
-      // form keeps its 16-bit operands and refreshes the bias columns
-      row.reuse_ops = col.reuse_ops = it > 0 ? 1 : 0;
-      if (o.symmetric) {
-        // Algorithm 3: both halves read iterate n, then average.
-        row.avg_with = B.f[fc];
-        row.out = B.f[fc ^ 1];
-        col.h = B.f[fc];
-        col.avg_with = B.g[gc];
-        col.out = B.g[gc ^ 1];
-        SoftminTask both[2] = {row, col};
-        GW_TRY(launch_softmin(both, 2, o.prec, sub, st));
-        fc ^= 1;
-        gc ^= 1;
-      } else {
-        // Algorithm 2: f from g^n, then g from f^{n+1}.
-        row.avg_with = nullptr;
-        row.out = B.f[fc ^ 1];
-        GW_TRY(launch_softmin(&row, 1, o.prec, sub, st));
-        fc ^= 1;
-        // the column task keeps its own operands beside the row task's
-        const size_t off = (softmin_ws_bytes(p.n, p.m, p.D, o.prec) + 255) & ~size_t(255);
-        Carver sub2(base + mark + off, ws_bytes - mark - off);
-        col.h = B.f[fc];
-        col.avg_with = nullptr;
-        col.out = B.g[gc ^ 1];
-        GW_TRY(launch_softmin(&col, 1, o.prec, sub2, st));
-        gc ^= 1;
-      }
+      GW_TRY(launch_iteration(p.X, B.V, p.s, p.t, B.loga, B.logb, B.f[fc], B.g[gc], B.f[fc ^ 1],
+                              B.g[gc ^ 1], eps, p.n, p.m, p.D, o.prec, o.symmetric != 0, it > 0,
+                              base + mark, ws_bytes - mark, st));
+      fc ^= 1;
+      gc ^= 1;
       if (stop_rule && (it + 1) % o.stop_every == 0) {
         // hybrid stop: Err of the plan this iteration measured
         GW_TRY(run_marginal_error(B.f[fc ^ 1], B.f[fc], p.a, p.n, B.g[gc ^ 1], B.g[gc], p.b, p.m,
@@ -300,6 +312,7 @@ size_t gw_workspace_size(int op, int64_t n, int64_t m, int D, int E, int prec) {
     case GW_OP_LIFT: return lift_ws_bytes(n, D) + 256;   /* (n points, D features) */
     case GW_OP_GRAD: return grad_ws_bytes(n, m, D, E, 4, prec) + 256;
     case GW_OP_COARSEN: return n >= 1 ? coarsen_ws_bytes(n, m, D) + 256 : 0;   /* (n points, m = k) */
+    case GW_OP_ITERATION: return iteration_ws_bytes(n, m, D, prec);
     default: return 0;
   }
 }
@@ -511,6 +524,35 @@ int gw_grad_x(const gw_problem* p, const float* f, const float* g, const double*
              "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
   return run_grad(*p, f, g, Gamma_t, Gamma_pi, eps, prec, x, dx_dim, kind, param, basis, eigvals,
                   dX, dx, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int gw_sinkhorn_iteration(const float* X, const float* V, const float* s, const float* t,
+                          const float* loga, const float* logb, const float* f, const float* g,
+                          float* f_out, float* g_out, float eps, int64_t n, int64_t m, int K,
+                          int prec, int symmetric, int reuse, void* ws, size_t ws_bytes,
+                          gw_stream_t stream) {
+  gw::set_error("");
+  GW_TRY(check_eps(eps));
+  GW_TRY(check_dims(n, m, K, 1));
+  GW_TRY(check_prec(prec));
+  GW_REQUIRE(n >= 1, GW_EINVAL, "n must be >= 1");
+  NONNULL(X);
+  NONNULL(V);
+  NONNULL(s);
+  NONNULL(t);
+  NONNULL(loga);
+  NONNULL(logb);
+  NONNULL(f);
+  NONNULL(g);
+  NONNULL(f_out);
+  NONNULL(g_out);
+  GW_REQUIRE(f_out != f && g_out != g, GW_EINVAL, "f_out / g_out must not alias f / g");
+  const size_t need = iteration_ws_bytes(n, m, K, prec);
+  GW_REQUIRE(ws != nullptr && ws_bytes >= need && reinterpret_cast<uintptr_t>(ws) % 256 == 0,
+             GW_ENOMEM, "workspace too small or unaligned: need %zu bytes, have %zu", need, ws_bytes);
+  return launch_iteration(X, V, s, t, loga, logb, f, g, f_out, g_out, eps, n, m, K, prec,
+                          symmetric != 0, reuse != 0, static_cast<char*>(ws), ws_bytes,
+                          reinterpret_cast<cudaStream_t>(stream));
 }
 
 int gw_coarsen(const float* X, const float* a, int64_t n, int D, const int64_t* init_idx,

@@ -173,3 +173,45 @@ def test_tensor_core_shift_estimate_paths(gw, prec, quality):
     tol = 0.5 * softmin_tolerance_prec(A, B, sA, sB, h, logw, eps, prec) + 1e-7 * np.abs(want)
     err = np.abs(host(out) - want)
     assert np.all(err <= tol), (quality, err.max())
+
+
+@pytest.mark.parametrize("prec", [0, 3])
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_sinkhorn_iteration_matches_oracle_and_reuse(gw, prec, symmetric):
+    """gw_sinkhorn_iteration: one iteration of Algorithm 3 (or 2) against the
+    oracle's, each half within its softmin tolerance (for Algorithm 2 the
+    column half reads the device's own f'); with reuse = 1 after a call on
+    other potentials, the result equals a fresh preparation."""
+    from helpers import softmin_tolerance_prec
+    n, m, K = 1500, 1300, 16
+    A, B, sA, sB, _, _ = make_inputs(n, m, K, seed=5)
+    g0 = W.rng(6)
+    la = np.log(np.asarray(W.random_weights(n, 7), np.float32)).astype(np.float64)
+    lb = np.log(np.asarray(W.random_weights(m, 8), np.float32)).astype(np.float64)
+    f = np.asarray(0.2 * g0.standard_normal(n), np.float32).astype(np.float64)
+    g = np.asarray(0.2 * g0.standard_normal(m), np.float32).astype(np.float64)
+    eps = 0.05
+    fo, go = gw.gw_sinkhorn_iteration(f32(A), f32(B), f32(sA), f32(sB), f32(la), f32(lb), f32(f),
+                                      f32(g), eps, prec=prec, symmetric=symmetric)
+    C = -16.0 * A @ B.T - 4.0 * np.outer(sA, sB)
+    Sf = O.softmin(eps, lb, g, C)
+    tol_f = softmin_tolerance_prec(A, B, sA, sB, g, lb, eps, prec)
+    if symmetric:
+        Sg = O.softmin(eps, la, f, C.T)
+        want_f, want_g = 0.5 * (f + Sf), 0.5 * (g + Sg)
+        tol_f = 0.5 * tol_f
+        tol_g = 0.5 * softmin_tolerance_prec(B, A, sB, sA, f, la, eps, prec)
+    else:
+        fd = host(fo)
+        want_f, want_g = Sf, O.softmin(eps, la, fd, C.T)
+        tol_g = softmin_tolerance_prec(B, A, sB, sA, fd, la, eps, prec)
+    assert np.all(np.abs(host(fo) - want_f) <= tol_f)
+    assert np.all(np.abs(host(go) - want_g) <= tol_g)
+    # reuse: prepare on other potentials, then iterate on (f, g) with reuse = 1
+    ws = gw.workspace(gw.gw_workspace_size(gw.OP_ITERATION, n, m, K, 1, prec), "cuda")
+    gw.gw_sinkhorn_iteration(f32(A), f32(B), f32(sA), f32(sB), f32(la), f32(lb), f32(0.5 * f),
+                             f32(-g), eps, prec=prec, symmetric=symmetric, ws=ws)
+    fr, gr = gw.gw_sinkhorn_iteration(f32(A), f32(B), f32(sA), f32(sB), f32(la), f32(lb), f32(f),
+                                      f32(g), eps, prec=prec, symmetric=symmetric, reuse=True,
+                                      ws=ws)
+    assert bool((fr == fo).all()) and bool((gr == go).all())
