@@ -365,7 +365,7 @@ def tc_kernel_traffic():
     if not mb or not mh:
         return None, "profile lacks traffic or source hash"
     h = hashlib.sha1()
-    for f in ("gw_softmin_tc.cu", "gw_tc.cuh"):
+    for f in ("gw_softmin_tc.cu", "gw_tc.cuh", "gw_tc_ops.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2602_06658_gb300", "csrc", f), "rb").read())
     if h.hexdigest() != mh.group(1):
         return None, "kernel changed since the ncu capture"

@@ -215,6 +215,14 @@ int run_marginal_error(const float* f0, const float* f1, const float* a, int64_t
 // rec[GW_EN_NINNER], rec[GW_EN_STOPERR] (err may be null: -1)
 int launch_record_extra(double* rec, int n_inner, const double* err, cudaStream_t st);
 
+// Plan-weighted column sums on the tensor cores (gw_plan_tc.cu): Wp partials
+// [splits][m][D + 2] of W_j = sum_i pi_ij [X_i, s_i, 1]; *flag_out is set on
+// the device when the FP32 kernel has to recompute them.
+bool plan_tc_supported(int D, int prec);
+size_t plan_tc_ws_bytes(int64_t n, int64_t m, int D, int prec);
+int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int* splits_out,
+                int* rows_per_split_out, int** flag_out, Carver& ws, cudaStream_t st);
+
 // Color / UV transfer (gw_transfer.cu)
 size_t transfer_ws_bytes(int64_t n, int64_t m, int D, int k);
 int run_transfer(const gw_problem& p, const float* f, const float* g, const double* Gamma_t,

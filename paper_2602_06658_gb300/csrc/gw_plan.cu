@@ -56,6 +56,7 @@ struct ColSumArgs {
   int D;
   int rows_per_split;
   float* Wp;       // [splits][m][D+2]
+  const int* cond; // run only when *cond != 0 (null: always)
 };
 
 // W_j = sum_i pi_ij [X_i, s_i, 1] over one row split, one column per thread.
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
   __shared__ float rb[kBR];
   __shared__ float us[kBR];
   __shared__ float ss[kBR];
+  if (P.cond != nullptr && *P.cond == 0) return;   // the tensor-core pass succeeded
 
   const int tid = threadIdx.x;
   const int64_t j = static_cast<int64_t>(blockIdx.x) * kThreads + tid;
@@ -573,10 +575,20 @@ int launch_gamma_y(const double* Gamma, const float* Y, int64_t m, int D, int E,
 }
 
 size_t cross_cov_ws_bytes(int64_t n, int64_t m, int D, int E, int prec) {
-  (void)prec;
   Carver c(nullptr, ~size_t(0));
   carve_cross_cov(c, n, m, D, E, true);
-  return c.used();
+  return c.used() + (plan_tc_supported(D, prec) ? plan_tc_ws_bytes(n, m, D, prec) : 0);
+}
+
+static void launch_colsum(const ColSumArgs& A, dim3 grid, cudaStream_t st) {
+  switch (dpad(A.D)) {
+    case 4: plan_colsum_kernel<4><<<grid, kThreads, 0, st>>>(A); break;
+    case 8: plan_colsum_kernel<8><<<grid, kThreads, 0, st>>>(A); break;
+    case 16: plan_colsum_kernel<16><<<grid, kThreads, 0, st>>>(A); break;
+    case 32: plan_colsum_kernel<32><<<grid, kThreads, 0, st>>>(A); break;
+    case 64: plan_colsum_kernel<64><<<grid, kThreads, 0, st>>>(A); break;
+    default: plan_colsum_kernel<128><<<grid, kThreads, 0, st>>>(A); break;
+  }
 }
 
 // Enqueue everything up to the Gamma partials; the caller finalizes.
@@ -600,21 +612,30 @@ static int cross_cov_stage(const PlanArgs& p, int prec, double* W_user, Carver& 
   A.n = p.n;
   A.m = p.m;
   A.D = p.D;
-  A.rows_per_split = L.rows_per_split;
-  A.Wp = L.Wp;
-  dim3 grid(ceil_div(p.m, kThreads), L.splits);
-  switch (dpad(p.D)) {
-    case 4: plan_colsum_kernel<4><<<grid, kThreads, 0, st>>>(A); break;
-    case 8: plan_colsum_kernel<8><<<grid, kThreads, 0, st>>>(A); break;
-    case 16: plan_colsum_kernel<16><<<grid, kThreads, 0, st>>>(A); break;
-    case 32: plan_colsum_kernel<32><<<grid, kThreads, 0, st>>>(A); break;
-    case 64: plan_colsum_kernel<64><<<grid, kThreads, 0, st>>>(A); break;
-    default: plan_colsum_kernel<128><<<grid, kThreads, 0, st>>>(A); break;
-  }
-  GW_LAUNCH_CHECK();
+  A.cond = nullptr;
   const int64_t count = p.m * (p.D + 2);
-  reduce_splits_kernel<<<ceil_div(count, 256), 256, 0, st>>>(L.Wp, L.splits, count, L.W);
-  GW_LAUNCH_CHECK();
+  if (plan_tc_supported(p.D, prec)) {
+    // both contractions on the tensor cores; the FP32 kernel recomputes the
+    // same partials only when that pass flagged a value it could not hold
+    float* Wp = nullptr;
+    int splits = 0, rps = 0;
+    int* flag = nullptr;
+    GW_TRY(run_plan_tc(p, prec, L.V, &Wp, &splits, &rps, &flag, ws, st));
+    A.rows_per_split = rps;
+    A.Wp = Wp;
+    A.cond = flag;
+    launch_colsum(A, dim3(ceil_div(p.m, kThreads), splits), st);
+    GW_LAUNCH_CHECK();
+    reduce_splits_kernel<<<ceil_div(count, 256), 256, 0, st>>>(Wp, splits, count, L.W);
+    GW_LAUNCH_CHECK();
+  } else {
+    A.rows_per_split = L.rows_per_split;
+    A.Wp = L.Wp;
+    launch_colsum(A, dim3(ceil_div(p.m, kThreads), L.splits), st);
+    GW_LAUNCH_CHECK();
+    reduce_splits_kernel<<<ceil_div(count, 256), 256, 0, st>>>(L.Wp, L.splits, count, L.W);
+    GW_LAUNCH_CHECK();
+  }
   const size_t shbytes = sizeof(double) * 32 * (p.D + 2 + p.E);
   gamma_partial_kernel<<<kRedBlocks, 256, shbytes, st>>>(L.W, p.Y, p.t, p.b, p.g, p.m, p.D, p.E,
                                                          L.Gp);
@@ -736,7 +757,8 @@ size_t energy_ws_bytes(int64_t n, int64_t m, int D, int E, int prec) {
   c.take<float>(static_cast<size_t>(n));        // fhat
   c.take<float>(static_cast<size_t>(m));        // log b
   c.take<double>(static_cast<size_t>(kRedBlocks) * 4);
-  return c.used() + softmin_ws_bytes(n, m, D, prec) + 256;
+  return c.used() + softmin_ws_bytes(n, m, D, prec) + 256 +
+         (plan_tc_supported(D, prec) ? plan_tc_ws_bytes(n, m, D, prec) : 0);
 }
 
 int run_marginal_error(const float* f0, const float* f1, const float* a, int64_t n,

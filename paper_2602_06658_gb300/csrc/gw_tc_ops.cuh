@@ -1,0 +1,281 @@
+// Operand preparation shared by the tensor-core kernels (the softmin and the
+// plan-weighted reduction): the 16-bit operand matrices whose product is the
+// whole base-2 exponent of the plan on c_Gamma (layout and splits described in
+// gw_softmin_tc.cu), their scales, the per-iteration refresh of the potential
+// columns, tensor-map encoding and a bounded mbarrier drain.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "gw_internal.cuh"
+#include "gw_tc.cuh"
+
+namespace gw {
+
+namespace {
+
+constexpr float kBiasConst = 32768.0f;       // A-side multiplier of the bias columns
+constexpr float kHalfMax = 65504.0f;
+constexpr float kShiftBias = 30.0f;          // fast-pass shift sits this far below the estimate
+
+struct TcOperandShape {
+  int K;        // feature dimension
+  int mult;     // 1 or 3 products in the dot
+  int KP;       // padded operand width
+  int col_u;    // first rank-one column
+  int col_w;    // first column-bias column
+  int col_e;    // first row-estimate column
+  int col_k;    // mask column (-inf for padded and zero-weight target columns)
+  int used;     // non-zero columns
+};
+
+TcOperandShape tc_shape(int K, int prec) {
+  TcOperandShape s;
+  s.K = K;
+  s.mult = prec == GW_PREC_BF16 ? 1 : 3;
+  s.col_u = s.mult * K;
+  s.col_w = s.col_u + 3;
+  s.col_e = s.col_w + 3;
+  s.col_k = s.col_e + 3;
+  s.used = s.col_k + 1;
+  s.KP = ((s.used + 63) / 64) * 64;
+  return s;
+}
+
+bool tc_is_bf16(int prec) { return prec != GW_PREC_F16X3; }
+
+int max_splits(int col_tiles) { return col_tiles < 64 ? col_tiles : 64; }
+
+template <class T>
+__device__ __forceinline__ T to16(float x);
+template <>
+__device__ __forceinline__ __half to16<__half>(float x) {
+  return __float2half_rn(x);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+__device__ __forceinline__ float from16(__half x) { return __half2float(x); }
+__device__ __forceinline__ float from16(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Part `part` (0, 1, 2) of a three-way 16-bit split of x (hi + mid + lo).
+template <class T>
+__device__ __forceinline__ float split3(float x, int part) {
+  const float x0 = from16(to16<T>(x));
+  const float r1 = x - x0;
+  const float x1 = from16(to16<T>(r1));
+  return part == 0 ? x0 : (part == 1 ? x1 : r1 - x1);
+}
+
+// Largest magnitudes that set the operand scales -> mx[0..5] (non-negative
+// floats compare as unsigned ints): |A|, |B|, |sA|, |sB|, the finite column
+// biases |w_j| and the row shifts |e_i| (when an estimate is given).
+__global__ void tc_absmax_kernel(const float* A, int64_t nA, const float* B, int64_t nB,
+                                 const float* sA, int64_t n, const float* sB, int64_t m,
+                                 const float* h, const float* logw, const float* est,
+                                 float inv_eps, unsigned* mx) {
+  float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < nA; i += stride) v[0] = fmaxf(v[0], fabsf(A[i]));
+  for (int64_t i = t0; i < nB; i += stride) v[1] = fmaxf(v[1], fabsf(B[i]));
+  for (int64_t i = t0; i < n; i += stride) v[2] = fmaxf(v[2], fabsf(sA[i]));
+  for (int64_t i = t0; i < m; i += stride) {
+    v[3] = fmaxf(v[3], fabsf(sB[i]));
+    const float w = (h[i] * inv_eps + logw[i]) * kLog2e;
+    if (isfinite(w)) v[4] = fmaxf(v[4], fabsf(w));
+  }
+  if (est)
+    for (int64_t i = t0; i < n; i += stride)
+      v[5] = fmaxf(v[5], fabsf(est[i] * inv_eps * kLog2e + kShiftBias));
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = fmaxf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&mx[k], __float_as_uint(v[k]));
+  }
+}
+
+// Power-of-two scale that brings max |x| / c to at most 2^14 (so a three-way
+// 16-bit split keeps all three parts normal), within [2^-14, 2^15].
+__device__ __forceinline__ float pow2_scale(float mxv) {
+  float c = 6.103515625e-05f;   // 2^-14
+  while (c < 32768.0f && mxv > 16384.0f * c) c *= 2.0f;
+  return c;
+}
+
+// Scale pair (sa, sb) with sa * sb = prod that balances max|x sa| and max|y sb|.
+__device__ __forceinline__ void balance(float prod, float mxa, float mxb, float* sa, float* sb) {
+  if (!(mxa > 0.f) || !(mxb > 0.f)) {
+    *sa = 1.0f;
+    *sb = prod;
+    return;
+  }
+  const float r = sqrtf(prod * mxb / mxa);
+  *sa = r;
+  *sb = prod / r;
+}
+
+// Operand rows.  role 0 = A side (row operand), role 1 = B side (column
+// operand, bias columns included).  Rows >= rows_valid are padding: zeros,
+// and for the B side a bias of -65504 * kBiasConst so they add nothing.
+template <class T>
+__global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, const float* logw,
+                               const float* est, int64_t rows_valid, int64_t rows_pad,
+                               TcOperandShape shp, int role, float alpha, float beta,
+                               float inv_eps, const unsigned* mx, T* op) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
+  if (r >= rows_pad) return;
+  const float mA = __uint_as_float(mx[0]), mB = __uint_as_float(mx[1]);
+  const float msA = __uint_as_float(mx[2]), msB = __uint_as_float(mx[3]);
+  const float cw = pow2_scale(__uint_as_float(mx[4]));
+  const float ce = pow2_scale(__uint_as_float(mx[5]));
+  float sa, sb, ua, ub;
+  balance(alpha, mA, mB, &sa, &sb);
+  balance(beta, msA, msB, &ua, &ub);
+  const float sc = role == 0 ? sa : sb;
+  const float us = role == 0 ? ua : ub;
+  T* row = op + r * shp.KP;
+  const bool valid = r < rows_valid;
+  const int K = shp.K;
+  for (int k = threadIdx.x; k < shp.KP; k += blockDim.x) {
+    float v = 0.0f;
+    if (valid) {
+      if (k < shp.col_u) {
+        const int part = k / K, kk = k % K;
+        const float x = X[r * K + kk] * sc;
+        const float hi = from16(to16<T>(x));
+        // A side [hi, hi, lo], B side [hi, lo, hi]: hi*hi + hi*lo + lo*hi
+        const bool lo = shp.mult == 3 && ((role == 0 && part == 2) || (role == 1 && part == 1));
+        v = lo ? x - hi : hi;
+      } else if (k < shp.col_w) {
+        const int part = k - shp.col_u;
+        const float x = sq[r] * us;
+        const float hi = from16(to16<T>(x));
+        if (role == 0) v = part < 2 ? hi : x - hi;   // [hi, hi, lo]
+        else v = part == 1 ? x - hi : hi;            // [hi, lo, hi]
+      } else if (k < shp.col_e) {
+        // column bias w_j = (h_j/eps + logw_j) log2(e) as c_w * split(w_j / c_w)
+        if (role == 0) {
+          v = cw;
+        } else {
+          const float w = (h[r] * inv_eps + logw[r]) * kLog2e;
+          v = isfinite(w) ? split3<T>(w / cw, k - shp.col_w) : 0.0f;
+        }
+      } else if (k < shp.col_k) {
+        // row shift e_i = -est_i log2(e) / eps - kShiftBias as -c_e * split(-e_i / c_e)
+        if (role == 1) {
+          v = ce;
+        } else if (est) {
+          v = split3<T>((est[r] * inv_eps * kLog2e + kShiftBias) / ce, k - shp.col_e);
+        }
+      } else if (k == shp.col_k) {
+        // mask: zero-weight target columns never contribute
+        if (role == 0) v = kBiasConst;
+        else v = isfinite(logw[r]) ? 0.0f : -kHalfMax;
+      }
+    } else if (role == 1 && k == shp.col_k) {
+      v = -kHalfMax;   // padding columns never contribute
+    }
+    row[k] = to16<T>(v);
+  }
+}
+
+// Per-iteration refresh: largest |w_j| (finite) and |e_i| -> mx[4], mx[5]
+__global__ void tc_bias_absmax_kernel(const float* h, const float* logw, int64_t m,
+                                      const float* est, int64_t n, float inv_eps, unsigned* mx) {
+  float vw = 0.f, ve = 0.f;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < m; i += stride) {
+    const float w = (h[i] * inv_eps + logw[i]) * kLog2e;
+    if (isfinite(w)) vw = fmaxf(vw, fabsf(w));
+  }
+  if (est)
+    for (int64_t i = t0; i < n; i += stride)
+      ve = fmaxf(ve, fabsf(est[i] * inv_eps * kLog2e + kShiftBias));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vw = fmaxf(vw, __shfl_xor_sync(0xffffffffu, vw, o));
+    ve = fmaxf(ve, __shfl_xor_sync(0xffffffffu, ve, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&mx[4], __float_as_uint(vw));
+    atomicMax(&mx[5], __float_as_uint(ve));
+  }
+}
+
+// Rewrite only the columns that change between Sinkhorn iterations: for the
+// A side the bias constants c_w and the split shift; for the B side the split
+// bias and the shift constants c_e.
+template <class T>
+__global__ void tc_refresh_kernel(const float* h, const float* logw, const float* est,
+                                  int64_t rows_valid, TcOperandShape shp, int role, float inv_eps,
+                                  const unsigned* mx, T* op) {
+  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows_valid) return;
+  const float cw = pow2_scale(__uint_as_float(mx[4]));
+  const float ce = pow2_scale(__uint_as_float(mx[5]));
+  T* row = op + r * shp.KP;
+  if (role == 0) {
+    const float e = est ? (est[r] * inv_eps * kLog2e + kShiftBias) / ce : 0.0f;
+    for (int k = 0; k < 3; ++k) {
+      row[shp.col_w + k] = to16<T>(cw);
+      row[shp.col_e + k] = to16<T>(est ? split3<T>(e, k) : 0.0f);
+    }
+  } else {
+    const float w = (h[r] * inv_eps + logw[r]) * kLog2e;
+    const bool fin = isfinite(w);
+    for (int k = 0; k < 3; ++k) {
+      row[shp.col_w + k] = to16<T>(fin ? split3<T>(w / cw, k) : 0.0f);
+      row[shp.col_e + k] = to16<T>(ce);
+    }
+  }
+}
+
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = tc::globaltimer();
+  while (!tc::mbar_try_wait(bar, parity)) {
+    if (tc::globaltimer() - t0 > tc::kWaitLimitNs) return false;
+  }
+  return true;
+}
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+int make_map(CUtensorMap* map, void* ptr, int64_t rows, int KP, bool bf16, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  GW_REQUIRE(enc != nullptr, GW_ECUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(KP), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(KP) * 2};
+  cuuint32_t box[2] = {64, static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  GW_REQUIRE(r == CUDA_SUCCESS, GW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return GW_OK;
+}
+
+}  // namespace
+
+}  // namespace gw

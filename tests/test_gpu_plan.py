@@ -112,3 +112,57 @@ def test_cross_cov_is_deterministic(gw):
     G1, s1, _ = gw.gw_cross_cov(*args)
     G2, s2, _ = gw.gw_cross_cov(*args)
     assert bool((G1 == G2).all()) and bool((s1 == s2).all())
+
+
+def tc_plan_tolerance(P, pi, D, prec):
+    """plan_tolerance for the tensor-core path: every product term of the
+    exponent carries TERM_REL[prec] relative error instead of 2^-24, and the
+    plan and the features each enter the second product as two f16 parts
+    (about 2^-21 relative)."""
+    from helpers import TERM_REL
+    X, Y, s, t, f, g = (P[k] for k in ("X", "Y", "s", "t", "f", "g"))
+    V = Y @ P["Gamma_t"].T
+    S = (16 * np.abs(X) @ np.abs(V).T + 4 * np.outer(s, t) + np.abs(f)[:, None] + np.abs(g)[None, :]
+         + P["eps"] * (np.abs(np.log(P["a"]))[:, None] + np.abs(np.log(P["b"]))[None, :])).max()
+    return 2.0 * ((D + 4) * TERM_REL[prec] * S / P["eps"] + np.sqrt(X.shape[0]) * 2.0 ** -23
+                  + 2.0 ** -20)
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("n,m,D,E,eps", [(300, 257, 2, 2, 0.2), (1000, 1000, 3, 3, 0.05),
+                                         (777, 1500, 16, 16, 0.1), (513, 600, 32, 32, 0.05),
+                                         (2000, 129, 5, 7, 0.1), (4100, 3000, 32, 32, 0.05)])
+def test_cross_cov_tensor_cores_match_oracle(gw, prec, n, m, D, E, eps):
+    """The tensor-core plan sums (both contractions on tcgen05) against the
+    dense FP64 plan: Gamma_{t+1}, W and the column statistics."""
+    P = plan_inputs(n, m, D, E, eps, seed=n + m + D)
+    G, stats, Wd = gw.gw_cross_cov(*dev_args(P), prec=prec, want_W=True)
+    pi = dense_plan(P)
+    rel = tc_plan_tolerance(P, pi, D, prec)
+    X, Y = P["X"], P["Y"]
+    bound = rel * (np.abs(X).T @ pi @ np.abs(Y)) + 1e-12
+    assert np.all(np.abs(host(G) - X.T @ pi @ Y) <= bound), np.max(np.abs(host(G) - X.T @ pi @ Y) / bound)
+    W_ref = np.concatenate([pi.T @ X, (pi.T @ P["s"])[:, None], pi.sum(0)[:, None]], axis=1)
+    Wb = rel * np.concatenate([pi.T @ np.abs(X), (pi.T @ P["s"])[:, None], pi.sum(0)[:, None]], axis=1)
+    err = np.abs(host(Wd) - W_ref)
+    assert np.all(err <= Wb + 1e-15), np.max(err / (Wb + 1e-15))
+    st = host(stats)
+    assert abs(st[0] - P["s"] @ pi @ P["t"]) <= rel * (P["s"] @ pi @ P["t"])
+    assert abs(st[2] - pi.sum()) <= rel * pi.sum()
+
+
+def test_cross_cov_tensor_core_overflow_falls_back_to_fp32(gw):
+    """A target potential far above its Sinkhorn value (g + 20 eps) scales
+    pi_ij / b_j by e^20, beyond what f16 holds: the tensor-core pass flags it
+    and the FP32 kernel recomputes the partials, so the result still meets
+    the FP32 bound of the plan the inputs define."""
+    P = plan_inputs(600, 500, 8, 8, 0.1, seed=17)
+    P["g"] = r32(P["g"] + 20 * P["eps"])
+    G, stats, Wd = gw.gw_cross_cov(*dev_args(P), prec=3, want_W=True)
+    pi = dense_plan(P)
+    rel = plan_tolerance(P, pi, 8)
+    W_ref = np.concatenate([pi.T @ P["X"], (pi.T @ P["s"])[:, None], pi.sum(0)[:, None]], axis=1)
+    Wb = rel * np.concatenate([pi.T @ np.abs(P["X"]), (pi.T @ P["s"])[:, None], pi.sum(0)[:, None]],
+                              axis=1)
+    assert np.all(np.abs(host(Wd) - W_ref) <= Wb + 1e-12)
+    assert np.isfinite(host(G)).all()
