@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--rate-frac", type=float, default=0.8,
                     help="serving arrival rate as a fraction of the measured saturated throughput")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--accuracy", action="store_true",
+                    help="run the whole eps schedule in FP32 and in --prec and print the per-step "
+                         "energy records side by side (no timing)")
     return ap.parse_args()
 
 
@@ -279,6 +282,8 @@ def run_gw(args, rank, world, local):
         torch.distributed.barrier()
     clk = clocks.stop()
     en = out_energy(outs[(tidx - 1) % 2])
+    acc = energy_check(gw, torch, X, Y, s, t, a, b, outs[(tidx - 1) % 2],
+                       eps_at(args, tidx - 1), prec) if prec != 0 else None
     local_t = sum(step_ms) / 1e3
     cells = float(n) * m * args.n_inner * args.steps
     t_max, units = aggregate(local_t, cells, world, dev)
@@ -314,6 +319,7 @@ def run_gw(args, rank, world, local):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "solves_per_s": (units / t_max) / (float(n) * m * args.n_inner * args.n_outer),
             "energy_last_step": en,
+            "energy_check": acc,
             "gpu_launches": launches,
             "clocks": clk,
             "roofline": rf,
@@ -327,6 +333,55 @@ def run_gw(args, rank, world, local):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def energy_check(gw, torch, X, Y, s, t, a, b, o, eps, prec):
+    """Error statement of the reduced-precision step: the energy record and
+    Gamma_{t+1} of the last step's final state evaluated with FP32 kernels and
+    with the step's precision (the same f, g, Gamma_t)."""
+    ev = {}
+    for p in (0, prec):
+        en, G = gw.gw_energy(X, Y, s, t, a, b, o["f"], o["g"], o["Gamma_plan"], eps, prec=p)
+        ev[p] = (en.cpu().numpy(), G.cpu().numpy())
+    e0, g0 = ev[0]
+    e1, g1 = ev[prec]
+    import numpy as np
+    return {"E_fp32": float(e0[0]), "E": float(e1[0]),
+            "E_rel_err": float(abs(e1[0] - e0[0]) / abs(e0[0])),
+            "L_rel_err": float(abs(e1[1] - e0[1]) / abs(e0[1])),
+            "Gamma_rel_err": float(np.linalg.norm(g1 - g0) / np.linalg.norm(g0)),
+            "col_l1_fp32": float(e0[7]), "col_l1": float(e1[7]), "eps": float(eps),
+            "note": "same state evaluated in FP32 and in the step's precision"}
+
+
+def run_accuracy(args, local):
+    """The whole eps schedule (n_outer x n_inner, annealed) solved in FP32 and
+    in --prec from Gamma_0 = 0; one JSON line with the per-step energy records
+    of both and their relative differences."""
+    import numpy as np
+    import torch
+    import paper_2602_06658_gb300 as gw
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = PREC[args.prec]
+    X, Y, s, t, a, b = make_features(args, gw, torch, dev, args.seed)
+    hist, secs = {}, {}
+    for p in (0, prec):
+        t0 = time.time()
+        o = gw.gw_solve(X, Y, s, t, a, b, args.eps0, args.n_outer, args.n_inner,
+                        eps_final=args.eps1, prec=p, record=True)
+        hist[p] = o["history"].cpu().numpy()
+        secs[p] = time.time() - t0
+    h0, h1 = hist[0], hist[prec]
+    rows = []
+    for k in range(args.n_outer):
+        rows.append({"step": k, "eps": float(h0[k, 12]), "E_fp32": float(h0[k, 0]),
+                     "E": float(h1[k, 0]), "E_rel": float(abs(h1[k, 0] - h0[k, 0]) / abs(h0[k, 0])),
+                     "L_rel": float(abs(h1[k, 1] - h0[k, 1]) / abs(h0[k, 1])),
+                     "dGamma_fp32": float(h0[k, 11]), "dGamma": float(h1[k, 11]),
+                     "col_l1_fp32": float(h0[k, 7]), "col_l1": float(h1[k, 7])})
+    print(json.dumps({"accuracy": workload_name(args), "prec": args.prec,
+                      "seconds": {"fp32": secs[0], args.prec: secs[prec]}, "steps": rows}))
 
 
 def gw_out(torch, dev, n, m, D):
@@ -598,6 +653,10 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, rank, world, local)
+        return
+    if args.accuracy:
+        if rank == 0:
+            run_accuracy(args, local)
         return
     run_gw(args, rank, world, local)
 
