@@ -3,12 +3,13 @@
 // the cross-covariance line of Algorithm 1 (Xtilde, Gamma_{t+1} = sum_j W_j Y_j^T)
 // with both contractions as tcgen05 MMAs, like an attention forward pass:
 //   1. exponent: the column-softmin operands (targets j as rows, sources i as
-//      columns, shift estimate g) give, per 128 x 64 tile, out_ji =
-//      log2(pi_ij / b_j) + 30 in TMEM (the same 16-bit split product as the
-//      softmin);
-//   2. the epilogue warps form q = exp2(out - 18) = 2^12 pi_ij / b_j and split
-//      it into f16 hi + lo, written to shared memory in the 128-byte swizzled
-//      K-major layout of an MMA A operand;
+//      columns, shift estimate g, shift bias 12) give, per 128 x 64 tile,
+//      out_ji = log2(pi_ij / b_j) + 12 in TMEM (the same 16-bit split product
+//      as the softmin);
+//   2. the epilogue warps form q = exp2(out) = 2^12 pi_ij / b_j and split it
+//      into f16 hi (q with its mantissa cut to f16 width, exact) + lo (the
+//      exact remainder, rounded), written to shared memory in the 128-byte
+//      swizzled K-major layout of an MMA A operand;
 //   3. W accumulates in TMEM as q_hi U_hi + q_hi U_lo + q_lo U_hi, with
 //      U = [X, s, 1] (per feature scaled by a power of two, f16 hi + lo,
 //      stored feature-major so its tiles are K-major B operands).
@@ -27,8 +28,9 @@ constexpr int kPlanBM = 256;
 constexpr int kPlanBN = 64;
 constexpr int kPlanEpiWarps = 16;
 constexpr int kPlanThreads = 64 + 32 * kPlanEpiWarps;
-constexpr float kPlanQBias = 18.0f;        // out - 18 = log2(2^12 pi / b)
+constexpr float kPlanShiftBias = 12.0f;    // out = log2(2^12 pi / b)
 constexpr float kPlanQScale = 4096.0f;     // 2^12
+constexpr uint32_t kHalfMaxBits = 0x477FE000u;   // 65504.0f: larger q (or inf / NaN) do not fit
 constexpr uint32_t kPlanWCol = 256;        // W accumulators after 2 buffers x 2 halves x 64
 
 template <int KP, int S, int NW>
@@ -222,7 +224,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     const int ch = g >> 1;  // column half of the 64-column tile
     const int q = warp & 3; // TMEM lane quarter
     const int rloc = q * 32 + lane;
-    bool ok = true, bad = false;
+    bool ok = true;
+    uint32_t qbits = 0;
     unsigned char* Ph = Ps + (h * 2 + 0) * L::kPBytes;
     unsigned char* Pl = Ps + (h * 2 + 1) * L::kPBytes;
     const uint32_t prow = static_cast<uint32_t>((rloc >> 3) * 1024 + (rloc & 7) * 128);
@@ -244,20 +247,22 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
-      // q = 2^12 pi_ij / b_j as f16 hi + lo, packed in pairs along the sources
+      // q = 2^12 pi_ij / b_j as f16 hi + lo, packed in pairs along the sources:
+      // hi keeps the top 11 significant bits (exact in f16 for q >= 2^-14),
+      // lo = q - hi is exact in FP32 and rounded once
       uint32_t hp[16], lp[16];
 #pragma unroll
       for (int k = 0; k < 32; k += 2) {
-        const float q0 = ex2(__uint_as_float(r[k]) - kPlanQBias);
-        const float q1 = ex2(__uint_as_float(r[k + 1]) - kPlanQBias);
-        bad = bad || !(q0 < kHalfMax) || !(q1 < kHalfMax);
-        const __half h0 = __float2half_rn(q0), h1 = __float2half_rn(q1);
-        const __half l0 = __float2half_rn(q0 - __half2float(h0));
-        const __half l1 = __float2half_rn(q1 - __half2float(h1));
-        hp[k / 2] = static_cast<uint32_t>(__half_as_ushort(h0)) |
-                    (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
-        lp[k / 2] = static_cast<uint32_t>(__half_as_ushort(l0)) |
-                    (static_cast<uint32_t>(__half_as_ushort(l1)) << 16);
+        const float q0 = ex2(__uint_as_float(r[k]));
+        const float q1 = ex2(__uint_as_float(r[k + 1]));
+        const uint32_t b0 = __float_as_uint(q0), b1 = __float_as_uint(q1);
+        qbits = max(qbits, max(b0, b1));   // q > 0: bit order = value order (inf, NaN above)
+        const float h0 = __uint_as_float(b0 & 0xFFFFE000u);
+        const float h1 = __uint_as_float(b1 & 0xFFFFE000u);
+        const __half2 hh = __floats2half2_rn(h0, h1);
+        const __half2 ll = __floats2half2_rn(q0 - h0, q1 - h1);
+        hp[k / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+        lp[k / 2] = *reinterpret_cast<const uint32_t*>(&ll);
       }
       // the P tile is free once the W MMAs of the previous tile are done
       if (t > 0) {
@@ -313,6 +318,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
         }
       }
     }
+    const bool bad = qbits >= kHalfMaxBits;
     const bool fail = __any_sync(0xffffffffu, bad || !ok || go == 0) != 0;
     if (fail && lane == 0) atomicExch(T.flag, 1);
   }
@@ -474,7 +480,7 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int
   const float inv_eps = 1.0f / p.eps;
   GW_CUDA_TRY(cudaMemsetAsync(B.mx, 0, 8 * sizeof(unsigned), st));
   tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(V, p.m * p.D, p.X, p.n * p.D, p.t, p.m, p.s, p.n,
-                                                 p.f, B.loga, p.g, inv_eps, B.mx);
+                                                 p.f, B.loga, p.g, inv_eps, B.mx, kPlanShiftBias);
   GW_LAUNCH_CHECK();
   const float alpha = 16.0f * kLog2e * inv_eps;
   const float beta = 4.0f * kLog2e * inv_eps;
@@ -482,7 +488,7 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int
   if (bf16) {
     tc_prep_kernel<__nv_bfloat16><<<ceil_div(Lt.rows_pad, 4), blk, 0, st>>>(
         V, p.t, nullptr, nullptr, p.g, p.m, Lt.rows_pad, shp, 0, alpha, beta, inv_eps, B.mx,
-        reinterpret_cast<__nv_bfloat16*>(B.opA));
+        reinterpret_cast<__nv_bfloat16*>(B.opA), kPlanShiftBias);
     GW_LAUNCH_CHECK();
     tc_prep_kernel<__nv_bfloat16><<<ceil_div(Lt.cols_pad, 4), blk, 0, st>>>(
         p.X, p.s, p.f, B.loga, nullptr, p.n, Lt.cols_pad, shp, 1, alpha, beta, inv_eps, B.mx,
@@ -491,7 +497,7 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int
   } else {
     tc_prep_kernel<__half><<<ceil_div(Lt.rows_pad, 4), blk, 0, st>>>(
         V, p.t, nullptr, nullptr, p.g, p.m, Lt.rows_pad, shp, 0, alpha, beta, inv_eps, B.mx,
-        reinterpret_cast<__half*>(B.opA));
+        reinterpret_cast<__half*>(B.opA), kPlanShiftBias);
     GW_LAUNCH_CHECK();
     tc_prep_kernel<__half><<<ceil_div(Lt.cols_pad, 4), blk, 0, st>>>(
         p.X, p.s, p.f, B.loga, nullptr, p.n, Lt.cols_pad, shp, 1, alpha, beta, inv_eps, B.mx,

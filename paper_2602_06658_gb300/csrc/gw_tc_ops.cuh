@@ -80,7 +80,7 @@ __device__ __forceinline__ float split3(float x, int part) {
 __global__ void tc_absmax_kernel(const float* A, int64_t nA, const float* B, int64_t nB,
                                  const float* sA, int64_t n, const float* sB, int64_t m,
                                  const float* h, const float* logw, const float* est,
-                                 float inv_eps, unsigned* mx) {
+                                 float inv_eps, unsigned* mx, float shift_bias = kShiftBias) {
   float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -94,7 +94,7 @@ __global__ void tc_absmax_kernel(const float* A, int64_t nA, const float* B, int
   }
   if (est)
     for (int64_t i = t0; i < n; i += stride)
-      v[5] = fmaxf(v[5], fabsf(est[i] * inv_eps * kLog2e + kShiftBias));
+      v[5] = fmaxf(v[5], fabsf(est[i] * inv_eps * kLog2e + shift_bias));
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
 #pragma unroll
@@ -130,7 +130,8 @@ template <class T>
 __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, const float* logw,
                                const float* est, int64_t rows_valid, int64_t rows_pad,
                                TcOperandShape shp, int role, float alpha, float beta,
-                               float inv_eps, const unsigned* mx, T* op) {
+                               float inv_eps, const unsigned* mx, T* op,
+                               float shift_bias = kShiftBias) {
   const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
   if (r >= rows_pad) return;
   const float mA = __uint_as_float(mx[0]), mB = __uint_as_float(mx[1]);
@@ -174,7 +175,7 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
         if (role == 1) {
           v = ce;
         } else if (est) {
-          v = split3<T>((est[r] * inv_eps * kLog2e + kShiftBias) / ce, k - shp.col_e);
+          v = split3<T>((est[r] * inv_eps * kLog2e + shift_bias) / ce, k - shp.col_e);
         }
       } else if (k == shp.col_k) {
         // mask: zero-weight target columns never contribute
