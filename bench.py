@@ -60,10 +60,14 @@ def parse():
                          "of the same shape (kernel-only runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
-    ap.add_argument("--workload", default="gmm8", choices=["gmm8", "sphere", "serving"],
+    ap.add_argument("--workload", default="gmm8",
+                    choices=["gmm8", "sphere", "serving", "square-batch"],
                     help="gmm8: the cells/s workload; sphere: unit sphere vs a smooth warp "
                          "(use with --n 250000 --D 64 --eps1 5e-4); serving: request stream, "
-                         "p50/p99 latency")
+                         "p50/p99 latency; square-batch: independent seeded 2D problems "
+                         "(N = M = 1000, 20 x 50), GW solves/s")
+    ap.add_argument("--batch", type=int, default=160, help="square-batch: number of problems")
+    ap.add_argument("--streams", type=int, default=8, help="square-batch: concurrent streams")
     ap.add_argument("--requests", type=int, default=512)
     ap.add_argument("--rate-frac", type=float, default=0.8,
                     help="serving arrival rate as a fraction of the measured saturated throughput")
@@ -567,6 +571,85 @@ def run_reference(args, rank, world):
     del O
 
 
+def run_square_batch(args, rank, world, local):
+    """Independent solves of the 2D squared-Euclidean problem (x ~ U[0,1]^2,
+    N = M = 1000, y = rotated x + N(0, 0.01^2) noise, shuffled, eps =
+    1e-2 diam^2, 20 outer x 50 symmetric Sinkhorn iterations), one seed per
+    problem, spread over several streams, each solve one CUDA graph; inputs
+    resident before timing.  Metric: GW solves/s over the whole batch."""
+    import numpy as np
+    import torch
+    import paper_2602_06658_gb300 as gw
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = PREC[args.prec]
+    probs = []
+    for k in range(args.batch):
+        w = W.square_rotated(1000, args.seed + 1000 * rank + k)
+        a = np.asarray(w["a"], np.float64)
+        b = np.asarray(w["b"], np.float64)
+        x = w["x"] - a @ w["x"]
+        y = w["y"] - b @ w["y"]
+        t32 = lambda v: torch.tensor(np.ascontiguousarray(v, dtype=np.float32), device=dev)
+        probs.append(dict(X=t32(x), Y=t32(y), s=t32((x * x).sum(1)), t=t32((y * y).sum(1)),
+                          a=t32(a), b=t32(b), eps=float(w["eps"])))
+    streams = [torch.cuda.Stream(device=dev) for _ in range(args.streams)]
+    wss = [gw.workspace(gw.gw_workspace_size(gw.OP_SOLVE, 1000, 1000, 2, 2, prec), dev)
+           for _ in streams]
+    outs = [gw_out(torch, dev, 1000, 1000, 2) for _ in streams]
+    for o in outs:
+        o["Gamma"] = torch.empty(2, 2, dtype=torch.float64, device=dev)
+        o["Gamma_plan"] = torch.empty(2, 2, dtype=torch.float64, device=dev)
+
+    def run(batch):
+        energies = []
+        for k, P in enumerate(batch):
+            j = k % len(streams)
+            with torch.cuda.stream(streams[j]):
+                o = gw.gw_solve(P["X"], P["Y"], P["s"], P["t"], P["a"], P["b"], P["eps"], 20, 50,
+                                prec=prec, record=False, ws=wss[j], out=outs[j],
+                                stream=streams[j])
+                energies.append(o["energy"][0].clone())
+        return energies
+
+    run(probs[:len(streams)])          # warm-up: one solve per stream
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    gw.gw_kernel_launches(reset=True)
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for st in streams:
+        st.wait_event(e0)
+    energies = run(probs)
+    e1s = []
+    for st in streams:
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(st)
+        e1s.append(ev)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dev_s = max(e0.elapsed_time(ev) for ev in e1s) / 1e3
+    launches = gw.gw_kernel_launches(reset=True)
+    clk = clocks.stop()
+    E = torch.stack(energies).cpu().numpy()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "GW solves/s (2D squared, N=M=1000, 20 x 50)", "value": args.batch / wall,
+            "unit": "solves/s", "higher_is_better": True, "n_gpus": world,
+            "device_seconds": dev_s, "wall_seconds": wall, "solves": args.batch,
+            "streams": args.streams, "dtype": DTYPE[args.prec], "data": "synthetic",
+            "cells_per_s": args.batch * 1000.0 * 1000.0 * 20 * 50 / wall,
+            "energy_mean": float(E.mean()), "energy_finite": bool(np.isfinite(E).all()),
+            "gpu_launches": launches, "clocks": clk,
+            "config": {"workload": "square-batch: U[0,1]^2 vs rotated + N(0, 0.01^2), shuffled, "
+                                   "N=M=1000, eps=1e-2 diam^2, 20 outer x 50 symmetric Sinkhorn",
+                       "seeds": f"{args.seed}..{args.seed + args.batch - 1}",
+                       "host_time_included": "yes: graph capture and instantiation per solve"}}),
+              flush=True)
+
+
 def run_serving(args, rank, world, local):
     """Request stream (Poisson arrivals, N and M log-uniform in [500, 50k],
     squared (D = 3) or lifted (D = 16, 32) penalties, eps log-uniform in
@@ -653,6 +736,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, rank, world, local)
+        return
+    if args.workload == "square-batch":
+        run_square_batch(args, rank, world, local)
         return
     if args.accuracy:
         if rank == 0:

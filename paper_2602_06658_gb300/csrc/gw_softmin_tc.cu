@@ -52,7 +52,7 @@ constexpr int kBM = 256;       // rows per CTA (two M = 128 halves)
 // columns per tile: 128, or 64 for the widest operands (KP = 256) so that the
 // ring still fits in shared memory
 __host__ __device__ constexpr int tile_cols(int KP) { return KP >= 256 ? 64 : 128; }
-constexpr int kEpiWarps = 16;  // 4 per scheduler: 2 per (half, lane quarter), one per tile parity
+constexpr int kEpiWarps = 16;  // 4 per scheduler: 2 per (half, lane quarter), one per column half
 constexpr int kThreadsTc = 64 + 32 * kEpiWarps;
 constexpr float kRunInit = -1.0e9f;          // running max start (below every real exponent)
 constexpr float kSumLo = 8.673617e-19f;      // 2^-60: a total below this underflowed
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&tfull[b], 1);
-      tc::mbar_init(&tempty[b], kEpiWarps / 2);   // the 8 warps of one tile parity
+      tc::mbar_init(&tempty[b], kEpiWarps);
     }
     tc::mbar_init(afull, 1);
     tc::mbar_init(drain, 1);
@@ -286,19 +286,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    // warp -> (tile parity ch, half h, lane quarter q = warp % 4): the warps of
-    // parity ch take the tiles t = ch, ch + 2, ... (TMEM buffer ch) over all
-    // of their rows' columns, so while one parity waits for its tile the
-    // other keeps the MUFU busy; the two partial sums of a row merge at the end
+    // warp -> (half h, lane quarter q = warp % 4, column half ch): each row's
+    // 128 columns per tile are shared by two warps, merged at the end
     const int e = warp - 2;
-    const int ch = e >> 3;
-    const int h = (e >> 2) & 1;
+    const int g = e >> 2;
+    const int h = g & 1;
+    const int ch = g >> 1;
     const int q = warp & 3;
     const int64_t row = static_cast<int64_t>(row0) + h * 128 + q * 32 + lane;
     // fast pass: the MMA already subtracted the shift e_i, the sum starts at 0
     float mrun = FAST ? 0.0f : kRunInit, srun = 0.0f;
     bool ok = true;
-    for (int t = ch; t < ntiles; t += 2) {
+    for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
       // one lane waits, the warp follows: tcgen05.ld needs a converged warp
       int got = 0;
@@ -309,30 +308,26 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         break;
       }
       tc::tc_fence_after();
-      const uint32_t tcol = tbase + (static_cast<uint32_t>(q * 32) << 16) + (b * 2 + h) * BN;
-      // 32-column chunks, the next one loading while the current one is reduced
-      uint32_t ra[32], rb[32];
-      tc::tmem_ld32_issue(tcol, ra);
-      tc::tmem_ld_wait(ra);
-#pragma unroll
-      for (int c = 0; c + 2 <= BN / 32; c += 2) {
-        tc::tmem_ld32_issue(tcol + (c + 1) * 32, rb);
+      const uint32_t tcol =
+          tbase + (static_cast<uint32_t>(q * 32) << 16) + (b * 2 + h) * BN + ch * (BN / 2);
+      uint32_t ra[32];
+      if constexpr (BN == 128) {
+        // the warp's 64 columns in one TMEM load, reduced as two chunks of 32
+        uint32_t r64[64];
+        tc::tmem_ld64_issue(tcol, r64);
+        tc::tmem_ld_wait(r64);
+        chunk<FAST>(*reinterpret_cast<const uint32_t(*)[32]>(&r64[0]), mrun, srun);
+        chunk<FAST>(*reinterpret_cast<const uint32_t(*)[32]>(&r64[32]), mrun, srun);
+      } else {
+        tc::tmem_ld32_issue(tcol, ra);
+        tc::tmem_ld_wait(ra);
         chunk<FAST>(ra, mrun, srun);
-        tc::tmem_ld_wait(rb);
-        if (c + 2 < BN / 32) {
-          tc::tmem_ld32_issue(tcol + (c + 2) * 32, ra);
-          chunk<FAST>(rb, mrun, srun);
-          tc::tmem_ld_wait(ra);
-        } else {
-          // every column of the buffer is in registers: hand it back first
-          tc::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&tempty[b]);
-          chunk<FAST>(rb, mrun, srun);
-        }
       }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[b]);
     }
-    // merge the two tile parities of each row (named barrier of the epilogue
+    // merge the two column halves of each row (named barrier of the epilogue
     // warps only); the ch = 0 warp writes the row
     {
       float* xm = reinterpret_cast<float*>(bars + 2 * S + 8);   // [256] shifts
