@@ -61,11 +61,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--workload", default="gmm8",
-                    choices=["gmm8", "sphere", "serving", "square-batch"],
+                    choices=["gmm8", "sphere", "serving", "square-batch", "grad"],
                     help="gmm8: the cells/s workload; sphere: unit sphere vs a smooth warp "
                          "(use with --n 250000 --D 64 --eps1 5e-4); serving: request stream, "
                          "p50/p99 latency; square-batch: independent seeded 2D problems "
-                         "(N = M = 1000, 20 x 50), GW solves/s")
+                         "(N = M = 1000, 20 x 50), GW solves/s; grad: the adjoint (gradient "
+                         "w.r.t. the source points through the lift) after a solve, use with --n 20000")
     ap.add_argument("--batch", type=int, default=160, help="square-batch: number of problems")
     ap.add_argument("--streams", type=int, default=8, help="square-batch: concurrent streams")
     ap.add_argument("--requests", type=int, default=512)
@@ -437,9 +438,12 @@ def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps
     launches): both half-steps fused in one launch, the 16-bit operands of
     the outer step reused, only the potential columns refreshed.  Work per
     launch: 2 N M cells (row and column softmins).
-    Tensor-core forms: bound = MUFU ex2, one exp2 per cell; peak = 152 SMs x
-    32 ex2/clk x max SM clock.  FP32 form: bound = FP32 FMA pipe, 2K + 2 FLOP
-    per cell; peak = 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock."""
+    Tensor-core forms: two ceilings, reported side by side, the higher
+    fraction naming the bound: MUFU (one exp2 per cell; peak = 152 SMs x 32
+    ex2/clk x max SM clock) and the tensor pipe (2 x used operand columns
+    FLOP per cell; peak = the measured cuBLAS bf16 burst rate).  FP32 form:
+    bound = FP32 FMA pipe, 2K + 2 FLOP per cell; peak = 152 SMs x 128 FP32
+    lanes x 2 FLOP x max SM clock."""
     n, m, D = X.shape[0], Y.shape[0], X.shape[1]
     V = (state["Gamma"].float() @ Y.T).T.contiguous()
     loga, logb = torch.log(a), torch.log(b)
@@ -479,14 +483,35 @@ def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {clk/1e6:.0f} MHz "
                                f"(clock from {src} peaks file)",
                 "ms_per_launch": dt * 1e3, "cells_per_s": cells / dt}
+    # the exponent is one 16-bit contraction per cell over `used` operand
+    # columns (mult * K split products + 3 rank-one + 3 bias + 3 shift + 1
+    # mask), 2 * used FLOP of it algorithmic (the zero padding to a multiple
+    # of 16 is not); MUFU does one exp2 per cell
+    mult = 1 if prec == PREC["bf16"] else 3
+    used = mult * D + 10
     ex2 = 152 * 32 * clk
+    tens = float(peaks.get("bf16_tflops", 1900.0)) * 1e12
+    mufu_frac = cells / dt / ex2
+    tens_frac = cells * 2.0 * used / dt / tens
     traffic, tsrc = tc_kernel_traffic() if (n, m, D) == (100_000, 100_000, 32) else (None, "other size")
+    common = {"traffic": traffic, "traffic_source": tsrc,
+              "kernel": "tcgen05 softmin, one fused Sinkhorn iteration as in the solve "
+                        "(row + column half-steps, 2 N M cells per launch, operands reused)",
+              "ms_per_launch": dt * 1e3, "cells_per_s": cells / dt,
+              "mufu": {"achieved": cells / dt / 1e12, "peak": ex2 / 1e12, "unit": "Tex2/s",
+                       "frac": mufu_frac,
+                       "peak_source": f"derived: 152 SMs x 32 MUFU ex2/clk x {clk/1e6:.0f} MHz"},
+              "tensor": {"achieved": cells * 2.0 * used / dt / 1e12, "peak": tens / 1e12,
+                         "unit": "TFLOP/s", "frac": tens_frac,
+                         "flop_per_cell": 2 * used,
+                         "peak_source": f"{src}: cuBLAS bf16 GEMM burst (same rate for f16)"}}
+    if tens_frac >= mufu_frac:
+        return {"bound": "tensor", "achieved": cells * 2.0 * used / dt / 1e12, "peak": tens / 1e12,
+                "unit": "TFLOP/s", "frac": tens_frac,
+                "peak_source": f"{src}: cuBLAS bf16 GEMM burst", **common}
     return {"bound": "alu", "achieved": cells / dt / 1e12, "peak": ex2 / 1e12, "unit": "Tex2/s",
-            "frac": cells / dt / ex2, "traffic": traffic, "traffic_source": tsrc,
-            "kernel": "tcgen05 softmin, one fused Sinkhorn iteration as in the solve "
-                      "(row + column half-steps, 2 N M cells per launch, operands reused)",
-            "peak_source": f"derived: 152 SMs x 32 MUFU ex2/clk x {clk/1e6:.0f} MHz",
-            "ms_per_launch": dt * 1e3, "cells_per_s": cells / dt}
+            "frac": mufu_frac, "peak_source": f"derived: 152 SMs x 32 MUFU ex2/clk x {clk/1e6:.0f} MHz",
+            **common}
 
 
 def run_e2e(args, gw, torch, dev, X, Y, s, t, a, b, prec, ws):
@@ -650,6 +675,61 @@ def run_square_batch(args, rank, world, local):
               flush=True)
 
 
+def run_grad(args, rank, world, local):
+    """The adjoint after a solve: 3D 8-blob clouds, ||x - x'|| lifted by Kernel
+    PCA (D features), eps annealed over n_outer x n_inner iterations in
+    --prec; then gw_grad_x (row-direction plan sums, closed-form feature
+    gradient, centering adjoint and the N x N Kernel-Proj VJP to the raw
+    points) timed with CUDA events after warm-up."""
+    import torch
+    import paper_2602_06658_gb300 as gw
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = PREC[args.prec]
+    n, D = args.n, args.D
+    w = W.gmm_rigid(n, seed=args.seed + rank)
+    a = torch.full((n,), 1.0 / n, device=dev)
+    xt = torch.tensor(w["x"], dtype=torch.float32, device=dev)
+    lx = gw.gw_lift(xt, D, kind=gw.PEN_POWER, param=1.0, w=a, want_basis=True)
+    ly = gw.gw_lift(torch.tensor(w["y"], dtype=torch.float32, device=dev), D, kind=gw.PEN_POWER,
+                    param=1.0, w=a)
+    o = gw.gw_solve(lx["X"], ly["X"], lx["s"], ly["s"], a, a, args.eps0, args.n_outer,
+                    args.n_inner, eps_final=args.eps1, prec=prec, record=False)
+    eps_T = float(o["energy"][12].item())
+    ws = gw.workspace(gw.gw_workspace_size(gw.OP_GRAD, n, n, D, D, prec), dev)
+
+    def grad():
+        return gw.gw_grad_x(lx["X"], ly["X"], lx["s"], ly["s"], a, a, o["f"], o["g"],
+                            o["Gamma_plan"], o["Gamma"], eps_T, prec=prec, x=xt,
+                            kind=gw.PEN_POWER, param=1.0, basis=lx["V"], eigvals=lx["lam"], ws=ws)
+
+    for _ in range(3):
+        grad()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        dX, dx = grad()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    dt = statistics.median(times)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "adjoint time (gradient w.r.t. source points)", "value": dt, "unit": "s",
+            "higher_is_better": False, "n_gpus": world, "steps": args.steps, "warmup": 3,
+            "dtype": DTYPE[args.prec], "data": "synthetic",
+            "pairs_per_s": (float(n) * n + float(n) * n) / dt,
+            "grad_finite": bool(torch.isfinite(dx).all().item()),
+            "energy": float(o["energy"][0].item()), "eps_final": eps_T,
+            "config": {"workload": f"grad: gmm8-3d N=M={n} ||x-x'|| Kernel-PCA D={D}, eps "
+                                   f"{args.eps0}->{args.eps1} over {args.n_outer} x {args.n_inner}",
+                       "work": "N x M plan sums + N x N Kernel-Proj VJP per gradient"}}),
+              flush=True)
+
+
 def run_serving(args, rank, world, local):
     """Request stream (Poisson arrivals, N and M log-uniform in [500, 50k],
     squared (D = 3) or lifted (D = 16, 32) penalties, eps log-uniform in
@@ -739,6 +819,9 @@ def main():
         return
     if args.workload == "square-batch":
         run_square_batch(args, rank, world, local)
+        return
+    if args.workload == "grad":
+        run_grad(args, rank, world, local)
         return
     if args.accuracy:
         if rank == 0:

@@ -433,7 +433,8 @@ typedef struct gw_request {
   int D;                /* feature dimension for lifted penalties */
   float eps, eps_final; /* temperature schedule (eps_final <= 0: constant) */
   int n_outer, n_inner;
-  int prec;             /* GW_PREC_* */
+  int prec;             /* GW_PREC_*; requests with n * m < 8e6 run the FP32 kernels (faster
+                           there, and at least as accurate) */
 } gw_request;
 
 typedef struct gw_response {

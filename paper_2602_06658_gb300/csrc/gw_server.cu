@@ -28,6 +28,9 @@
 namespace gw {
 namespace {
 
+constexpr double kSmallCells = 8.0e6;   // N*M below which requests run the FP32 kernels
+
+
 double now_s() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
@@ -194,7 +197,10 @@ void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
     O.n_outer = r.n_outer;
     O.n_inner = r.n_inner;
     O.symmetric = 1;
-    O.prec = r.prec;
+    // Below ~8e6 cells an iteration of the tensor-core forms is bound by its
+    // ~10 small launches (operand refresh, two passes, merges); the FP32
+    // kernels are faster there and at least as accurate.
+    O.prec = static_cast<double>(r.n) * static_cast<double>(r.m) < kSmallCells ? GW_PREC_FP32 : r.prec;
     O.record = 0;
     O.use_graph = 1;
     gw_result R{G, Gp, f, g, en, nullptr};
