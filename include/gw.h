@@ -214,7 +214,7 @@ typedef struct gw_options {
   int prec;           /* GW_PREC_* for the cost tiles */
   int record;         /* 1: energy record after every outer step into history */
   int use_graph;      /* 1: capture the whole solve as one CUDA graph */
-  const double* Gamma0; /* D x E initial map, NULL = 0 (Algorithm 1, first line) */
+  const double* Gamma0; /* D x E initial map, NULL = 0 (the start of Algorithm 1) */
   const float* f0;    /* initial potentials (warm start), NULL = 0 */
   const float* g0;
   /* Algorithm 6 (Appendix B.4) applied to CNT-GW: 1 = n_inner is the initial

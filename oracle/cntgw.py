@@ -109,7 +109,7 @@ def sqnorms(X):
 
 def kernel_from_cost(C, a):
     """Algorithm 4 (Kernel): K_ij = (C_i1 + C_1j - C_ij)/2 with base index 1
-    (Prop. 2.3), then the weighted double centering of its second line."""
+    (Prop. 2.3), then the weighted double centering that Algorithm 4 applies."""
     C = np.asarray(C, F64)
     a = np.asarray(a, F64)
     K = (C[:, :1] + C[:1, :] - C) / 2.0

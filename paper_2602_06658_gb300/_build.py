@@ -2,7 +2,7 @@
 
 Every translation unit compiles in parallel to an object file; the objects
 link into one shared library with the CUDA runtime linked statically, so the
-library depends on nothing but the driver.
+library depends on nothing but the CUDA driver.
 """
 
 from __future__ import annotations

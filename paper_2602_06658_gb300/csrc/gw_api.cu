@@ -54,7 +54,7 @@ int check_dims(int64_t n, int64_t m, int D, int E) {
 int check_prec(int prec) {
   GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_F16X3, GW_EINVAL, "unknown precision %d",
              prec);
-  GW_REQUIRE(prec_ok(prec), GW_EUNSUPPORTED, "precision %d is not available in this build", prec);
+  GW_REQUIRE(prec_ok(prec), GW_EUNSUPPORTED, "precision %d is not supported", prec);
   return GW_OK;
 }
 
@@ -214,7 +214,7 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
                                pow(static_cast<double>(o.eps_final) / o.eps,
                                    static_cast<double>(t) / (o.n_outer - 1)));
     }
-    // Zbar_j <- Gamma_t Y_j (Algorithm 1, line 4)
+    // Zbar_j <- Gamma_t Y_j (Algorithm 1)
     GW_TRY(launch_gamma_y(B.G[Gc], p.Y, p.m, p.D, p.E, B.V, st));
     int n_run = n_cur;
     bool checked = false;
@@ -237,7 +237,7 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
         }
       }
     }
-    // Xtilde / Gamma_{t+1} lines of Algorithm 1, plus the energy record
+    // Xtilde and Gamma_{t+1} of Algorithm 1, plus the energy record
     PlanArgs pa;
     pa.X = p.X;
     pa.Y = p.Y;

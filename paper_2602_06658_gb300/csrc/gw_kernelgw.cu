@@ -500,7 +500,7 @@ int run_kernel_gw(const float* CX, const float* CY, const float* a, const float*
   cublasHandle_t h = nullptr;
   GW_TRY(blas_handle(&h));
   GW_REQUIRE(blas().set_stream(h, st) == CUBLAS_STATUS_SUCCESS, GW_ECUDA, "cublasSetStream failed");
-  // Algorithm 4 on both sides (line 1 of Algorithm 5)
+  // Algorithm 4 on both sides (the kernels of Algorithm 5)
   GW_TRY(kernel_from_cost_dev(CX, a, n, B.KX, B.k, B.MX, B, st));
   GW_TRY(kernel_from_cost_dev(CY, b, m, B.KY, B.l, B.MY, B, st));
   GW_TRY(launch_log(a, n, B.loga, st));

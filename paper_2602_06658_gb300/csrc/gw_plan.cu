@@ -1,5 +1,5 @@
-// Plan-weighted reductions of CNT-GW (Algorithm 1's Xtilde / Gamma_{t+1}
-// lines, Theorem 3.3), the moments behind C(alpha, beta) (Lemma, Appendix C.1),
+// Plan-weighted reductions of CNT-GW (the Xtilde and Gamma_{t+1} steps of
+// Algorithm 1, Theorem 3.3), the moments behind C(alpha, beta) (Lemma, Appendix C.1),
 // the marginals and the energy record, FP32 CUDA-core form.
 //
 // The plan pi_ij = a_i b_j exp((f_i + g_j - C_ij)/eps) is rebuilt tile by tile

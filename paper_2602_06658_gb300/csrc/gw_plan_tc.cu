@@ -1,6 +1,6 @@
 // Plan-weighted column reduction on the tensor cores:
 //   W_j = sum_i pi_ij [X_i, s_i, 1],   pi_ij = a_i b_j exp((f_i + g_j - c_ij) / eps),
-// the cross-covariance line of Algorithm 1 (Xtilde, Gamma_{t+1} = sum_j W_j Y_j^T)
+// the cross-covariance step of Algorithm 1 (Xtilde, Gamma_{t+1} = sum_j W_j Y_j^T)
 // with both contractions as tcgen05 MMAs, like an attention forward pass:
 //   1. exponent: the column-softmin operands (targets j as rows, sources i as
 //      columns, shift estimate g, shift bias 12) give, per 128 x 64 tile,
