@@ -61,12 +61,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--workload", default="gmm8",
-                    choices=["gmm8", "sphere", "serving", "square-batch", "grad"],
+                    choices=["gmm8", "sphere", "serving", "square-batch", "grad", "multiscale"],
                     help="gmm8: the cells/s workload; sphere: unit sphere vs a smooth warp "
                          "(use with --n 250000 --D 64 --eps1 5e-4); serving: request stream, "
                          "p50/p99 latency; square-batch: independent seeded 2D problems "
                          "(N = M = 1000, 20 x 50), GW solves/s; grad: the adjoint (gradient "
-                         "w.r.t. the source points through the lift) after a solve, use with --n 20000")
+                         "w.r.t. the source points through the lift) after a solve, use with --n 20000; "
+                         "multiscale: time to solution of Multiscale-GW against the direct solve")
     ap.add_argument("--batch", type=int, default=160, help="square-batch: number of problems")
     ap.add_argument("--streams", type=int, default=8, help="square-batch: concurrent streams")
     ap.add_argument("--requests", type=int, default=512)
@@ -730,6 +731,62 @@ def run_grad(args, rank, world, local):
               flush=True)
 
 
+def run_multiscale(args, rank, world, local):
+    """Time to solution on the lifted 3D workload: the direct annealed solve
+    (n_outer x n_inner) against Multiscale-GW (K-Means to 10% of the points,
+    as the paper's default ratio; the coarse solve at the first eps, then a
+    warm-started fine solve of fewer outer steps), both from Gamma_0 = 0, each
+    timed with CUDA events around the whole call after a warm-up call."""
+    import numpy as np
+    import torch
+    import paper_2602_06658_gb300 as gw
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = PREC[args.prec]
+    X, Y, s, t, a, b = make_features(args, gw, torch, dev, args.seed + rank)
+    n, m = X.shape[0], Y.shape[0]
+    kx, ky = max(1, n // 10), max(1, m // 10)
+    g = np.random.default_rng(args.seed + 17)
+    ix = torch.tensor(g.choice(n, kx, replace=False), dtype=torch.int64, device=dev)
+    iy = torch.tensor(g.choice(m, ky, replace=False), dtype=torch.int64, device=dev)
+    fine_outer = max(2, args.n_outer // 4)
+
+    def direct():
+        return gw.gw_solve(X, Y, s, t, a, b, args.eps0, args.n_outer, args.n_inner,
+                           eps_final=args.eps1, prec=prec, record=False)
+
+    def multiscale():
+        return gw.gw_multiscale(X, Y, s, t, a, b, args.eps0, ix, iy, 10, args.n_outer,
+                                args.n_inner, fine_outer, args.n_inner, eps_final=args.eps1,
+                                prec=prec, record=False)
+
+    res = {}
+    for name, fn in (("direct", direct), ("multiscale", multiscale)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        o = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        en = o["energy"].cpu().numpy()
+        res[name] = {"seconds": e0.elapsed_time(e1) / 1e3, "wall_seconds": time.perf_counter() - t0,
+                     "E": float(en[0]), "row_l1": float(en[6]), "col_l1": float(en[7]),
+                     "eps": float(en[12])}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "time to solution (Multiscale-GW vs direct)",
+            "value": res["multiscale"]["seconds"], "unit": "s", "higher_is_better": False,
+            "speedup": res["direct"]["seconds"] / res["multiscale"]["seconds"],
+            "E_rel_diff": abs(res["multiscale"]["E"] - res["direct"]["E"]) / abs(res["direct"]["E"]),
+            "direct": res["direct"], "multiscale": res["multiscale"], "n_gpus": world,
+            "dtype": DTYPE[args.prec], "data": "synthetic",
+            "config": {"workload": workload_name(args), "coarse_points": [kx, ky],
+                       "coarse_outer": args.n_outer, "fine_outer": fine_outer,
+                       "kmeans_rounds": 10, "n_inner": args.n_inner}}), flush=True)
+
+
 def run_serving(args, rank, world, local):
     """Request stream (Poisson arrivals, N and M log-uniform in [500, 50k],
     squared (D = 3) or lifted (D = 16, 32) penalties, eps log-uniform in
@@ -822,6 +879,9 @@ def main():
         return
     if args.workload == "grad":
         run_grad(args, rank, world, local)
+        return
+    if args.workload == "multiscale":
+        run_multiscale(args, rank, world, local)
         return
     if args.accuracy:
         if rank == 0:

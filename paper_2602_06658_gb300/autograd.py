@@ -6,7 +6,7 @@ from __future__ import annotations
 
 import torch
 
-from . import (EN, PEN_SQEUCLID, PREC_FP32, gw_grad_x, gw_lift, gw_solve)
+from . import (EN, PEN_SQEUCLID, PREC_FP32, gw_grad_x, gw_lift, gw_sgw, gw_solve)
 
 
 class GWEnergy(torch.autograd.Function):
@@ -57,3 +57,45 @@ def gw_energy_fn(x, y, a, b, eps, n_outer, n_inner, **kw):
     return GWEnergy.apply(x, y, a, b, eps, n_outer, n_inner, kw.get("penalty", PEN_SQEUCLID),
                           kw.get("param", 2.0), kw.get("D"), kw.get("prec", PREC_FP32),
                           kw.get("eps_final", 0.0), kw.get("Gamma0"), kw.get("seed", 0))
+
+
+class SGWDivergence(torch.autograd.Function):
+    """SGW_eps(alpha, beta) = GW_eps(alpha, beta) - (GW_eps(alpha, alpha) +
+    GW_eps(beta, beta)) / 2 (Section 4.1), with the gradient with respect to
+    the source points x (envelope theorem, the self term through both of its
+    sides).  gw_sgw computes the value and the gradient in one call; the
+    backward pass scales the stored gradient.  Penalties as GWEnergy."""
+
+    @staticmethod
+    def forward(ctx, x, y, a, b, eps, n_outer, n_inner, penalty=PEN_SQEUCLID, param=2.0, D=None,
+                prec=PREC_FP32, eps_final=0.0, seed=0):
+        x = x.detach().contiguous()
+        y = y.detach().contiguous()
+        lifted = penalty != PEN_SQEUCLID
+        Dx = x.shape[1] if not lifted else int(D)
+        Dy = y.shape[1] if not lifted else int(D)
+        lx = gw_lift(x, Dx, kind=penalty, param=param, w=a, want_basis=lifted, seed=seed)
+        ly = gw_lift(y, Dy, kind=penalty, param=param, w=b, seed=seed + 1)
+        if lifted:
+            out = gw_sgw(lx["X"], ly["X"], lx["s"], ly["s"], a, b, eps, n_outer, n_inner,
+                         eps_final=eps_final, prec=prec, grad=True, x=x, kind=penalty,
+                         param=param, basis=lx["V"], eigvals=lx["lam"])
+            dx = out["dx"]
+        else:
+            out = gw_sgw(lx["X"], ly["X"], lx["s"], ly["s"], a, b, eps, n_outer, n_inner,
+                         eps_final=eps_final, prec=prec, grad=True)
+            dx = out["dX"]
+        ctx.save_for_backward(dx)
+        return out["sgw"][0].clone()
+
+    @staticmethod
+    def backward(ctx, gS):
+        (dx,) = ctx.saved_tensors
+        return (gS * dx, None, None, None, None, None, None, None, None, None, None, None, None)
+
+
+def sgw_fn(x, y, a, b, eps, n_outer, n_inner, **kw):
+    """Functional form: SGWDivergence.apply with keyword options."""
+    return SGWDivergence.apply(x, y, a, b, eps, n_outer, n_inner, kw.get("penalty", PEN_SQEUCLID),
+                               kw.get("param", 2.0), kw.get("D"), kw.get("prec", PREC_FP32),
+                               kw.get("eps_final", 0.0), kw.get("seed", 0))

@@ -113,3 +113,21 @@ def test_sgw_lifted_gradient_runs_through_the_lift(gw):
     want = O.kernel_proj_vjp(host(out["dX"]), xr, xr, host(a), host(lx["V"]), host(lx["lam"]),
                              "power", 1.0)
     assert np.abs(dx - want).max() <= 2e-3 * np.abs(want).max()
+
+
+def test_sgw_autograd_flow_step_decreases_the_divergence(gw):
+    """SGWDivergence through torch.autograd: a finite gradient, and a small
+    step against it on the source points lowers SGW (one step of the gradient
+    flows the divergence is meant for)."""
+    import torch
+    from paper_2602_06658_gb300.autograd import sgw_fn
+    x, y, a, b = clouds(300, 260, 21)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda", requires_grad=True)
+    yt, at, bt = f32(y), f32(a), f32(b)
+    S = sgw_fn(xt, yt, at, bt, 0.05, 20, 100)
+    (gx,) = torch.autograd.grad(S, xt)
+    assert torch.isfinite(gx).all() and gx.abs().max() > 0
+    step = 0.1 * S.item() / (gx * gx).sum().item()
+    x2 = (xt.detach() - step * gx).requires_grad_(True)
+    S2 = sgw_fn(x2, yt, at, bt, 0.05, 20, 100)
+    assert S2.item() < S.item()
