@@ -512,6 +512,7 @@ size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
   c.take<float>(static_cast<size_t>(s) * n);
   c.take<float>(static_cast<size_t>(s) * n);
   c.take<int>(static_cast<size_t>(n_pad / kBM));       // recompute flags per row tile
+  c.take<float>(static_cast<size_t>(2 * 2 * kSmCount));  // per-block maxima of the refresh
   return c.used();
 }
 
@@ -536,6 +537,8 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     all_est = all_est && tasks[q].est != nullptr && tasks[q].est != tasks[q].out;
   // one split count for the launch, chosen from both tasks' tiles
   const int splits = tc_splits(row_tiles[0], col_tiles[0], ntasks == 2 ? row_tiles[1] : 0);
+  RefreshTask refresh[2];
+  memset(refresh, 0, sizeof(refresh));
   for (int q = 0; q < ntasks; ++q) {
     SoftminTask& T = tasks[q];
     const int64_t n_pad = static_cast<int64_t>(row_tiles[q]) * kBM;
@@ -556,32 +559,14 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     const bool use_est = all_est;
     int* flags = ws.take<int>(static_cast<size_t>(row_tiles[q]));
     GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
-    GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q], st));
     const float inv_eps = 1.0f / T.eps;
     if (T.reuse_ops) {
-      // main, rank-one and mask columns are unchanged: refresh the rest
-      GW_CUDA_TRY(cudaMemsetAsync(mx + 4, 0, 2 * sizeof(unsigned), st));
-      tc_bias_absmax_kernel<<<kSmCount, 256, 0, st>>>(T.h, T.logw, T.m, use_est ? T.est : nullptr,
-                                                      T.n, inv_eps, mx);
-      GW_LAUNCH_CHECK();
-      if (bf16) {
-        tc_refresh_kernel<__nv_bfloat16><<<ceil_div(T.n, 256), 256, 0, st>>>(
-            nullptr, nullptr, use_est ? T.est : nullptr, T.n, shp, 0, inv_eps, mx,
-            reinterpret_cast<__nv_bfloat16*>(opA));
-        GW_LAUNCH_CHECK();
-        tc_refresh_kernel<__nv_bfloat16><<<ceil_div(T.m, 256), 256, 0, st>>>(
-            T.h, T.logw, nullptr, T.m, shp, 1, inv_eps, mx, reinterpret_cast<__nv_bfloat16*>(opB));
-        GW_LAUNCH_CHECK();
-      } else {
-        tc_refresh_kernel<__half><<<ceil_div(T.n, 256), 256, 0, st>>>(
-            nullptr, nullptr, use_est ? T.est : nullptr, T.n, shp, 0, inv_eps, mx,
-            reinterpret_cast<__half*>(opA));
-        GW_LAUNCH_CHECK();
-        tc_refresh_kernel<__half><<<ceil_div(T.m, 256), 256, 0, st>>>(
-            T.h, T.logw, nullptr, T.m, shp, 1, inv_eps, mx, reinterpret_cast<__half*>(opB));
-        GW_LAUNCH_CHECK();
-      }
+      // main, rank-one and mask columns are unchanged: the bias and shift
+      // columns of every task are refreshed after this loop, in two launches
+      refresh[q] = RefreshTask{T.h, T.logw, use_est ? T.est : nullptr, T.n, T.m, inv_eps, flags,
+                               row_tiles[q], opA, opB};
     } else {
+    GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q], st));
     GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 8 * sizeof(unsigned), st));
     tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
                                                    T.sB, T.m, T.h, T.logw,
@@ -628,6 +613,22 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     K.out = T.out;
     K.pm = T.pm;
     K.ps = T.ps;
+  }
+  if (tasks[0].reuse_ops) {
+    float* part = ws.take<float>(static_cast<size_t>(2 * 2 * kSmCount));
+    GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
+    tc_refresh_max_kernel<<<kSmCount, 256, 0, st>>>(refresh[0], refresh[1], ntasks, part);
+    GW_LAUNCH_CHECK();
+    int64_t rows = 0;
+    for (int q = 0; q < ntasks; ++q) rows += refresh[q].n + refresh[q].m;
+    if (bf16) {
+      tc_refresh_multi_kernel<__nv_bfloat16><<<ceil_div(rows, 256), 256, 0, st>>>(
+          refresh[0], refresh[1], ntasks, shp, part, kSmCount);
+    } else {
+      tc_refresh_multi_kernel<__half><<<ceil_div(rows, 256), 256, 0, st>>>(
+          refresh[0], refresh[1], ntasks, shp, part, kSmCount);
+    }
+    GW_LAUNCH_CHECK();
   }
   if (ntasks == 1) {
     maps[2] = maps[0];

@@ -189,55 +189,111 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
   }
 }
 
-// Per-iteration refresh: largest |w_j| (finite) and |e_i| -> mx[4], mx[5]
-__global__ void tc_bias_absmax_kernel(const float* h, const float* logw, int64_t m,
-                                      const float* est, int64_t n, float inv_eps, unsigned* mx) {
-  float vw = 0.f, ve = 0.f;
+// Per-iteration refresh of up to two tasks in two launches.  The first writes
+// each block's largest |w_j| (finite) and |e_i| per task to part[task][block][2]
+// and zeroes the tasks' recompute flags; the second reduces those partials in
+// every block (a max, so the order does not matter: the same scales as one
+// grid-wide maximum) and rewrites the bias and shift columns of both sides of
+// both tasks.  Operands come out identical to tc_bias_absmax + tc_refresh.
+struct RefreshTask {
+  const float* h;       // column potentials (B side)
+  const float* logw;    // column log-weights
+  const float* est;     // row shift estimate (A side) or null
+  int64_t n, m;         // A rows, B rows
+  float inv_eps;
+  int* flags;
+  int nflags;
+  void* opA;
+  void* opB;
+};
+
+__global__ void tc_refresh_max_kernel(RefreshTask t0, RefreshTask t1, int ntasks, float* part) {
+  __shared__ float red[2][8];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  for (int64_t i = t0; i < m; i += stride) {
-    const float w = (h[i] * inv_eps + logw[i]) * kLog2e;
-    if (isfinite(w)) vw = fmaxf(vw, fabsf(w));
-  }
-  if (est)
-    for (int64_t i = t0; i < n; i += stride)
-      ve = fmaxf(ve, fabsf(est[i] * inv_eps * kLog2e + kShiftBias));
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int q = 0; q < ntasks; ++q) {
+    const RefreshTask& T = q == 0 ? t0 : t1;
+    float vw = 0.f, ve = 0.f;
+    for (int64_t i = i0; i < T.m; i += stride) {
+      const float w = (T.h[i] * T.inv_eps + T.logw[i]) * kLog2e;
+      if (isfinite(w)) vw = fmaxf(vw, fabsf(w));
+    }
+    if (T.est)
+      for (int64_t i = i0; i < T.n; i += stride)
+        ve = fmaxf(ve, fabsf(T.est[i] * T.inv_eps * kLog2e + kShiftBias));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    vw = fmaxf(vw, __shfl_xor_sync(0xffffffffu, vw, o));
-    ve = fmaxf(ve, __shfl_xor_sync(0xffffffffu, ve, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&mx[4], __float_as_uint(vw));
-    atomicMax(&mx[5], __float_as_uint(ve));
+    for (int o = 16; o > 0; o >>= 1) {
+      vw = fmaxf(vw, __shfl_xor_sync(0xffffffffu, vw, o));
+      ve = fmaxf(ve, __shfl_xor_sync(0xffffffffu, ve, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = vw;
+      red[1][threadIdx.x >> 5] = ve;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float a = 0.f, b = 0.f;
+      for (int k = 0; k < static_cast<int>(blockDim.x >> 5); ++k) {
+        a = fmaxf(a, red[0][k]);
+        b = fmaxf(b, red[1][k]);
+      }
+      part[(static_cast<int64_t>(q) * gridDim.x + blockIdx.x) * 2 + 0] = a;
+      part[(static_cast<int64_t>(q) * gridDim.x + blockIdx.x) * 2 + 1] = b;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+      for (int k = threadIdx.x; k < T.nflags; k += blockDim.x) T.flags[k] = 0;
   }
 }
 
-// Rewrite only the columns that change between Sinkhorn iterations: for the
-// A side the bias constants c_w and the split shift; for the B side the split
-// bias and the shift constants c_e.
 template <class T>
-__global__ void tc_refresh_kernel(const float* h, const float* logw, const float* est,
-                                  int64_t rows_valid, TcOperandShape shp, int role, float inv_eps,
-                                  const unsigned* mx, T* op) {
-  const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= rows_valid) return;
-  const float cw = pow2_scale(__uint_as_float(mx[4]));
-  const float ce = pow2_scale(__uint_as_float(mx[5]));
-  T* row = op + r * shp.KP;
-  if (role == 0) {
-    const float e = est ? (est[r] * inv_eps * kLog2e + kShiftBias) / ce : 0.0f;
-    for (int k = 0; k < 3; ++k) {
-      row[shp.col_w + k] = to16<T>(cw);
-      row[shp.col_e + k] = to16<T>(est ? split3<T>(e, k) : 0.0f);
+__global__ void tc_refresh_multi_kernel(RefreshTask t0, RefreshTask t1, int ntasks,
+                                        TcOperandShape shp, const float* part, int nparts) {
+  __shared__ float cw[2], ce[2];
+  if (threadIdx.x < 32) {
+    for (int q = 0; q < ntasks; ++q) {
+      float a = 0.f, b = 0.f;
+      for (int k = threadIdx.x; k < nparts; k += 32) {
+        a = fmaxf(a, part[(static_cast<int64_t>(q) * nparts + k) * 2 + 0]);
+        b = fmaxf(b, part[(static_cast<int64_t>(q) * nparts + k) * 2 + 1]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+      }
+      if (threadIdx.x == 0) {
+        cw[q] = pow2_scale(a);
+        ce[q] = pow2_scale(b);
+      }
     }
-  } else {
-    const float w = (h[r] * inv_eps + logw[r]) * kLog2e;
-    const bool fin = isfinite(w);
-    for (int k = 0; k < 3; ++k) {
-      row[shp.col_w + k] = to16<T>(fin ? split3<T>(w / cw, k) : 0.0f);
-      row[shp.col_e + k] = to16<T>(ce);
+  }
+  __syncthreads();
+  // rows: task 0 A, task 0 B, task 1 A, task 1 B
+  int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int q = 0; q < ntasks; ++q) {
+    const RefreshTask& K = q == 0 ? t0 : t1;
+    if (r < K.n) {
+      T* row = static_cast<T*>(K.opA) + r * shp.KP;
+      const float e = K.est ? (K.est[r] * K.inv_eps * kLog2e + kShiftBias) / ce[q] : 0.0f;
+      for (int k = 0; k < 3; ++k) {
+        row[shp.col_w + k] = to16<T>(cw[q]);
+        row[shp.col_e + k] = to16<T>(K.est ? split3<T>(e, k) : 0.0f);
+      }
+      return;
     }
+    r -= K.n;
+    if (r < K.m) {
+      T* row = static_cast<T*>(K.opB) + r * shp.KP;
+      const float w = (K.h[r] * K.inv_eps + K.logw[r]) * kLog2e;
+      const bool fin = isfinite(w);
+      for (int k = 0; k < 3; ++k) {
+        row[shp.col_w + k] = to16<T>(fin ? split3<T>(w / cw[q], k) : 0.0f);
+        row[shp.col_e + k] = to16<T>(ce[q]);
+      }
+      return;
+    }
+    r -= K.m;
   }
 }
 
