@@ -413,11 +413,26 @@ PlanLayout plan_layout(int64_t m, int64_t n) {
   Lt.col_tiles = static_cast<int>(ceil_div(n, kPlanBN));
   Lt.rows_pad = static_cast<int64_t>(Lt.row_tiles) * kPlanBM;
   Lt.cols_pad = static_cast<int64_t>(Lt.col_tiles) * kPlanBN;
-  // about two waves of CTAs, at least 8 tiles each
-  int s = static_cast<int>(ceil_div(2 * kSmCount, Lt.row_tiles));
+  // At most 128 source tiles (8192 sources) per split: each split's W sums
+  // in one FP32 TMEM accumulator, whose rounding over a long chain of MMAs
+  // dominates the error of these sums.  Among the counts above that floor
+  // (and with at least 8 tiles per CTA to amortise its set-up), the one that
+  // fills whole waves of 152 CTAs best.
   const int smax = Lt.col_tiles / 8 > 1 ? Lt.col_tiles / 8 : 1;
-  if (s > smax) s = smax;
-  if (s < 1) s = 1;
+  int smin = static_cast<int>(ceil_div(Lt.col_tiles, 128));
+  if (smin > smax) smin = smax;
+  int s = smin;
+  double best = 0.0;
+  for (int c = smin; c <= smax && c <= smin + 64; ++c) {
+    const double ctas = static_cast<double>(Lt.row_tiles) * c;
+    const double waves = ctas / kSmCount;
+    const double eff = waves / ceil(waves);
+    if (eff > best + 1e-3) {
+      best = eff;
+      s = c;
+    }
+    if (eff > 0.97) break;
+  }
   Lt.tiles_per_split = static_cast<int>(ceil_div(Lt.col_tiles, s));
   Lt.splits = static_cast<int>(ceil_div(Lt.col_tiles, Lt.tiles_per_split));
   return Lt;
