@@ -202,6 +202,21 @@ int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* lo
 
 // Kernel PCA / centering lift (gw_lift.cu); synchronous.
 size_t lift_ws_bytes(int64_t n, int D);
+// Its N x N block product Z = C P on the tensor cores (gw_lift_tc.cu):
+// prepare once per point set (coordinate table and cost scale), then one
+// matvec per block; Zp receives `splits` partials [splits][n][RP].
+struct LiftTcBufs {
+  float* xt;
+  uint16_t *Ph, *Pl;
+  unsigned *qmax, *r2;
+  float *uinv, *scal;
+  int splits;
+};
+LiftTcBufs carve_lift_tc(Carver& c, int64_t n, int RP);
+int lift_tc_prepare(const float* x, int64_t n, int d, int kind, float param, int RP,
+                    LiftTcBufs& B, cudaStream_t st);
+int lift_tc_matvec(const float* P, int64_t n, int d, int kind, float param, int RP,
+                   LiftTcBufs& B, float* Zp, cudaStream_t st);
 int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float param, int D,
              int n_iter, uint64_t seed, float* X, float* sqn, float* basis, float* eigvals,
              void* ws, size_t ws_bytes, cudaStream_t st);

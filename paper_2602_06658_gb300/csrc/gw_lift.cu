@@ -7,7 +7,8 @@
 // rank-one u terms, so
 //     K~ = -1/2 (I - 1 w^T) C (I - w 1^T).
 // Its D largest eigenpairs come from block subspace iteration: Q <- K~ Q
-// (matrix-free: C is never stored, each product is one N x N tiled pass),
+// (matrix-free: C is never stored, each product is one N x N tiled pass on
+// the tensor cores, gw_lift_tc.cu),
 // re-orthonormalised by Cholesky QR, and a final Rayleigh-Ritz step.  The
 // small r x r Cholesky and eigen-problems run on the host in float64 (cyclic
 // Jacobi); every N-sized step runs in the kernels below.
@@ -23,79 +24,12 @@ namespace gw {
 
 namespace {
 
-constexpr int kLiftThreads = 128;
-constexpr int kLiftTile = 32;   // source points staged per shared-memory tile
 constexpr int kGramBlocks = 148;
 
 struct CostParams {
   int kind;
   float param;
 };
-
-__device__ __forceinline__ float cnt_cost(float d2, CostParams cp) {
-  if (cp.kind == GW_PEN_SQEUCLID) return d2;
-  if (cp.kind == GW_PEN_POWER) {
-    if (cp.param == 1.0f) return sqrtf(d2);
-    if (cp.param == 2.0f) return d2;
-    return d2 > 0.0f ? exp2f(0.5f * cp.param * log2f(d2)) : 0.0f;
-  }
-  // GW_PEN_GAUSS: 2 (1 - exp(-d2 / (2 sigma^2)))
-  return 2.0f * (1.0f - expf(-d2 / (2.0f * cp.param * cp.param)));
-}
-
-// Zp[split][i][:] = sum_{k in split} C(x_i, x_k) P_k   (rows of P padded to RP)
-template <int RP>
-__global__ void __launch_bounds__(kLiftThreads)
-    cost_matvec_kernel(const float* x, int64_t n, int d, const float* P, CostParams cp,
-                       int64_t cols_per_split, float* Zp) {
-  __shared__ __align__(16) float Ps[kLiftTile][RP];
-  __shared__ float xs[kLiftTile][4];
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * kLiftThreads + threadIdx.x;
-  const bool ok = i < n;
-  float xi[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int c = 0; c < d && c < 4; ++c) xi[c] = ok ? x[i * d + c] : 0.f;
-  float z[RP];
-#pragma unroll
-  for (int r = 0; r < RP; ++r) z[r] = 0.f;
-  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * cols_per_split;
-  const int64_t k1 = k0 + cols_per_split < n ? k0 + cols_per_split : n;
-  for (int64_t kb = k0; kb < k1; kb += kLiftTile) {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < kLiftTile * RP; idx += kLiftThreads) {
-      const int kk = idx / RP, r = idx % RP;
-      const int64_t k = kb + kk;
-      Ps[kk][r] = k < k1 ? P[k * RP + r] : 0.f;
-    }
-    if (threadIdx.x < kLiftTile) {
-      const int64_t k = kb + threadIdx.x;
-      for (int c = 0; c < 4; ++c) xs[threadIdx.x][c] = (k < k1 && c < d) ? x[k * d + c] : 0.f;
-    }
-    __syncthreads();
-    const int cnt = static_cast<int>(k1 - kb < kLiftTile ? k1 - kb : kLiftTile);
-    for (int kk = 0; kk < cnt; ++kk) {
-      float d2 = 0.f;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float df = xi[c] - xs[kk][c];
-        d2 = fmaf(df, df, d2);
-      }
-      const float cv = cnt_cost(d2, cp);
-      const float4* pr = reinterpret_cast<const float4*>(&Ps[kk][0]);
-#pragma unroll
-      for (int r4 = 0; r4 < RP / 4; ++r4) {
-        const float4 pv = pr[r4];
-        z[4 * r4 + 0] = fmaf(cv, pv.x, z[4 * r4 + 0]);
-        z[4 * r4 + 1] = fmaf(cv, pv.y, z[4 * r4 + 1]);
-        z[4 * r4 + 2] = fmaf(cv, pv.z, z[4 * r4 + 2]);
-        z[4 * r4 + 3] = fmaf(cv, pv.w, z[4 * r4 + 3]);
-      }
-    }
-  }
-  if (!ok) return;
-  float* out = Zp + (static_cast<int64_t>(blockIdx.y) * n + i) * RP;
-#pragma unroll
-  for (int r = 0; r < RP; ++r) out[r] = z[r];
-}
 
 // Column sums weighted by w (or plain) of an n x RP matrix: partials per block.
 __global__ void colsum_partial_kernel(const float* Q, const float* w, double wu, int64_t n,
@@ -214,35 +148,62 @@ __global__ void random_block_kernel(float* Q, int64_t count, uint64_t seed) {
 }
 
 // Sign convention: the entry of largest magnitude of each eigenvector is positive.
-__global__ void sign_fix_kernel(float* V, int64_t n, int D, float* X, float* sqn,
-                                const float* sqrt_lam) {
-  // one block; thread c handles column c (D <= 128)
-  __shared__ int flip[128];
-  for (int c = threadIdx.x; c < D; c += blockDim.x) {
-    float best = 0.f;
-    float val = 0.f;
-    for (int64_t i = 0; i < n; ++i) {
-      const float v = V[i * D + c];
-      if (fabsf(v) > best) {
-        best = fabsf(v);
-        val = v;
-      }
+// Per block of rows (in order) and column c < D: the largest |V_ic| and the
+// first row that holds it.  blockDim.x >= D.
+__global__ void sign_partial_kernel(const float* V, int64_t n, int D, double* best,
+                                    double* where) {
+  const int c = threadIdx.x;
+  if (c >= D) return;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk;
+  const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
+  float b = -1.f;
+  int64_t at = i0;
+  for (int64_t i = i0; i < i1; ++i) {
+    const float v = fabsf(V[i * D + c]);
+    if (v > b) {
+      b = v;
+      at = i;
     }
-    flip[c] = val < 0.f;
   }
-  __syncthreads();
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    float s = 0.f;
-    for (int c = 0; c < D; ++c) {
-      float v = V[i * D + c];
-      if (flip[c]) v = -v;
-      V[i * D + c] = v;
-      const float xv = v * sqrt_lam[c];
-      X[i * D + c] = xv;
-      s = fmaf(xv, xv, s);
+  best[static_cast<int64_t>(blockIdx.x) * D + c] = b;
+  where[static_cast<int64_t>(blockIdx.x) * D + c] = static_cast<double>(at);
+}
+
+// flip[c] = 1 when the first entry of largest magnitude of column c is negative
+__global__ void sign_final_kernel(const float* V, int D, int blocks, const double* best,
+                                  const double* where, double* flip) {
+  const int c = threadIdx.x;
+  if (c >= D) return;
+  double b = -1.0, at = 0.0;
+  for (int k = 0; k < blocks; ++k) {
+    const double v = best[static_cast<int64_t>(k) * D + c];
+    if (v > b) {
+      b = v;
+      at = where[static_cast<int64_t>(k) * D + c];
     }
-    sqn[i] = s;
   }
+  flip[c] = V[static_cast<int64_t>(at) * D + c] < 0.f ? 1.0 : 0.0;
+}
+
+// Sign convention applied: V_c <- -V_c where flipped; X = V diag(sqrt(lam)),
+// sqn = ||X_i||^2 (one warp per row)
+__global__ void sign_apply_kernel(float* V, int64_t n, int D, const double* flip, float* X,
+                                  float* sqn, const float* sqrt_lam) {
+  const int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int c = lane; c < D; c += 32) {
+    float v = V[i * D + c];
+    if (flip[c] != 0.0) v = -v;
+    V[i * D + c] = v;
+    const float xv = v * sqrt_lam[c];
+    X[i * D + c] = xv;
+    s = fmaf(xv, xv, s);
+  }
+  s = warp_sum(s);
+  if (lane == 0) sqn[i] = s;
 }
 
 // Squared lift: X = x - sum w x; sqn = ||X||^2 (one block, d <= 128)
@@ -280,14 +241,6 @@ int rpad(int D) {
   for (int o : opts)
     if (o >= want) return o;
   return 128;
-}
-
-int lift_splits(int64_t n) {
-  const int rb = ceil_div(n, kLiftThreads);
-  int s = ceil_div(4 * kSmCount, rb);
-  const int smax = ceil_div(n, 256);
-  if (s > smax) s = smax;
-  return s < 1 ? 1 : s;
 }
 
 // ---- host-side small dense linear algebra (float64) ----
@@ -366,12 +319,14 @@ struct LiftBufs {
   float *Q, *P, *Z, *Zp, *V, *sl;
   double *cs_part, *cs, *g_part, *G, *M;
   int splits, RP;
+  LiftTcBufs tc;
 };
 
 LiftBufs carve_lift(Carver& c, int64_t n, int D) {
   LiftBufs B;
   B.RP = rpad(D);
-  B.splits = lift_splits(n);
+  B.tc = carve_lift_tc(c, n, B.RP);
+  B.splits = B.tc.splits;
   const size_t nr = static_cast<size_t>(n) * B.RP;
   B.Q = c.take<float>(nr);
   B.P = c.take<float>(nr);
@@ -405,21 +360,8 @@ int apply_kernel(const float* x, int64_t n, int d, const float* w, CostParams cp
   GW_TRY(weighted_colsum(B.Q, nullptr, 1.0, n, RP, B, st));            // 1^T Q
   center_right_kernel<<<ceil_div(nr, 256), 256, 0, st>>>(B.Q, w, wu, B.cs, n, RP, B.P);
   GW_LAUNCH_CHECK();
-  const int64_t cps =
-      (static_cast<int64_t>(ceil_div(n, B.splits)) + kLiftTile - 1) / kLiftTile * kLiftTile;
-  const int splits = ceil_div(n, cps);
-  dim3 grid(ceil_div(n, kLiftThreads), splits);
-  float* dst = splits > 1 ? B.Zp : B.Z;
-  switch (RP) {
-    case 16: cost_matvec_kernel<16><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
-    case 32: cost_matvec_kernel<32><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
-    case 48: cost_matvec_kernel<48><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
-    case 64: cost_matvec_kernel<64><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
-    case 80: cost_matvec_kernel<80><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
-    case 96: cost_matvec_kernel<96><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
-    default: cost_matvec_kernel<128><<<grid, kLiftThreads, 0, st>>>(x, n, d, B.P, cp, cps, dst); break;
-  }
-  GW_LAUNCH_CHECK();
+  const int splits = B.splits;
+  GW_TRY(lift_tc_matvec(B.P, n, d, cp.kind, cp.param, RP, B.tc, splits > 1 ? B.Zp : B.Z, st));
   if (splits > 1) {
     reduce_splits_f32_kernel<<<ceil_div(nr, 256), 256, 0, st>>>(B.Zp, splits, nr, B.Z);
     GW_LAUNCH_CHECK();
@@ -487,6 +429,7 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
   GW_REQUIRE(n > RP, GW_EINVAL, "Kernel PCA with D=%d needs more than %d points (n=%lld)", D, RP,
              static_cast<long long>(n));
   CostParams cp{kind, param};
+  GW_TRY(lift_tc_prepare(x, n, d, kind, param, RP, B.tc, st));
   const int iters = n_iter > 0 ? n_iter : 40;
   random_block_kernel<<<ceil_div(n * RP, 256), 256, 0, st>>>(B.Q, n * RP, seed);
   GW_LAUNCH_CHECK();
@@ -521,7 +464,12 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
   GW_CUDA_TRY(cudaMemcpyAsync(B.sl, sl.data(), sizeof(float) * D, cudaMemcpyHostToDevice, st));
   right_mult_kernel<<<ceil_div(n * D, 256), 256, 0, st>>>(B.Q, n, RP, B.M, D, D, B.V);
   GW_LAUNCH_CHECK();
-  sign_fix_kernel<<<1, 256, 0, st>>>(B.V, n, D, X, sqn, B.sl);
+  sign_partial_kernel<<<kGramBlocks, 128, 0, st>>>(B.V, n, D, B.g_part, B.g_part + kGramBlocks * D);
+  GW_LAUNCH_CHECK();
+  sign_final_kernel<<<1, 128, 0, st>>>(B.V, D, kGramBlocks, B.g_part, B.g_part + kGramBlocks * D,
+                                       B.cs);
+  GW_LAUNCH_CHECK();
+  sign_apply_kernel<<<ceil_div(n * 32, 256), 256, 0, st>>>(B.V, n, D, B.cs, X, sqn, B.sl);
   GW_LAUNCH_CHECK();
   if (basis) {
     GW_CUDA_TRY(cudaMemcpyAsync(basis, B.V, sizeof(float) * n * D, cudaMemcpyDeviceToDevice, st));

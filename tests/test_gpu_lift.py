@@ -60,3 +60,20 @@ def test_kernel_pca_reproduces_cost_at_high_rank(gw):
     Dg = O.pairwise_sqdist(Xg, Xg)
     Do = O.pairwise_sqdist(ref["X"], ref["X"])
     assert np.abs(Dg - Do).max() <= 1e-3 * Do.max()
+
+
+@pytest.mark.parametrize("d,kind,param,n,D", [(2, 1, 1.0, 900, 8), (4, 1, 1.5, 800, 10),
+                                              (4, 2, 0.5, 700, 8), (1, 1, 1.0, 400, 4),
+                                              (3, 0, 2.0, 1100, 3)])
+def test_kernel_pca_point_dims_and_costs(gw, d, kind, param, n, D):
+    """Point dimensions 1-4 and every cost form of the block product (sqrt,
+    general power, Gaussian, squared distance through Kernel PCA) against the
+    oracle's dense eigendecomposition; eigenvalues as in the test above."""
+    x = r32(W.normalize_radius(W.random_features(n, d, seed=n + d)))
+    a = r32(W.uniform_weights(n))
+    kname = {0: "sqeuclid", 1: "power", 2: "gauss"}[kind]
+    out = gw.gw_lift(f32(x), D, kind=kind, param=param, want_basis=True, seed=5)
+    ref = O.lift(x, a, kname, param, D=D)
+    lam_g, lam_o = host(out["lam"]), ref["lam"]
+    assert np.all(np.abs(lam_g - lam_o) <= 2e-5 * lam_o[0]), (lam_g[:5], lam_o[:5])
+    assert np.abs(a @ host(out["X"])).max() <= 1e-5 * np.abs(host(out["X"])).max()
