@@ -24,7 +24,7 @@ __all__ = [
 ]
 
 GW_OK = 0
-PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_BF16X3, PREC_F16X3 = 0, 1, 2, 3
 PEN_SQEUCLID, PEN_POWER, PEN_GAUSS = 0, 1, 2
 OP_SOFTMIN, OP_CROSS_COV, OP_ENERGY, OP_SOLVE, OP_LIFT, OP_GRAD, OP_COARSEN, OP_ITERATION = range(8)
 EN_LEN = 16

@@ -20,6 +20,8 @@
 //      order afterwards (deterministic).
 // A wait that gives up makes the CTA write NaN rows, which the
 // orthonormalisation that follows reports as an error.
+#include <algorithm>
+
 #include "gw_tc_ops.cuh"
 
 namespace gw {
@@ -494,7 +496,17 @@ int lt_encode(CUtensorMap* map, CUtensorMapDataType type, void* ptr, int64_t inn
 template <int DIM, int KIND>
 int launch_lt(const CUtensorMap* maps, const LtTask& T, const LtLayout& L, cudaStream_t st) {
   auto kern = lift_tc_kernel<DIM, KIND>;
-  GW_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem_bytes));
+  // set once, at the largest size any RP needs: launches for different RP
+  // may run concurrently on several host threads, and a per-launch setting
+  // would let one thread lower the limit under another's launch
+  static std::once_flag once;
+  static cudaError_t attr_rc = cudaSuccess;
+  std::call_once(once, [&] {
+    int mx = 0;
+    for (int rp : {16, 32, 48, 64, 80, 96, 128}) mx = std::max(mx, lt_layout(kLtBN, rp).smem_bytes);
+    attr_rc = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  });
+  GW_CUDA_TRY(attr_rc);
   kern<<<L.row_tiles * L.splits, kLtThreads, L.smem_bytes, st>>>(maps[0], maps[1], maps[2], T);
   GW_LAUNCH_CHECK();
   return GW_OK;

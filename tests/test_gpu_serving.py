@@ -99,3 +99,22 @@ def test_admission_respects_memory_and_rejects_oversized(gw):
         assert e.value.code == 2
     finally:
         srv.close()
+
+
+def test_concurrent_lifts_of_different_widths(gw):
+    """Lifted requests with D = 16 and D = 32 run their Kernel PCA products
+    concurrently on several worker threads (different shared-memory sizes of
+    the same kernel); every one must succeed."""
+    g = W.rng(21)
+    reqs = []
+    for k in range(24):
+        n, m = (int(v) for v in np.exp(g.uniform(np.log(500), np.log(2500), 2)))
+        reqs.append(make_request(k, n, m, 1, 16 if k % 2 else 32, 0.05, seed=300 + k))
+    srv = gw.Server(pool_bytes=4 << 30, max_active=8)
+    try:
+        out = run_all(srv, reqs)
+    finally:
+        srv.close()
+    for rid, res in out.items():
+        assert res["status"] == 0, (rid, res["status"])
+        assert np.isfinite(res["energy"][0]), rid
