@@ -413,6 +413,41 @@ size_t gw_sgw_workspace_size(int64_t n, int64_t m, int D, int E, int prec, int w
                              int dx_dim);
 
 /*
+ * gw_solve_batch -- many small CNT-GW problems in one persistent launch
+ * (Algorithm 1 with the symmetric Sinkhorn loop of Algorithm 3, or
+ * Algorithm 2 when symmetric == 0; FP32 softmins on the CUDA cores, FP64
+ * cross-covariance and energy, the math of gw_solve's GW_PREC_FP32 path).
+ *   Problem q owns sources [xo[q], xo[q+1]) and targets [yo[q], yo[q+1]) of
+ *   packed arrays: X ((sum n) x D), s, a, f per source; Y ((sum m) x E),
+ *   t, b, g per target.  xo, yo: nprob + 1 non-decreasing int64 offsets
+ *   (device).  eps0[q] > 0 (device); eps1 NULL (constant eps) or eps1[q] > 0,
+ *   the geometric schedule of gw_solve's eps_final.  Every problem starts
+ *   from f = g = 0, Gamma = 0 and runs n_outer x n_inner iterations.
+ *   Outputs (device): f, g (packed like s, t), Gamma and Gamma_plan
+ *   (nprob x D x E float64: the last update and the Gamma of the last plan,
+ *   as gw_result), energy (nprob x GW_EN_LEN: the record of the last plan),
+ *   history (NULL, or nprob x n_outer x GW_EN_LEN: every outer step).
+ *   A device work queue hands problems to CTAs; each problem is solved by one
+ *   CTA entirely in shared memory, so results do not depend on the batch
+ *   (bitwise).  Sizes: 1 <= D, E <= 4; n_max, m_max (host) bound every
+ *   problem's n and m and size the shared memory, which must hold
+ *   (n_max + m_max) (D + 7) floats plus padding (about 7000 points in all at
+ *   D = 2); a problem outside the bounds (or with n or m = 0) gets
+ *   GW_EINVAL in its record's GW_EN_STATUS and untouched outputs.
+ * Workspace: gw_solve_batch_workspace_size() bytes (the queue counter).
+ * Errors: GW_EINVAL (nprob < 1, n_outer / n_inner < 1, a null pointer),
+ *   GW_EUNSUPPORTED (D or E outside 1..4, sizes that do not fit), GW_ENOMEM,
+ *   GW_ECUDA.
+ */
+int gw_solve_batch(int nprob, const int64_t* xo, const int64_t* yo, int64_t n_max, int64_t m_max,
+                   int D, int E, const float* X, const float* Y, const float* s, const float* t,
+                   const float* a, const float* b, const float* eps0, const float* eps1,
+                   int n_outer, int n_inner, int symmetric, float* f, float* g, double* Gamma,
+                   double* Gamma_plan, double* energy, double* history, void* ws,
+                   size_t ws_bytes, gw_stream_t stream);
+size_t gw_solve_batch_workspace_size(void);
+
+/*
  * Request server (continuous batching; no counterpart in the paper, which
  * solves one problem at a time).  Requests are admitted in arrival order as
  * soon as a worker slot is free and their device memory fits in the pool the

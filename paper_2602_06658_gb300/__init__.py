@@ -107,6 +107,11 @@ lib.gw_sgw_workspace_size.argtypes = [_i64, _i64, _int, _int, _int, _int, _int]
 lib.gw_sgw_workspace_size.restype = _sz
 lib.gw_multiscale_workspace_size.argtypes = [_i64, _i64, _int, _int, _i64, _i64, _int]
 lib.gw_multiscale_workspace_size.restype = _sz
+lib.gw_solve_batch.argtypes = [_int, _p, _p, _i64, _i64, _int, _int, _p, _p, _p, _p, _p, _p, _p,
+                               _p, _int, _int, _int, _p, _p, _p, _p, _p, _p, _p, _sz, _p]
+lib.gw_solve_batch.restype = _int
+lib.gw_solve_batch_workspace_size.argtypes = []
+lib.gw_solve_batch_workspace_size.restype = _sz
 class GwRequest(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("n", _i64), ("m", _i64), ("d", _int), ("kind", _int),
                 ("param", _f), ("D", _int), ("eps", _f), ("eps_final", _f), ("n_outer", _int),
@@ -462,6 +467,70 @@ def gw_sgw(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=Tru
                       _ptr(out["dX"]), _ptr(_f32(x, "x")) if grad else None, dxd, int(kind),
                       float(param), _ptr(_f32(basis, "basis")), _ptr(_f32(eigvals, "eigvals")),
                       _ptr(out["dx"]), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def pack_problems(problems, device=None):
+    """Packs a list of problems, each dict(X, Y, s, t, a, b) of host or device
+    arrays, into the layout of gw_solve_batch: concatenated float32 device
+    tensors and int64 offsets xo, yo (nprob + 1).  Returns a dict with those
+    and n_max, m_max."""
+    import numpy as np
+    dev = device or "cuda"
+
+    def dev32(v):
+        v = v if torch.is_tensor(v) else torch.as_tensor(np.asarray(v, np.float32))
+        return v.to(device=dev, dtype=torch.float32)
+
+    cat = {k: torch.cat([dev32(p[k]) for p in problems]).contiguous()
+           for k in ("X", "Y", "s", "t", "a", "b")}
+    ns = [len(p["s"]) for p in problems]
+    ms = [len(p["t"]) for p in problems]
+    cat["xo"] = torch.tensor([0] + list(np.cumsum(ns)), dtype=torch.int64, device=dev)
+    cat["yo"] = torch.tensor([0] + list(np.cumsum(ms)), dtype=torch.int64, device=dev)
+    cat["n_max"], cat["m_max"] = max(ns), max(ms)
+    return cat
+
+
+def gw_solve_batch(packed, eps, n_outer, n_inner, eps_final=None, symmetric=True, record=False,
+                   ws=None, stream=None):
+    """Persistent batched solver (gw.h: gw_solve_batch) over the problems of
+    pack_problems().  eps, eps_final: one value per problem (float tensors or
+    sequences) or a scalar for all.  Returns dict(f, g packed like s, t;
+    Gamma, Gamma_plan (nprob, D, E) float64; energy (nprob, GW_EN_LEN);
+    history (nprob, n_outer, GW_EN_LEN) when record)."""
+    X, Y = packed["X"], packed["Y"]
+    dev = X.device
+    nprob = packed["xo"].numel() - 1
+    D, E = X.shape[1], Y.shape[1]
+
+    def per_problem(v):
+        if v is None:
+            return None
+        if torch.is_tensor(v) and v.numel() == nprob:
+            return v.to(device=dev, dtype=torch.float32).contiguous()
+        if not torch.is_tensor(v) and hasattr(v, "__len__"):
+            return torch.tensor([float(e) for e in v], dtype=torch.float32, device=dev)
+        return torch.full((nprob,), float(v), dtype=torch.float32, device=dev)
+
+    e0, e1 = per_problem(eps), per_problem(eps_final)
+    out = {"f": torch.empty(packed["s"].numel(), dtype=torch.float32, device=dev),
+           "g": torch.empty(packed["t"].numel(), dtype=torch.float32, device=dev),
+           "Gamma": torch.empty(nprob, D, E, dtype=torch.float64, device=dev),
+           "Gamma_plan": torch.empty(nprob, D, E, dtype=torch.float64, device=dev),
+           "energy": torch.zeros(nprob, 16, dtype=torch.float64, device=dev),
+           "history": torch.zeros(nprob, int(n_outer), 16, dtype=torch.float64, device=dev)
+           if record else None}
+    if ws is None:
+        ws = workspace(lib.gw_solve_batch_workspace_size(), dev)
+    _check(lib.gw_solve_batch(nprob, _ptr(packed["xo"]), _ptr(packed["yo"]), int(packed["n_max"]),
+                              int(packed["m_max"]), D, E, _ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")),
+                              _ptr(_f32(packed["s"], "s")), _ptr(_f32(packed["t"], "t")),
+                              _ptr(_f32(packed["a"], "a")), _ptr(_f32(packed["b"], "b")),
+                              _ptr(e0), _ptr(e1), int(n_outer), int(n_inner), int(bool(symmetric)),
+                              _ptr(out["f"]), _ptr(out["g"]), _ptr(out["Gamma"]),
+                              _ptr(out["Gamma_plan"]), _ptr(out["energy"]), _ptr(out["history"]),
+                              _ptr(ws), ws.numel(), _stream(stream)))
     return out
 
 

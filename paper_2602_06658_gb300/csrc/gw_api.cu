@@ -666,6 +666,41 @@ int gw_sgw(const gw_problem* p, const gw_options* o, double* sgw, double* record
                  dx, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
+size_t gw_solve_batch_workspace_size(void) { return batch_ws_bytes(); }
+
+int gw_solve_batch(int nprob, const int64_t* xo, const int64_t* yo, int64_t n_max, int64_t m_max,
+                   int D, int E, const float* X, const float* Y, const float* s, const float* t,
+                   const float* a, const float* b, const float* eps0, const float* eps1,
+                   int n_outer, int n_inner, int symmetric, float* f, float* g, double* Gamma,
+                   double* Gamma_plan, double* energy, double* history, void* ws,
+                   size_t ws_bytes, gw_stream_t stream) {
+  gw::set_error("");
+  GW_REQUIRE(nprob >= 1, GW_EINVAL, "nprob must be >= 1 (got %d)", nprob);
+  NONNULL(xo);
+  NONNULL(yo);
+  NONNULL(X);
+  NONNULL(Y);
+  NONNULL(s);
+  NONNULL(t);
+  NONNULL(a);
+  NONNULL(b);
+  NONNULL(eps0);
+  NONNULL(f);
+  NONNULL(g);
+  NONNULL(Gamma);
+  NONNULL(Gamma_plan);
+  NONNULL(energy);
+  GW_REQUIRE(D >= 1 && D <= 4 && E >= 1 && E <= 4, GW_EUNSUPPORTED,
+             "the batched solver takes feature widths 1..4 (got D=%d, E=%d)", D, E);
+  GW_REQUIRE(n_max >= 1 && m_max >= 1 && n_max <= (1 << 20) && m_max <= (1 << 20), GW_EINVAL,
+             "n_max, m_max must be in 1..2^20");
+  GW_REQUIRE(n_outer >= 1 && n_inner >= 1, GW_EINVAL, "n_outer, n_inner must be >= 1");
+  GW_REQUIRE(n_outer <= 100000 && n_inner <= 1000000, GW_EINVAL, "iteration counts too large");
+  return run_solve_batch(nprob, xo, yo, n_max, m_max, D, E, X, Y, s, t, a, b, eps0, eps1, n_outer,
+                         n_inner, symmetric != 0 ? 1 : 0, f, g, Gamma, Gamma_plan, energy, history,
+                         ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
 size_t gw_multiscale_workspace_size(int64_t n, int64_t m, int D, int E, int64_t kx, int64_t ky,
                                     int prec) {
   if (n < 1 || m < 1 || kx < 1 || ky < 1 || D < 1 || E < 1) return 0;

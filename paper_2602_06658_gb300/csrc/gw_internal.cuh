@@ -200,6 +200,15 @@ size_t energy_ws_bytes(int64_t n, int64_t m, int D, int E, int prec);
 int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* logb_pre,
                double* energy, double* Gamma_out, Carver& ws, cudaStream_t st);
 
+// Persistent batched solver (gw_batch.cu); arguments as gw_solve_batch.
+size_t batch_ws_bytes();
+int run_solve_batch(int nprob, const int64_t* xo, const int64_t* yo, int64_t n_max, int64_t m_max,
+                    int D, int E, const float* X, const float* Y, const float* s, const float* t,
+                    const float* a, const float* b, const float* eps0, const float* eps1,
+                    int n_outer, int n_inner, int symmetric, float* f, float* g, double* Gamma,
+                    double* Gamma_plan, double* energy, double* history, void* ws,
+                    size_t ws_bytes, cudaStream_t st);
+
 // Kernel PCA / centering lift (gw_lift.cu); synchronous.
 size_t lift_ws_bytes(int64_t n, int D);
 // Its N x N block product Z = C P on the tensor cores (gw_lift_tc.cu):

@@ -1,0 +1,153 @@
+"""gw_solve_batch (the persistent batched solver) against the FP64 oracle and
+against gw_solve's FP32 path on the same inputs.
+
+Tolerances: vs the oracle as tests/test_gpu_solve.py (max relative error 1e-4
+on the energy, 1e-3 on the marginals); vs gw_solve (the same FP32 arithmetic
+with another summation order: the per-split column merges of the streaming
+softmin against one chain per row here) 1e-5 relative on the energy and
+1e-4 relative on the potentials and Gamma.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import f32, host
+
+pytestmark = pytest.mark.gpu
+
+r32 = lambda x: np.asarray(x, np.float32).astype(np.float64)
+
+
+def config1(n=1000, seed=0):
+    w = W.square_rotated(n, seed)
+    a, b = r32(w["a"]), r32(w["b"])
+    X, Y = r32(O.center(w["x"], a)), r32(O.center(w["y"], b))
+    return dict(X=X, Y=Y, s=r32((X * X).sum(1)), t=r32((Y * Y).sum(1)), a=a, b=b,
+                eps=float(np.float32(w["eps"])))
+
+
+def random_problem(n, m, D, E, seed, scale=0.3):
+    g = W.rng(seed)
+    a = r32(W.random_weights(n, seed + 1, spread=0.5))
+    b = r32(W.random_weights(m, seed + 2, spread=0.5))
+    X = g.standard_normal((n, D)) * scale
+    Y = g.standard_normal((m, E)) * scale
+    X, Y = r32(X - a @ X), r32(Y - b @ Y)
+    return dict(X=X, Y=Y, s=r32((X * X).sum(1)), t=r32((Y * Y).sum(1)), a=a, b=b)
+
+
+def solve_alone(gw, P, eps, n_outer, n_inner, eps_final=0.0, symmetric=True):
+    return gw.gw_solve(f32(P["X"]), f32(P["Y"]), f32(P["s"]), f32(P["t"]), f32(P["a"]),
+                       f32(P["b"]), eps, n_outer, n_inner, eps_final=eps_final,
+                       symmetric=symmetric, prec=0, record=True)
+
+
+def split(packed, v, side):
+    off = host(packed["xo" if side == "x" else "yo"]).astype(np.int64)
+    v = host(v)
+    return [v[off[q]:off[q + 1]] for q in range(len(off) - 1)]
+
+
+@pytest.fixture(scope="module")
+def cfg1_oracle():
+    P = config1()
+    res = O.cnt_gw(P["a"], P["b"], P["X"], P["Y"], P["eps"], 20, 50, symmetric=True)
+    return P, res
+
+
+def test_config1_batch_matches_oracle(gw, cfg1_oracle):
+    """Config 1 (2D, N = M = 1000, 20 x 50, Algorithm 3) as problem 0 of a
+    batch of four seeds: energy per outer step, marginal errors and the
+    singular values of Gamma against the FP64 oracle."""
+    P, res = cfg1_oracle
+    probs = [P] + [config1(seed=k) for k in (1, 2, 3)]
+    packed = gw.pack_problems(probs)
+    out = gw.gw_solve_batch(packed, [p["eps"] for p in probs], 20, 50, record=True)
+    en = host(out["energy"])
+    assert np.all(en[:, gw.EN["status"]] == 0)
+    last = res["history"][-1]
+    assert abs(en[0, gw.EN["E"]] - last["E"]) <= 1e-4 * abs(last["E"])
+    hist = host(out["history"])[0]
+    E_or = np.array([h["E"] for h in res["history"]])
+    assert np.all(np.abs(hist[:, gw.EN["E"]] - E_or) <= 1e-4 * np.abs(E_or))
+    assert abs(en[0, gw.EN["row_l1"]] - np.abs(last["row"] - P["a"]).sum()) <= 1e-3
+    assert abs(en[0, gw.EN["col_l1"]] - np.abs(last["col"] - P["b"]).sum()) <= 1e-3
+    sv_g = np.linalg.svd(host(out["Gamma"])[0], compute_uv=False)
+    sv_o = np.linalg.svd(res["Gamma"], compute_uv=False)
+    assert np.allclose(sv_g, sv_o, rtol=1e-3)
+
+
+def test_ragged_batch_matches_gw_solve(gw):
+    """Ragged sizes (1 to 1777 points, tails off the 8-column chunks) and a
+    per-problem annealed eps: every problem as gw_solve solves it alone."""
+    sizes = [(37, 52), (300, 211), (1000, 1000), (611, 1777), (5, 9), (1, 3), (2, 1)]
+    probs = [random_problem(n, m, 3, 3, seed=10 * k) for k, (n, m) in enumerate(sizes)]
+    eps0 = [0.2, 0.05, 0.03, 0.1, 0.3, 0.5, 0.08]
+    eps1 = [e / 4 for e in eps0]
+    packed = gw.pack_problems(probs)
+    out = gw.gw_solve_batch(packed, eps0, 4, 30, eps_final=eps1, record=True)
+    hist, fs, gs = host(out["history"]), split(packed, out["f"], "x"), split(packed, out["g"], "y")
+    G = host(out["Gamma"])
+    for q, P in enumerate(probs):
+        ref = solve_alone(gw, P, eps0[q], 4, 30, eps_final=eps1[q])
+        rh = host(ref["history"])
+        assert np.all(hist[q, :, gw.EN["status"]] == 0), q
+        assert np.allclose(hist[q, :, gw.EN["eps"]], rh[:, gw.EN["eps"]], rtol=1e-7), q
+        assert np.all(np.abs(hist[q, :, gw.EN["E"]] - rh[:, gw.EN["E"]])
+                      <= 1e-5 * np.abs(rh[:, gw.EN["E"]]) + 1e-9), (q, hist[q, :, 0], rh[:, 0])
+        fr, gr = host(ref["f"]), host(ref["g"])
+        assert np.abs(fs[q] - fr).max() <= 1e-4 * (np.abs(fr).max() + 1e-3), q
+        assert np.abs(gs[q] - gr).max() <= 1e-4 * (np.abs(gr).max() + 1e-3), q
+        Gr = host(ref["Gamma"])
+        assert np.abs(G[q] - Gr).max() <= 1e-4 * (np.abs(Gr).max() + 1e-6), q
+
+
+@pytest.mark.parametrize("symmetric,D,E", [(False, 2, 2), (True, 4, 3), (False, 3, 1),
+                                           (True, 1, 4)])
+def test_batch_variants_match_gw_solve(gw, symmetric, D, E):
+    """Algorithm 2 as well as 3, and feature widths 1-4 on either side."""
+    sizes = [(200, 150), (333, 400), (64, 64)]
+    probs = [random_problem(n, m, D, E, seed=7 + k) for k, (n, m) in enumerate(sizes)]
+    packed = gw.pack_problems(probs)
+    out = gw.gw_solve_batch(packed, 0.05, 3, 25, symmetric=symmetric, record=True)
+    hist = host(out["history"])
+    for q, P in enumerate(probs):
+        rh = host(solve_alone(gw, P, 0.05, 3, 25, symmetric=symmetric)["history"])
+        assert np.all(np.abs(hist[q, :, gw.EN["E"]] - rh[:, gw.EN["E"]])
+                      <= 1e-5 * np.abs(rh[:, gw.EN["E"]]) + 1e-9), (q, hist[q, :, 0], rh[:, 0])
+        for key in ("row_l1", "col_l1", "mass", "Gamma2"):
+            k = gw.EN[key]
+            assert np.all(np.abs(hist[q, :, k] - rh[:, k]) <= 1e-4 * np.abs(rh[:, k]) + 1e-6), (q, key)
+
+
+def test_result_does_not_depend_on_the_batch(gw):
+    """One CTA per problem, fixed-order reductions: a problem's outputs are
+    bitwise the same alone and among others (of other sizes)."""
+    P = random_problem(777, 555, 3, 3, seed=99)
+    others = [random_problem(n, m, 3, 3, seed=200 + n) for n, m in [(100, 90), (1500, 1200), (8, 8)]]
+    alone = gw.gw_solve_batch(gw.pack_problems([P]), 0.04, 3, 20)
+    mixed_p = gw.pack_problems(others[:2] + [P] + others[2:])
+    mixed = gw.gw_solve_batch(mixed_p, 0.04, 3, 20)
+    assert np.array_equal(host(alone["energy"])[0], host(mixed["energy"])[2])
+    assert np.array_equal(host(alone["f"]), split(mixed_p, mixed["f"], "x")[2])
+    assert np.array_equal(host(alone["g"]), split(mixed_p, mixed["g"], "y")[2])
+    assert np.array_equal(host(alone["Gamma"])[0], host(mixed["Gamma"])[2])
+
+
+def test_batch_rejects_what_it_cannot_hold(gw):
+    probs = [random_problem(300, 200, 2, 2, seed=1), random_problem(90, 80, 2, 2, seed=2)]
+    packed = gw.pack_problems(probs)
+    # a problem larger than the stated bound is skipped with GW_EINVAL in its record
+    out = gw.gw_solve_batch(dict(packed, n_max=100), 0.05, 2, 10)
+    en = host(out["energy"])
+    assert en[0, gw.EN["status"]] == 1 and en[1, gw.EN["status"]] == 0
+    # sizes whose shared memory does not fit, and feature widths above 4
+    with pytest.raises(gw.GWError) as e:
+        gw.gw_solve_batch(dict(packed, n_max=40000, m_max=40000), 0.05, 2, 10)
+    assert e.value.code == 6
+    wide = gw.pack_problems([random_problem(50, 40, 5, 2, seed=3)])
+    with pytest.raises(gw.GWError) as e:
+        gw.gw_solve_batch(wide, 0.05, 2, 10)
+    assert e.value.code == 6
