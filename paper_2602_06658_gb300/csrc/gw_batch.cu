@@ -84,16 +84,78 @@ __device__ void block_reduce(double* v, int cnt, unsigned is_max, double* red, d
   __syncthreads();
 }
 
+__device__ __forceinline__ uint64_t b_pack2(float lo, float hi) {
+  uint64_t p;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(lo), "f"(hi));
+  return p;
+}
+__device__ __forceinline__ void b_unpack2(uint64_t p, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+__device__ __forceinline__ uint64_t b_add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Exponent of one cell in base 2, minus `shift`, as a chain of FMAs that
+// starts from the other side's bias:
+//   bias_l - shift + beta sq_k sq_l + alpha <F_k, F_l>.
+template <int DP>
+__device__ __forceinline__ float cell(const float (&a)[DP], float u, float nshift, float4 o,
+                                      float4 o2) {
+  float z = fmaf(u, o.y, o.x + nshift);
+  z = fmaf(a[0], o.z, z);
+  z = fmaf(a[1], o.w, z);
+  if constexpr (DP == 4) {
+    z = fmaf(a[2], o2.x, z);
+    z = fmaf(a[3], o2.y, z);
+  }
+  return z;
+}
+
+// Exact base-2 log-sum-exp of one own entry with a running max (updated per
+// chunk of 8), for the entries whose shifted sum left the safe range.
+template <int DP>
+__device__ float lse2_exact(const float (&a)[DP], float u, const float4* oth0, const float4* oth1,
+                            int n_oth_pad) {
+  float M = kNegBig, S = 0.0f;
+  for (int l0 = 0; l0 < n_oth_pad; l0 += kBChunk) {
+    float z[kBChunk];
+#pragma unroll
+    for (int c = 0; c < kBChunk; ++c)
+      z[c] = cell<DP>(a, u, 0.0f, oth0[l0 + c], DP == 4 ? oth1[l0 + c] : make_float4(0, 0, 0, 0));
+    float cm = z[0];
+#pragma unroll
+    for (int c = 1; c < kBChunk; ++c) cm = fmaxf(cm, z[c]);
+    if (cm > M) {
+      S *= ex2(M - cm);
+      M = cm;
+    }
+    float tsum = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kBChunk; ++c) tsum += ex2(z[c] - M);
+    S += tsum;
+  }
+  return M + log2f(S);
+}
+
 // One log-sum-exp half-step for the entries of one side ("own": rows for the
 // row softmin, columns for the column one) against the packed entries of
 // the other side:
 //   out_k = -eps ln2 LSE2_l [bias_l + beta sq_k sq_l + alpha <F_k, F_l>],
 // averaged with avg_k when avg is not null (Algorithm 3).  Two own entries
-// per thread share every broadcast load of the other side.
+// per thread share every broadcast load of the other side.  The sum runs
+// against a known shift instead of a running max: the own side's current
+// potential est_k, whose softmin is close to est_k, gives LSE2 ~ -est_k hs,
+// so sum_l 2^(z_kl + est_k hs) stays near 1 and needs neither a max nor a
+// subtraction per cell (the two entries' terms are added as one FP32x2
+// pair).  An entry whose sum lands outside [2^-20, 2^100] (the estimate far
+// off: overflow, or most of the mass below the FP32 range) is redone exactly.
 template <int DP>
 __device__ void lse_side(const float4* own0, const float4* own1, int n_own, const float4* oth0,
                          const float4* oth1, int n_oth_pad, float alpha, float beta, float eps,
-                         const float* avg, float* out) {
+                         float hs, const float* est, const float* avg, float* out) {
   for (int k0 = threadIdx.x; k0 < n_own; k0 += 2 * kBt) {
     const int k1 = k0 + kBt;
     const bool has1 = k1 < n_own;
@@ -113,56 +175,29 @@ __device__ void lse_side(const float4* own0, const float4* own1, int n_own, cons
       a1[3] = q1.y * alpha;
     }
     const float u0 = p0.y * beta, u1 = p1.y * beta;
-    float M0 = kNegBig, S0 = 0.0f, M1 = kNegBig, S1 = 0.0f;
+    const float ns0 = est[k0] * hs, ns1 = has1 ? est[k1] * hs : 0.0f;   // -shift
+    uint64_t S01 = b_pack2(0.0f, 0.0f);
     for (int l0 = 0; l0 < n_oth_pad; l0 += kBChunk) {
-      float z0[kBChunk], z1[kBChunk];
 #pragma unroll
       for (int c = 0; c < kBChunk; ++c) {
         const float4 o = oth0[l0 + c];
-        float acc0 = fmaf(u0, o.y, o.x);
-        float acc1 = fmaf(u1, o.y, o.x);
-        acc0 = fmaf(a0[0], o.z, acc0);
-        acc1 = fmaf(a1[0], o.z, acc1);
-        acc0 = fmaf(a0[1], o.w, acc0);
-        acc1 = fmaf(a1[1], o.w, acc1);
-        if constexpr (DP == 4) {
-          const float4 o2 = oth1[l0 + c];
-          acc0 = fmaf(a0[2], o2.x, acc0);
-          acc1 = fmaf(a1[2], o2.x, acc1);
-          acc0 = fmaf(a0[3], o2.y, acc0);
-          acc1 = fmaf(a1[3], o2.y, acc1);
-        }
-        z0[c] = acc0;
-        z1[c] = acc1;
+        const float4 o2 = DP == 4 ? oth1[l0 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float z0 = cell<DP>(a0, u0, ns0, o, o2);
+        const float z1 = cell<DP>(a1, u1, ns1, o, o2);
+        S01 = b_add2(S01, b_pack2(ex2(z0), ex2(z1)));
       }
-      float c0 = z0[0], c1 = z1[0];
-#pragma unroll
-      for (int c = 1; c < kBChunk; ++c) {
-        c0 = fmaxf(c0, z0[c]);
-        c1 = fmaxf(c1, z1[c]);
-      }
-      if (c0 > M0) {
-        S0 *= ex2(M0 - c0);
-        M0 = c0;
-      }
-      if (c1 > M1) {
-        S1 *= ex2(M1 - c1);
-        M1 = c1;
-      }
-      float t0 = 0.0f, t1 = 0.0f;
-#pragma unroll
-      for (int c = 0; c < kBChunk; ++c) {
-        t0 += ex2(z0[c] - M0);
-        t1 += ex2(z1[c] - M1);
-      }
-      S0 += t0;
-      S1 += t1;
     }
-    float v0 = -eps * kLn2 * (M0 + log2f(S0));
+    float S0, S1;
+    b_unpack2(S01, S0, S1);
+    float l0v = S0 >= 9.5367431640625e-07f && S0 <= 1.2676506e30f ? log2f(S0) - ns0
+                                                                 : lse2_exact<DP>(a0, u0, oth0, oth1, n_oth_pad);
+    float v0 = -eps * kLn2 * l0v;
     if (avg) v0 = 0.5f * (avg[k0] + v0);
     out[k0] = v0;
     if (has1) {
-      float v1 = -eps * kLn2 * (M1 + log2f(S1));
+      float l1v = S1 >= 9.5367431640625e-07f && S1 <= 1.2676506e30f ? log2f(S1) - ns1
+                                                                   : lse2_exact<DP>(a1, u1, oth0, oth1, n_oth_pad);
+      float v1 = -eps * kLn2 * l1v;
       if (avg) v1 = 0.5f * (avg[k1] + v1);
       out[k1] = v1;
     }
@@ -283,8 +318,8 @@ __device__ void solve_one(const BatchArgs& A, int q, int64_t x0, int64_t y0, int
         for (int i = tid; i < n; i += kBt) rp0[i].x = f[i] * hs + la[i] * kLog2e;
         for (int j = tid; j < m; j += kBt) cp0[j].x = g[j] * hs + lb[j] * kLog2e;
         __syncthreads();
-        lse_side<DP>(rp0, rp1, n, cp0, cp1, mpad, alpha, beta, eps, f, fbuf + (fc ^ 1) * NP);
-        lse_side<DP>(cp0, cp1, m, rp0, rp1, npad, alpha, beta, eps, g, gbuf + (gc ^ 1) * MP);
+        lse_side<DP>(rp0, rp1, n, cp0, cp1, mpad, alpha, beta, eps, hs, f, f, fbuf + (fc ^ 1) * NP);
+        lse_side<DP>(cp0, cp1, m, rp0, rp1, npad, alpha, beta, eps, hs, g, g, gbuf + (gc ^ 1) * MP);
         __syncthreads();
         fc ^= 1;
         gc ^= 1;
@@ -292,13 +327,13 @@ __device__ void solve_one(const BatchArgs& A, int q, int64_t x0, int64_t y0, int
         // Algorithm 2: f from g^n, then g from f^{n+1}
         for (int j = tid; j < m; j += kBt) cp0[j].x = g[j] * hs + lb[j] * kLog2e;
         __syncthreads();
-        lse_side<DP>(rp0, rp1, n, cp0, cp1, mpad, alpha, beta, eps, nullptr, fbuf + (fc ^ 1) * NP);
+        lse_side<DP>(rp0, rp1, n, cp0, cp1, mpad, alpha, beta, eps, hs, f, nullptr, fbuf + (fc ^ 1) * NP);
         __syncthreads();
         fc ^= 1;
         f = fbuf + fc * NP;
         for (int i = tid; i < n; i += kBt) rp0[i].x = f[i] * hs + la[i] * kLog2e;
         __syncthreads();
-        lse_side<DP>(cp0, cp1, m, rp0, rp1, npad, alpha, beta, eps, nullptr, gbuf + (gc ^ 1) * MP);
+        lse_side<DP>(cp0, cp1, m, rp0, rp1, npad, alpha, beta, eps, hs, g, nullptr, gbuf + (gc ^ 1) * MP);
         __syncthreads();
         gc ^= 1;
       }
@@ -375,7 +410,7 @@ __device__ void solve_one(const BatchArgs& A, int q, int64_t x0, int64_t y0, int
       for (int j = tid; j < m; j += kBt) cp0[j].x = g[j] * hs + lb[j] * kLog2e;
       __syncthreads();
       float* fhat = fbuf + (fc ^ 1) * NP;
-      lse_side<DP>(rp0, rp1, n, cp0, cp1, mpad, alpha, beta, eps, nullptr, fhat);
+      lse_side<DP>(rp0, rp1, n, cp0, cp1, mpad, alpha, beta, eps, hs, f, nullptr, fhat);
       __syncthreads();
       double w3[kBRed];
       for (int k = 0; k < kBRed; ++k) w3[k] = 0.0;
