@@ -352,8 +352,7 @@ int weighted_colsum(const float* Q, const float* w, double wu, int64_t n, int RP
 }
 
 // Z = K~ Q = -1/2 (I - 1 w^T) C (I - w 1^T) Q
-int apply_kernel(const float* x, int64_t n, int d, const float* w, CostParams cp, LiftBufs& B,
-                 cudaStream_t st) {
+int apply_kernel(int64_t n, int d, const float* w, CostParams cp, LiftBufs& B, cudaStream_t st) {
   const int RP = B.RP;
   const int64_t nr = n * RP;
   const float wu = 1.0f / static_cast<float>(n);
@@ -434,11 +433,11 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
   random_block_kernel<<<ceil_div(n * RP, 256), 256, 0, st>>>(B.Q, n * RP, seed);
   GW_LAUNCH_CHECK();
   for (int it = 0; it < iters; ++it) {
-    GW_TRY(apply_kernel(x, n, d, w, cp, B, st));
+    GW_TRY(apply_kernel(n, d, w, cp, B, st));
     GW_TRY(orthonormalize(n, B, st));
   }
   // Rayleigh-Ritz: T = Q^T K~ Q, eigenpairs of T, V = Q U_{1:D}
-  GW_TRY(apply_kernel(x, n, d, w, cp, B, st));
+  GW_TRY(apply_kernel(n, d, w, cp, B, st));
   std::vector<double> T;
   GW_TRY(gram(B.Q, B.Z, n, RP, B, T, st));
   for (int i = 0; i < RP; ++i)

@@ -95,11 +95,6 @@ LtLayout lt_layout(int64_t n, int RP) {
   return L;
 }
 
-__device__ __forceinline__ float lt_sqrt(float x) {
-  float y;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 __device__ __forceinline__ float lt_rsqrt(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -112,10 +107,10 @@ __device__ __forceinline__ float lt_lg2(float x) {
 }
 
 // C' from the scaled squared distance (the scale is in the coordinates for
-// the power costs and in the 2^14 factor for the Gaussian one)
+// the power costs and in the 2^14 factor for the Gaussian one); the power
+// p = 1 is taken in the kernel as d2 rsqrt(d2), two entries at a time
 template <int KIND>
 __device__ __forceinline__ float lt_cost(float d2, float gk) {
-  if (KIND == kLtSqrt) return lt_sqrt(d2);
   if (KIND == kLtGauss) return fmaf(-kLtCMax, ex2(-d2 * gk), kLtCMax);
   if (gk == 1.0f) return d2;
   return d2 > 0.0f ? ex2(gk * lt_lg2(d2)) : 0.0f;
