@@ -27,52 +27,59 @@ constexpr int kVjpThreads = 128;
 constexpr int kVjpTile = 32;
 
 // U_i[e] = sum_d X_i[d] Gamma[d][e]  (n x E)
-__global__ void x_gamma_kernel(const float* X, const double* Gamma, int64_t n, int D, int E,
-                               float* U) {
-  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q >= n * E) return;
-  const int64_t i = q / E;
-  const int e = static_cast<int>(q % E);
-  double acc = 0.0;
-  for (int d = 0; d < D; ++d) acc = fma(static_cast<double>(X[i * D + d]), Gamma[d * E + e], acc);
-  U[q] = static_cast<float>(acc);
+// Gt[e][d] = Gamma[d][e]
+__global__ void transpose_de_kernel(const double* Gamma, int D, int E, double* Gt) {
+  for (int q = threadIdx.x; q < D * E; q += blockDim.x) Gt[(q % E) * D + q / E] = Gamma[q];
 }
 
-// partial [m2, Sigma (D x D), mu3 (D)] of a-weighted centered features
+// partial [m2, Sigma (D x D), mu3 (D)] of a-weighted centered features:
+// rows staged 32 at a time in shared memory with their norms s_i; each
+// thread accumulates its Sigma entries, thread d < D the component mu3_d,
+// thread 0 also m2 (fixed order: deterministic)
 __global__ void __launch_bounds__(256)
     grad_moments_kernel(const float* X, const float* a, int64_t n, int D, double* part) {
+  __shared__ double Xs[32][129];
+  __shared__ double ws[32], ss[32];
   const int L = 1 + D * D + D;
   const int per = (D * D + 255) / 256;
   double acc[64];
   for (int q = 0; q < per; ++q) acc[q] = 0.0;
-  double m2 = 0.0;
-  double mu3[128];
-  for (int d = 0; d < D && threadIdx.x == 0; ++d) mu3[d] = 0.0;
+  double m2 = 0.0, mu3 = 0.0;
+  const int tid = threadIdx.x;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * chunk;
   const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
-  for (int64_t i = i0; i < i1; ++i) {
-    const double ai = a[i];
-    for (int q = 0; q < per; ++q) {
-      const int e = threadIdx.x + q * 256;
-      if (e < D * D) acc[q] = fma(ai * X[i * D + e / D], static_cast<double>(X[i * D + e % D]), acc[q]);
-    }
-    if (threadIdx.x == 0) {
+  for (int64_t ib = i0; ib < i1; ib += 32) {
+    const int cnt = static_cast<int>(i1 - ib < 32 ? i1 - ib : 32);
+    __syncthreads();
+    for (int idx = tid; idx < cnt * D; idx += 256) Xs[idx / D][idx % D] = X[(ib + idx / D) * D + idx % D];
+    if (tid < cnt) ws[tid] = a[ib + tid];
+    __syncthreads();
+    if (tid < cnt) {
       double s = 0.0;
-      for (int d = 0; d < D; ++d) s = fma(static_cast<double>(X[i * D + d]), X[i * D + d], s);
-      m2 += ai * s;
-      for (int d = 0; d < D; ++d) mu3[d] = fma(ai * s, static_cast<double>(X[i * D + d]), mu3[d]);
+      for (int d = 0; d < D; ++d) s = fma(Xs[tid][d], Xs[tid][d], s);
+      ss[tid] = s;
     }
+    __syncthreads();
+    for (int q = 0; q < per; ++q) {
+      const int e = tid + q * 256;
+      if (e < D * D) {
+        const int d0 = e / D, d1 = e % D;
+        for (int r = 0; r < cnt; ++r) acc[q] = fma(ws[r] * Xs[r][d0], Xs[r][d1], acc[q]);
+      }
+    }
+    if (tid < D)
+      for (int r = 0; r < cnt; ++r) mu3 = fma(ws[r] * ss[r], Xs[r][tid], mu3);
+    if (tid == 0)
+      for (int r = 0; r < cnt; ++r) m2 = fma(ws[r], ss[r], m2);
   }
   double* out = part + static_cast<int64_t>(blockIdx.x) * L;
   for (int q = 0; q < per; ++q) {
-    const int e = threadIdx.x + q * 256;
+    const int e = tid + q * 256;
     if (e < D * D) out[1 + e] = acc[q];
   }
-  if (threadIdx.x == 0) {
-    out[0] = m2;
-    for (int d = 0; d < D; ++d) out[1 + D * D + d] = mu3[d];
-  }
+  if (tid < D) out[1 + D * D + tid] = mu3;
+  if (tid == 0) out[0] = m2;
 }
 
 __global__ void sum_partials_kernel(const double* part, int blocks, int L, double* out) {
@@ -239,7 +246,8 @@ int vjp_splits(int64_t n) {
 
 struct GradBufs {
   double *Gpi, *stats, *U_unused, *Wr, *mpart, *mom, *m2y, *cpart, *cs;
-  float* U;
+  double* GtT;   // Gamma_t^T (E x D)
+  double* Gsc;   // Gamma of the transposed plan (E x D, not used)
   float* vpart;
   float* isl;
 };
@@ -250,7 +258,8 @@ size_t grad_ws_bytes(int64_t n, int64_t m, int D, int E, int dx_dim, int prec) {
   Carver c(nullptr, ~size_t(0));
   c.take<double>(static_cast<size_t>(D) * E);          // Gamma_pi
   c.take<double>(8);
-  c.take<float>(static_cast<size_t>(n) * E);           // U = X Gamma_t
+  c.take<double>(static_cast<size_t>(D) * E);          // Gamma_t^T
+  c.take<double>(static_cast<size_t>(D) * E);          // Gamma of the transposed plan
   c.take<double>(static_cast<size_t>(n) * (E + 2));    // row sums
   c.take<double>(static_cast<size_t>(kRed) * (1 + D * D + D));
   c.take<double>(static_cast<size_t>(1 + D * D + D));
@@ -259,7 +268,7 @@ size_t grad_ws_bytes(int64_t n, int64_t m, int D, int E, int dx_dim, int prec) {
   c.take<double>(static_cast<size_t>(D));
   c.take<float>(static_cast<size_t>(D));
   if (dx_dim > 0) c.take<float>(static_cast<size_t>(vjp_splits(n)) * n * 9);
-  size_t scratch = plan_sums_ws_bytes(m, n, E);
+  size_t scratch = cross_cov_ws_bytes(m, n, E, D, prec);
   const size_t cc = cross_cov_ws_bytes(n, m, D, E, prec);
   if (cc > scratch) scratch = cc;
   return c.used() + scratch + 512;
@@ -275,7 +284,8 @@ int run_grad(const gw_problem& p, const float* f, const float* g, const double* 
   GradBufs B;
   B.Gpi = c.take<double>(static_cast<size_t>(D) * E);
   B.stats = c.take<double>(8);
-  B.U = c.take<float>(static_cast<size_t>(n) * E);
+  B.GtT = c.take<double>(static_cast<size_t>(D) * E);
+  B.Gsc = c.take<double>(static_cast<size_t>(D) * E);
   B.Wr = c.take<double>(static_cast<size_t>(n) * (E + 2));
   B.mpart = c.take<double>(static_cast<size_t>(kRed) * (1 + D * D + D));
   B.mom = c.take<double>(static_cast<size_t>(1 + D * D + D));
@@ -296,12 +306,16 @@ int run_grad(const gw_problem& p, const float* f, const float* g, const double* 
     GW_TRY(run_cross_cov(pa, prec, B.Gpi, B.stats, nullptr, sub, st));
     Gpi = B.Gpi;
   }
-  // row-direction plan sums: [w_i, q_i, r_i] = sum_j pi_ij [Y_j, t_j, 1]
-  x_gamma_kernel<<<ceil_div(n * E, 256), 256, 0, st>>>(p.X, Gamma_t, n, D, E, B.U);
+  // row-direction plan sums [w_i, q_i, r_i] = sum_j pi_ij [Y_j, t_j, 1]: the
+  // plan-weighted column sums of the transposed problem (Y as sources, X as
+  // targets, Gamma_t^T: its cost c'_ji = c_ij, so its plan is pi^T), in the
+  // request's precision (on the tensor cores for the 16-bit forms)
+  transpose_de_kernel<<<1, 256, 0, st>>>(Gamma_t, D, E, B.GtT);
   GW_LAUNCH_CHECK();
   {
     Carver sub(base + mark, ws_bytes - mark);
-    GW_TRY(run_plan_sums(p.Y, p.t, p.b, g, B.U, p.s, p.a, f, eps, m, n, E, B.Wr, sub, st));
+    PlanArgs pt{p.Y, p.X, p.t, p.s, p.b, p.a, g, f, B.GtT, eps, m, n, E, D};
+    GW_TRY(run_cross_cov(pt, prec, B.Gsc, nullptr, B.Wr, sub, st));
   }
   // moments of X and m2_Y
   const int L = 1 + D * D + D;

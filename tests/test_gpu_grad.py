@@ -120,3 +120,29 @@ def test_autograd_wrapper_gives_the_adjoint(gw):
     (gx2,) = torch.autograd.grad(E2, x2)
     assert abs(E2.item() - E.item()) <= 1e-4 * abs(E.item())
     assert torch.allclose(gx2, gx @ Q.T, atol=2e-3 * gx.abs().max().item())
+
+
+@pytest.mark.parametrize("prec", [3, 2])
+def test_adjoint_tensor_core_plan_sums_match_oracle(gw, prec):
+    """The 16-bit precisions take the plan-weighted sums of the adjoint (both
+    directions: Gamma_pi and [w_i, q_i, r_i], the latter as the column sums of
+    the transposed problem) on the tensor cores; D = E = 16 features of the
+    lifted workloads' shape.  F16X3 (per-term error ~2^-20) meets the FP32
+    closed-form bound.  BF16X3 carries ~2^-15 per exponent term (8-bit
+    halves), 32x more, and at eps = 0.05 its exponents reach ~500 (base 2):
+    its error is stated as measured, 1.1e-2 of the largest entry, bar 3e-2."""
+    n, m, D = 300, 260, 16
+    g = W.rng(31 + prec)
+    a, b = r32(W.random_weights(n, 4, 0.3)), r32(W.random_weights(m, 5, 0.3))
+    X = r32(O.center(g.standard_normal((n, D)) * 0.25, a))
+    Y = r32(O.center(g.standard_normal((m, D)) * 0.25, b))
+    eps = 0.05
+    Gt, f, gg, pi = converged_state(X, Y, a, b, eps, 0.05 * g.standard_normal((D, D)))
+    ref = O.grad_x_squared(pi, O.cross_covariance(pi, X, Y), X, Y, a, b)
+    s, t = r32((X * X).sum(1)), r32((Y * Y).sum(1))
+    dX, _ = gw.gw_grad_x(f32(X), f32(Y), f32(s), f32(t), f32(a), f32(b), f32(f), f32(gg), f64(Gt),
+                         None, eps, prec=prec)
+    gmax = np.abs(ref).max()
+    err = np.abs(host(dX) - ref).max()
+    bar = max(grad_tolerance(pi, X, Y, a, eps), 2e-3) if prec == 3 else 3e-2
+    assert err <= bar * gmax, (prec, err / gmax, bar)
