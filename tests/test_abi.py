@@ -62,3 +62,30 @@ def test_host_side_queries_without_gpu():
     rc = lib.gw_sinkhorn_softmin(None, None, None, None, None, None, 1.0, 4, 4, 200, 0, None, None,
                                  None, 0, None)
     assert rc == 6  # GW_EUNSUPPORTED: K > 128
+
+
+def test_batched_solver_validates_on_the_host():
+    """gw_solve_batch refuses bad arguments before any CUDA call (dummy
+    pointers are never dereferenced)."""
+    lib = ctypes.CDLL(builder().build())
+    p, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.gw_solve_batch.restype = i32
+    lib.gw_solve_batch.argtypes = [i32, p, p, i64, i64, i32, i32, p, p, p, p, p, p, p, p, i32, i32,
+                                   i32, p, p, p, p, p, p, p, ctypes.c_size_t, p]
+    lib.gw_solve_batch_workspace_size.restype = ctypes.c_size_t
+    lib.gw_last_error.restype = ctypes.c_char_p
+    d = p(0x1000)
+
+    def call(nprob=2, n_max=100, m_max=100, D=2, E=2, n_outer=2, n_inner=3, X=d, ws_bytes=4096):
+        return lib.gw_solve_batch(nprob, d, d, n_max, m_max, D, E, X, d, d, d, d, d, d, None,
+                                  n_outer, n_inner, 1, d, d, d, d, d, None, d, ws_bytes, None)
+
+    assert lib.gw_solve_batch_workspace_size() >= 4
+    assert call(nprob=0) == 1                      # GW_EINVAL: empty batch
+    assert call(X=None) == 1 and b"X" in lib.gw_last_error()
+    assert call(n_inner=0) == 1
+    assert call(D=5) == 6                          # GW_EUNSUPPORTED: feature width above 4
+    assert call(E=0) == 6
+    assert call(n_max=40000, m_max=40000) == 6     # shared memory of one problem does not fit
+    assert b"shared memory" in lib.gw_last_error()
+    assert call(ws_bytes=8) == 2                   # GW_ENOMEM: workspace too small
