@@ -80,7 +80,8 @@ __global__ void center_left_kernel(float* Z, const double* wz, int64_t n, int RP
 }
 
 // Gram partials: part[b][r1][r2] = sum_{i in block b} U_i[r1] Z_i[r2]
-__global__ void gram_partial_kernel(const float* U, const float* Z, int64_t n, int RP,
+// (when sym, U == Z and only r1 <= r2 is computed)
+__global__ void gram_partial_kernel(const float* U, const float* Z, int64_t n, int RP, bool sym,
                                     double* part) {
   extern __shared__ float sh[];
   float* Us = sh;               // [32][RP]
@@ -104,6 +105,7 @@ __global__ void gram_partial_kernel(const float* U, const float* Z, int64_t n, i
       const int e = threadIdx.x + q * blockDim.x;
       if (e >= RR) break;
       const int r1 = e / RP, r2 = e % RP;
+      if (sym && r1 > r2) continue;
       double a = 0.0;
       for (int ii = 0; ii < cnt; ++ii)
         a = fma(static_cast<double>(Us[ii * RP + r1]), static_cast<double>(Zs[ii * RP + r2]), a);
@@ -116,11 +118,14 @@ __global__ void gram_partial_kernel(const float* U, const float* Z, int64_t n, i
   }
 }
 
-__global__ void gram_final_kernel(const double* part, int blocks, int RR, double* G) {
+__global__ void gram_final_kernel(const double* part, int blocks, int RP, bool sym, double* G) {
+  const int RR = RP * RP;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= RR) return;
+  const int r1 = e / RP, r2 = e % RP;
+  const int src = (sym && r1 > r2) ? r2 * RP + r1 : e;   // the mirrored entry
   double a = 0.0;
-  for (int b = 0; b < blocks; ++b) a += part[static_cast<int64_t>(b) * RR + e];
+  for (int b = 0; b < blocks; ++b) a += part[static_cast<int64_t>(b) * RR + src];
   G[e] = a;
 }
 
@@ -374,9 +379,10 @@ int apply_kernel(int64_t n, int d, const float* w, CostParams cp, LiftBufs& B, c
 int gram(const float* U, const float* Z, int64_t n, int RP, LiftBufs& B, std::vector<double>& G,
          cudaStream_t st) {
   const size_t shb = sizeof(float) * 2 * 32 * RP;
-  gram_partial_kernel<<<kGramBlocks, 256, shb, st>>>(U, Z, n, RP, B.g_part);
+  const bool sym = U == Z;
+  gram_partial_kernel<<<kGramBlocks, 256, shb, st>>>(U, Z, n, RP, sym, B.g_part);
   GW_LAUNCH_CHECK();
-  gram_final_kernel<<<ceil_div(RP * RP, 256), 256, 0, st>>>(B.g_part, kGramBlocks, RP * RP, B.G);
+  gram_final_kernel<<<ceil_div(RP * RP, 256), 256, 0, st>>>(B.g_part, kGramBlocks, RP, sym, B.G);
   GW_LAUNCH_CHECK();
   G.resize(static_cast<size_t>(RP) * RP);
   GW_CUDA_TRY(cudaMemcpyAsync(G.data(), B.G, sizeof(double) * RP * RP, cudaMemcpyDeviceToHost, st));
