@@ -200,9 +200,12 @@ void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
     // Below ~8e6 cells an iteration of the tensor-core forms is bound by its
     // ~10 small launches (operand refresh, two passes, merges); the FP32
     // kernels are faster there and at least as accurate.
-    O.prec = static_cast<double>(r.n) * static_cast<double>(r.m) < kSmallCells ? GW_PREC_FP32 : r.prec;
+    const bool small = static_cast<double>(r.n) * static_cast<double>(r.m) < kSmallCells;
+    O.prec = small ? GW_PREC_FP32 : r.prec;
     O.record = 0;
-    O.use_graph = 1;
+    // A request's graph runs once: below the threshold its capture and
+    // instantiation cost more host time than launching the kernels directly.
+    O.use_graph = small ? 0 : 1;
     gw_result R{G, Gp, f, g, en, nullptr};
     rc = gw_solve(&P, &O, &R, ws, ws_bytes, gs);
     if (rc != GW_OK) break;
