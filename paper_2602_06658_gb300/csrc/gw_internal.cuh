@@ -174,14 +174,6 @@ size_t cross_cov_ws_bytes(int64_t n, int64_t m, int D, int E, int prec);
 int run_cross_cov(const PlanArgs& p, int prec, double* Gamma_out, double* stats, double* W,
                   Carver& ws, cudaStream_t st);
 
-// W_j = sum_i pi_ij [X_i, s_i, 1] for j < m (m x (D+2), float64) with
-// pi_ij = a_i b_j exp((f_i + g_j + 16 <X_i, V_j> + 4 s_i t_j) / eps): the
-// plan-weighted reduction in either direction (swap the roles for rows).
-size_t plan_sums_ws_bytes(int64_t n, int64_t m, int D);
-int run_plan_sums(const float* X, const float* s, const float* a, const float* f, const float* V,
-                  const float* t, const float* b, const float* g, float eps, int64_t n, int64_t m,
-                  int D, double* W, Carver& ws, cudaStream_t st);
-
 // Adjoint (gw_grad.cu)
 size_t grad_ws_bytes(int64_t n, int64_t m, int D, int E, int dx_dim, int prec);
 int run_grad(const gw_problem& p, const float* f, const float* g, const double* Gamma_t,

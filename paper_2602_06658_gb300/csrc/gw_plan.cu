@@ -644,55 +644,6 @@ static int cross_cov_stage(const PlanArgs& p, int prec, double* W_user, Carver& 
   return GW_OK;
 }
 
-size_t plan_sums_ws_bytes(int64_t n, int64_t m, int D) {
-  Carver c(nullptr, ~size_t(0));
-  const int splits = colsum_row_splits(n, m);
-  int rps = ceil_div(n, splits);
-  rps = ((rps + kBR - 1) / kBR) * kBR;
-  c.take<float>(static_cast<size_t>(ceil_div(n, rps)) * m * (D + 2));
-  return c.used();
-}
-
-int run_plan_sums(const float* X, const float* s, const float* a, const float* f, const float* V,
-                  const float* t, const float* b, const float* g, float eps, int64_t n, int64_t m,
-                  int D, double* W, Carver& ws, cudaStream_t st) {
-  int splits = colsum_row_splits(n, m);
-  int rps = ceil_div(n, splits);
-  rps = ((rps + kBR - 1) / kBR) * kBR;
-  splits = ceil_div(n, rps);
-  float* Wp = ws.take<float>(static_cast<size_t>(splits) * m * (D + 2));
-  GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the plan-weighted sums");
-  ColSumArgs A;
-  A.X = X;
-  A.s = s;
-  A.a = a;
-  A.f = f;
-  A.V = V;
-  A.t = t;
-  A.b = b;
-  A.g = g;
-  A.eps = eps;
-  A.n = n;
-  A.m = m;
-  A.D = D;
-  A.rows_per_split = rps;
-  A.Wp = Wp;
-  dim3 grid(ceil_div(m, kThreads), splits);
-  switch (dpad(D)) {
-    case 4: plan_colsum_kernel<4><<<grid, kThreads, 0, st>>>(A); break;
-    case 8: plan_colsum_kernel<8><<<grid, kThreads, 0, st>>>(A); break;
-    case 16: plan_colsum_kernel<16><<<grid, kThreads, 0, st>>>(A); break;
-    case 32: plan_colsum_kernel<32><<<grid, kThreads, 0, st>>>(A); break;
-    case 64: plan_colsum_kernel<64><<<grid, kThreads, 0, st>>>(A); break;
-    default: plan_colsum_kernel<128><<<grid, kThreads, 0, st>>>(A); break;
-  }
-  GW_LAUNCH_CHECK();
-  const int64_t count = m * (D + 2);
-  reduce_splits_kernel<<<ceil_div(count, 256), 256, 0, st>>>(Wp, splits, count, W);
-  GW_LAUNCH_CHECK();
-  return GW_OK;
-}
-
 int run_cross_cov(const PlanArgs& p, int prec, double* Gamma_out, double* stats, double* W,
                   Carver& ws, cudaStream_t st) {
   CrossCovLayout L;
