@@ -6,8 +6,11 @@
 // iterations on the bilinear cost (Algorithm 3, or Algorithm 2), the plan-
 // weighted sums W_j = sum_i pi_ij [X_i, s_i, 1] that give Gamma_{t+1} and T,
 // and the energy record.  The arithmetic is that of the FP32 path of
-// gw_solve (same exponent, same online max/sum in chunks of 8 columns, FP64
-// cross-covariance and energy); a problem never depends on the others, and
+// gw_solve (the same base-2 exponent, FP64 cross-covariance and energy),
+// except that each softmin sum is taken against the current potential as a
+// known shift, with the exact online max/sum of gw_solve (chunks of 8
+// columns) only where that sum leaves a safe range; a problem never depends
+// on the others, and
 // every reduction runs in a fixed order inside its CTA, so a result is
 // bitwise the same alone and in any batch.
 //
