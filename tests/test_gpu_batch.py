@@ -155,3 +155,30 @@ def test_batch_rejects_what_it_cannot_hold(gw):
     with pytest.raises(gw.GWError) as e:
         gw.gw_solve_batch(wide, 0.05, 2, 10)
     assert e.value.code == 6
+
+
+def test_exact_fallback_when_the_shift_is_far_off(gw):
+    """Unit-scale features: in the first iteration (f = g = 0) the shifted
+    sums overflow (beta s_i t_j reaches ~1e3 in base 2 at eps = 0.05), so
+    the entries go through the exact running-max form; the outer step (the
+    one that starts from f = g = 0) still matches gw_solve's FP32 path, in
+    energy and potentials.  Later outer steps of this data are not compared:
+    with s t up to ~9 the energy falls from ~26 to ~13 in three unconverged
+    outer steps and the Gamma updates amplify FP32 differences (4e-4 between
+    the two FP32 paths); at eps = 0.005 even the first step differs by 0.2%."""
+    probs = [random_problem(n, m, 3, 3, seed=500 + n, scale=1.0) for n, m in [(120, 90), (64, 200)]]
+    packed = gw.pack_problems(probs)
+    out = gw.gw_solve_batch(packed, 0.05, 1, 40, record=True)
+    hist = host(out["history"])
+    fs, gs = split(packed, out["f"], "x"), split(packed, out["g"], "y")
+    for q, P in enumerate(probs):
+        s_max, t_max = P["s"].max(), P["t"].max()
+        assert 4.0 / 0.05 * np.log2(np.e) * s_max * t_max > 200.0   # the shift starts far off
+        ref = solve_alone(gw, P, 0.05, 1, 40)
+        rh = host(ref["history"])
+        assert np.all(hist[q, :, gw.EN["status"]] == 0), q
+        assert np.all(np.abs(hist[q, :, gw.EN["E"]] - rh[:, gw.EN["E"]])
+                      <= 5e-5 * np.abs(rh[:, gw.EN["E"]]) + 1e-9), (q, hist[q, :, 0], rh[:, 0])
+        fr, gr = host(ref["f"]), host(ref["g"])
+        assert np.abs(fs[q] - fr).max() <= 1e-4 * (np.abs(fr).max() + 0.05), q
+        assert np.abs(gs[q] - gr).max() <= 1e-4 * (np.abs(gr).max() + 0.05), q
