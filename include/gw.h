@@ -92,7 +92,8 @@ typedef struct CUstream_st* gw_stream_t;
 #define GW_EN_MASS 10      /* sum_ij pi_ij */
 #define GW_EN_DGAMMA 11    /* ||Gamma_{t+1} - Gamma_t||_F */
 #define GW_EN_EPS 12       /* eps used */
-#define GW_EN_STATUS 13    /* 0, or GW_ENONFINITE when a term is not finite */
+#define GW_EN_STATUS 13    /* 0, GW_ENONFINITE when a term is not finite, or
+                              (gw_solve) GW_ETIMEOUT when a bounded wait gave up */
 #define GW_EN_NINNER 14    /* gw_solve: Sinkhorn iterations run in this outer step */
 #define GW_EN_STOPERR 15   /* gw_solve: Err of the stop rule's last check, -1 if none */
 #define GW_EN_LEN 16
@@ -140,7 +141,9 @@ int gw_sinkhorn_softmin(const float* A, const float* B, const float* sA, const f
  *     GW_ENOMEM with the sizes in gw_last_error().
  *   - The first call on a device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
- *     The current device must be the device of `stream`.
+ *     The current device must be the device of `stream`.  The address is
+ *     kept for the life of the process and is not looked up again after a
+ *     cudaDeviceReset: do not call this entry point after resetting a device.
  *   - All calls on a device share the one array: calls that overlap on the
  *     GPU (different streams, or host threads) race and give wrong results.
  *     Serialise them, e.g. on one stream.
@@ -432,9 +435,11 @@ size_t gw_sgw_workspace_size(int64_t n, int64_t m, int D, int E, int prec, int w
  *   (bitwise).  Sizes: 1 <= D, E <= 4; n_max, m_max (host) bound every
  *   problem's n and m and size the shared memory, which must hold
  *   (n_max + m_max) (D + 7) floats plus padding (about 7000 points in all at
- *   D = 2); a problem outside the bounds (or with n or m = 0) gets
- *   GW_EINVAL in its record's GW_EN_STATUS and untouched outputs.
- * Workspace: gw_solve_batch_workspace_size() bytes (the queue counter).
+ *   D = 2); a problem outside the bounds (or with n or m = 0, or an eps0 /
+ *   eps1 that is not finite and > 0) gets a record of NaN terms with
+ *   GW_EINVAL in GW_EN_STATUS, and its other outputs are left untouched.
+ * Workspace: gw_solve_batch_workspace_size() bytes (the queue counter),
+ *   256-byte aligned.
  * Errors: GW_EINVAL (nprob < 1, n_outer / n_inner < 1, a null pointer),
  *   GW_EUNSUPPORTED (D or E outside 1..4, sizes that do not fit), GW_ENOMEM,
  *   GW_ECUDA.
@@ -509,6 +514,46 @@ int gw_version(void);
  * captured into a CUDA graph count once, at capture).  reset != 0 returns the
  * count and sets it to zero.  Diagnostic only. */
 unsigned long long gw_kernel_launches(int reset);
+
+/*
+ * Bounded device waits (failure detection).  The tensor-core kernels run a
+ * pipeline of copy, MMA and epilogue roles inside each CTA that wait on one
+ * another through shared-memory barriers.  No wait is unbounded: a wait that
+ * has not been satisfied after the limit below (nanoseconds of the GPU's
+ * global timer; default 2 s) gives up, the CTA waits (at most 2 s more) for
+ * its own copies and MMAs already in flight, frees its tensor memory, writes
+ * NaN for its rows and adds 1 to a per-device counter.  The context stays
+ * usable.  Because the potentials then hold NaN, a solve's energy record
+ * reports it: gw_solve sets GW_EN_STATUS to GW_ETIMEOUT when the counter
+ * moved during the call (a give-up in a call that ran at the same time on
+ * another stream of the device is attributed to both).  The tensor-core
+ * plan sums recompute their partials on the CUDA cores instead.
+ *
+ * gw_set_wait_limit_ns: limit for kernels enqueued after the call (process-
+ *   wide; kernels already captured in a CUDA graph keep theirs).  1 ns ..
+ *   600 s, else GW_EINVAL.  A limit far below a kernel's run time makes its
+ *   waits give up: that is how the failure path is exercised.
+ * gw_wait_limit_ns: the current limit.
+ * gw_wait_status: synchronizes the current device, then returns GW_ETIMEOUT
+ *   if its counter is non-zero (else GW_OK); reset != 0 sets it to zero.
+ *   The counter's address is looked up once per device and kept for the
+ *   life of the process (not again after a cudaDeviceReset).
+ */
+int gw_set_wait_limit_ns(unsigned long long ns);
+unsigned long long gw_wait_limit_ns(void);
+int gw_wait_status(int reset);
+
+/*
+ * gw_probe_ex2 -- measurement aid, not part of the method: enqueues one
+ * kernel of `blocks` x 512 threads in which every thread evaluates 8
+ * independent register chains x <- 2^-x with ex2.approx (the instruction
+ * the softmin epilogue spends one of per cell), `iters` x 4 steps each.
+ * *h_ops receives the number of exponentials the launch evaluates; timing
+ * the launch (CUDA events on `stream`) gives the measured exponential
+ * throughput that bounds the softmin.  out: blocks x 512 floats (device).
+ * Errors: GW_EINVAL, GW_ECUDA.
+ */
+int gw_probe_ex2(int blocks, int iters, float* out, unsigned long long* h_ops, gw_stream_t stream);
 
 #ifdef __cplusplus
 }

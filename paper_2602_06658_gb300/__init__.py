@@ -21,6 +21,7 @@ __all__ = [
     "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
     "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
     "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer", "gw_sinkhorn_iteration",
+    "gw_set_wait_limit_ns", "gw_wait_limit_ns", "gw_wait_status", "gw_probe_ex2",
 ]
 
 GW_OK = 0
@@ -142,6 +143,14 @@ lib.gw_last_error.restype = ctypes.c_char_p
 lib.gw_version.restype = _int
 lib.gw_kernel_launches.argtypes = [_int]
 lib.gw_kernel_launches.restype = ctypes.c_ulonglong
+lib.gw_set_wait_limit_ns.argtypes = [ctypes.c_ulonglong]
+lib.gw_set_wait_limit_ns.restype = _int
+lib.gw_wait_limit_ns.argtypes = []
+lib.gw_wait_limit_ns.restype = ctypes.c_ulonglong
+lib.gw_wait_status.argtypes = [_int]
+lib.gw_wait_status.restype = _int
+lib.gw_probe_ex2.argtypes = [_int, _int, _p, ctypes.POINTER(ctypes.c_ulonglong), _p]
+lib.gw_probe_ex2.restype = _int
 for _name in ("gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve", "gw_lift", "gw_grad_x",
               "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer", "gw_sinkhorn_iteration", "gw_transfer"):
     getattr(lib, _name).restype = _int
@@ -158,6 +167,38 @@ def gw_version() -> int:
 def gw_kernel_launches(reset: bool = False) -> int:
     """Kernels libgw has enqueued in this process (graph captures count once)."""
     return int(lib.gw_kernel_launches(int(bool(reset))))
+
+
+def gw_set_wait_limit_ns(ns: int) -> int:
+    """Set the bounded-wait limit of the tensor-core kernels enqueued from now
+    on; returns the previous limit."""
+    prev = int(lib.gw_wait_limit_ns())
+    _check(lib.gw_set_wait_limit_ns(int(ns)))
+    return prev
+
+
+def gw_wait_limit_ns() -> int:
+    return int(lib.gw_wait_limit_ns())
+
+
+def gw_wait_status(reset: bool = False) -> int:
+    """GW_OK, or GW_ETIMEOUT (5) when a bounded wait of this device gave up
+    since the last reset.  Synchronizes the device; does not raise for a
+    timeout (other errors raise)."""
+    rc = int(lib.gw_wait_status(int(bool(reset))))
+    if rc not in (GW_OK, 5):
+        raise GWError(rc, gw_last_error())
+    return rc
+
+
+def gw_probe_ex2(blocks: int, iters: int, out=None, stream=None) -> int:
+    """Enqueue the exponential-throughput probe (measurement aid); returns
+    the number of exponentials the launch evaluates."""
+    if out is None:
+        out = torch.empty(blocks * 512, dtype=torch.float32, device="cuda")
+    ops = ctypes.c_ulonglong(0)
+    _check(lib.gw_probe_ex2(int(blocks), int(iters), _ptr(out), ctypes.byref(ops), _stream(stream)))
+    return int(ops.value)
 
 
 def gw_workspace_size(op: int, n: int, m: int, D: int, E: int, prec: int = PREC_FP32) -> int:

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "gw_internal.cuh"
@@ -30,6 +31,40 @@ std::atomic<unsigned long long> g_launches{0};
 }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------ bounded waits
+// Every CTA of the tensor-core kernels whose pipeline wait gave up adds 1
+// here (one counter per device).
+__device__ unsigned int g_wait_gave_up = 0;
+
+namespace {
+std::atomic<unsigned long long> g_wait_limit_ns{2000000000ull};   // 2 s
+constexpr int kMaxDevices = 64;
+std::mutex g_gave_up_mu;
+unsigned int* g_gave_up_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+// The device address of this device's counter, looked up once per device
+// (null when the lookup fails: the kernels then count nothing).
+static unsigned int* gave_up_counter() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_gave_up_mu);
+  if (g_gave_up_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_wait_gave_up) == cudaSuccess) {
+      g_gave_up_ptr[dev] = static_cast<unsigned int*>(p);
+    } else {
+      cudaGetLastError();
+    }
+  }
+  return g_gave_up_ptr[dev];
+}
+
+tc::WaitCtl wait_ctl() { return tc::WaitCtl{g_wait_limit_ns.load(), gave_up_counter()}; }
 
 namespace {
 
@@ -75,6 +110,7 @@ size_t solve_fixed_bytes(int64_t n, int64_t m, int D, int E) {
   c.take<double>(GW_EN_LEN);        // scratch energy record
   c.take<double>(kMargBlocks);      // stop-rule partials
   c.take<double>(2);                // stop-rule Err
+  c.take<unsigned>(1);              // give-up counter as the call began
   return c.used();
 }
 
@@ -149,6 +185,7 @@ int launch_iteration(const float* X, const float* V, const float* s, const float
 struct SolveBufs {
   float *loga, *logb, *f[2], *g[2], *V;
   double *G[2], *C, *en, *mpart, *merr;
+  unsigned* gave_up0;
 };
 
 // read one device double (the stream is drained first)
@@ -175,11 +212,19 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
   B.en = c.take<double>(GW_EN_LEN);
   B.mpart = c.take<double>(kMargBlocks);
   B.merr = c.take<double>(2);
+  B.gave_up0 = c.take<unsigned>(1);
   GW_TRY(check_ws(c, ws));
   const size_t mark = c.used();
   char* base = static_cast<char*>(ws);
 
   const size_t DE = static_cast<size_t>(p.D) * p.E;
+  // the records report GW_ETIMEOUT when the give-up counter moves during the call
+  const unsigned* counter = wait_ctl().gave_up;
+  if (counter) {
+    GW_CUDA_TRY(cudaMemcpyAsync(B.gave_up0, counter, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+  } else {
+    B.gave_up0 = nullptr;
+  }
   GW_TRY(launch_log(p.a, p.n, B.loga, st));
   GW_TRY(launch_log(p.b, p.m, B.logb, st));
   if (o.f0) {
@@ -258,7 +303,7 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
     if (o.record || last || o.adaptive) {
       double* rec = (o.record && r.history) ? r.history + static_cast<size_t>(t) * GW_EN_LEN : B.en;
       GW_TRY(run_energy(pa, o.prec, B.C, B.logb, rec, B.G[Gc ^ 1], sub, st));
-      GW_TRY(launch_record_extra(rec, n_run, checked ? B.merr : nullptr, st));
+      GW_TRY(launch_record_extra(rec, n_run, checked ? B.merr : nullptr, B.gave_up0, st));
       if (o.adaptive) {
         // Algorithm 6: an energy increase means Sinkhorn was not converged
         double E = 0.0;
@@ -300,6 +345,31 @@ int gw_version(void) { return 100; }
 
 unsigned long long gw_kernel_launches(int reset) {
   return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+int gw_set_wait_limit_ns(unsigned long long ns) {
+  gw::set_error("");
+  GW_REQUIRE(ns >= 1 && ns <= 600000000000ull, GW_EINVAL,
+             "wait limit must be in [1 ns, 600 s] (got %llu)", ns);
+  g_wait_limit_ns.store(ns);
+  return GW_OK;
+}
+
+unsigned long long gw_wait_limit_ns(void) { return g_wait_limit_ns.load(); }
+
+int gw_wait_status(int reset) {
+  gw::set_error("");
+  unsigned int* p = gave_up_counter();
+  GW_REQUIRE(p != nullptr, GW_ECUDA, "the give-up counter of this device is not reachable");
+  GW_CUDA_TRY(cudaDeviceSynchronize());
+  unsigned int v = 0;
+  GW_CUDA_TRY(cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost));
+  if (reset) GW_CUDA_TRY(cudaMemset(p, 0, sizeof(unsigned int)));
+  if (v != 0) {
+    gw::set_error("%u CTA(s) gave up a bounded wait", v);
+    return GW_ETIMEOUT;
+  }
+  return GW_OK;
 }
 
 size_t gw_workspace_size(int op, int64_t n, int64_t m, int D, int E, int prec) {
@@ -437,6 +507,7 @@ int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, s
   GW_REQUIRE(ws != nullptr && ws_bytes >= need, GW_ENOMEM,
              "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  (void)wait_ctl();   // looks the counter up outside any capture
   const bool host_driven = o->adaptive || o->stop_tol > 0.0f;
   if (!o->use_graph || st == nullptr || host_driven) return enqueue_solve(*p, *o, *r, ws, ws_bytes, st);
 

@@ -488,9 +488,19 @@ __global__ void __launch_bounds__(kBt, 2) batch_solve_kernel(BatchArgs A) {
     if (q >= A.nprob) break;
     const int64_t x0 = A.xo[q], y0 = A.yo[q];
     const int64_t n = A.xo[q + 1] - x0, m = A.yo[q + 1] - y0;
-    if (n < 1 || m < 1 || n > A.n_max || m > A.m_max || x0 < 0 || y0 < 0) {
-      if (threadIdx.x == 0)
-        A.energy[static_cast<int64_t>(q) * GW_EN_LEN + GW_EN_STATUS] = static_cast<double>(GW_EINVAL);
+    const float e0 = A.eps0[q];
+    const float e1 = A.eps1 != nullptr ? A.eps1[q] : e0;
+    const bool eps_ok = e0 > 0.0f && isfinite(e0) && e1 > 0.0f && isfinite(e1);
+    if (n < 1 || m < 1 || n > A.n_max || m > A.m_max || x0 < 0 || y0 < 0 || !eps_ok) {
+      // the whole record, so that a caller that did not clear it reads no
+      // stale terms: NaN everywhere, the status GW_EINVAL
+      if (threadIdx.x < GW_EN_LEN) {
+        double v = __longlong_as_double(0x7ff8000000000000ll);
+        if (threadIdx.x == GW_EN_STATUS) v = static_cast<double>(GW_EINVAL);
+        if (threadIdx.x == GW_EN_NINNER) v = 0.0;
+        if (threadIdx.x == GW_EN_STOPERR) v = -1.0;
+        A.energy[static_cast<int64_t>(q) * GW_EN_LEN + threadIdx.x] = v;
+      }
       continue;
     }
     solve_one<DP>(A, q, x0, y0, static_cast<int>(n), static_cast<int>(m), bsm);
@@ -509,6 +519,8 @@ int run_solve_batch(int nprob, const int64_t* xo, const int64_t* yo, int64_t n_m
                     size_t ws_bytes, cudaStream_t st) {
   GW_REQUIRE(ws_bytes >= batch_ws_bytes() && ws != nullptr, GW_ENOMEM,
              "workspace too small: need %zu bytes", batch_ws_bytes());
+  GW_REQUIRE(reinterpret_cast<uintptr_t>(ws) % 256 == 0, GW_ENOMEM,
+             "workspace must be 256-byte aligned");
   const size_t smem = batch_smem_bytes(n_max, m_max, D);
   GW_REQUIRE(smem <= 227 * 1024 - 64, GW_EUNSUPPORTED,
              "problems of up to %lld + %lld points at D = %d need %zu bytes of shared memory "

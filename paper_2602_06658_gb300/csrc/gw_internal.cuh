@@ -78,6 +78,19 @@ inline int check_ws(const Carver& c, void* ws) {
   return GW_OK;
 }
 
+// --------------------------------------------------------- bounded waits
+namespace tc {
+// Limit of the pipeline waits of one launch (nanoseconds of %globaltimer)
+// and the device counter a CTA increments when one of its waits gave up
+// (null: not counted).
+struct WaitCtl {
+  uint64_t limit_ns;
+  unsigned int* gave_up;
+};
+}  // namespace tc
+// The current limit (gw_set_wait_limit_ns) and this device's give-up counter.
+tc::WaitCtl wait_ctl();
+
 // ------------------------------------------------------------ device math
 __device__ __forceinline__ float ex2(float x) {
   float y;
@@ -228,8 +241,11 @@ constexpr int kMargBlocks = 152;
 int run_marginal_error(const float* f0, const float* f1, const float* a, int64_t n,
                        const float* g0, const float* g1, const float* b, int64_t m, float eps,
                        bool symmetric, double* part, double* out, cudaStream_t st);
-// rec[GW_EN_NINNER], rec[GW_EN_STOPERR] (err may be null: -1)
-int launch_record_extra(double* rec, int n_inner, const double* err, cudaStream_t st);
+// rec[GW_EN_NINNER], rec[GW_EN_STOPERR] (err may be null: -1); with
+// gave_up0 (the device's give-up counter as the call began) the status
+// becomes GW_ETIMEOUT when the counter moved since
+int launch_record_extra(double* rec, int n_inner, const double* err, const unsigned* gave_up0,
+                        cudaStream_t st);
 
 // Plan-weighted column sums on the tensor cores (gw_plan_tc.cu): Wp partials
 // [splits][m][D + 2] of W_j = sum_i pi_ij [X_i, s_i, 1]; *flag_out is set on

@@ -50,6 +50,7 @@ struct LtLayout {
 };
 
 struct LtTask {
+  tc::WaitCtl wc;
   int64_t n;
   int64_t rows_pad;     // row stride of the coordinate table
   int RP;
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(kLtThreads, 1)
   tc::tc_fence_after();
   const uint32_t tbase = tmem_base;
   volatile int* ab = &abort_flag;
+  const uint64_t lim = T.wc.limit_ns;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(kLtThreads, 1)
       int issued = 0;
       for (int t = 0; t < ntiles; ++t) {
         const int s = t % S;
-        if (!tc::mbar_wait(&empty[s], ((t / S) & 1) ^ 1, ab)) break;
+        if (!tc::mbar_wait(&empty[s], ((t / S) & 1) ^ 1, ab, lim)) break;
         tc::mbar_arrive_expect_tx(&full[s], T.stage_bytes);
         unsigned char* st = Ss + s * T.stage_bytes;
         const int k0 = (tile0 + t) * kLtBN;
@@ -227,8 +229,8 @@ __global__ void __launch_bounds__(kLtThreads, 1)
       const uint32_t id1 = tc::f16_idesc(128, RP, false);
       for (int t = 0; t < ntiles; ++t) {
         const int s = t % S, b = t & 1;
-        if (!tc::mbar_wait(&cfull[b], (t >> 1) & 1, ab)) break;
-        if (!tc::mbar_wait(&full[s], (t / S) & 1, ab)) break;
+        if (!tc::mbar_wait(&cfull[b], (t >> 1) & 1, ab, lim)) break;
+        if (!tc::mbar_wait(&full[s], (t / S) & 1, ab, lim)) break;
         *reinterpret_cast<volatile int*>(&consumed) = t + 1;   // this stage's copies landed
         tc::tc_fence_after();
         const unsigned char* Cb = Cs + b * kLtCBuf;
@@ -278,8 +280,8 @@ __global__ void __launch_bounds__(kLtThreads, 1)
     bool ok = true;
     for (int t = 0; t < ntiles; ++t) {
       const int s = t % S, b = t & 1;
-      bool got = tc::mbar_wait(&full[s], (t / S) & 1, ab);
-      if (got && t >= 2) got = tc::mbar_wait(&cempty[b], ((t >> 1) & 1) ^ 1, ab);
+      bool got = tc::mbar_wait(&full[s], (t / S) & 1, ab, lim);
+      if (got && t >= 2) got = tc::mbar_wait(&cempty[b], ((t >> 1) & 1) ^ 1, ab, lim);
       if (!__all_sync(0xffffffffu, got)) {
         ok = false;
         break;
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(kLtThreads, 1)
     // partial rows: warp -> (TMEM lane quarter q = warp % 4, half hh, column
     // half ch); thread -> one row
     int fin = (ok && ntiles > 0) ? 1 : 0;
-    if (fin && lane == 0) fin = tc::mbar_wait(wdone, 0, ab) ? 1 : 0;
+    if (fin && lane == 0) fin = tc::mbar_wait(wdone, 0, ab, lim) ? 1 : 0;
     fin = __shfl_sync(0xffffffffu, fin, 0);
     const bool good = __all_sync(0xffffffffu, fin != 0 && *ab == 0);
     const int q = warp & 3, g = e >> 2, hh = g & 1, ch = g >> 1;
@@ -374,6 +376,7 @@ __global__ void __launch_bounds__(kLtThreads, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
+  if (threadIdx.x == 0) tc::note_gave_up(T.wc, ab);
   if (warp == 0) {
     __syncwarp();
     tc::tc_fence_after();
@@ -569,6 +572,7 @@ int lift_tc_matvec(const float* P, int64_t n, int d, int kind, float param, int 
   T.xt = B.xt;
   T.uinv = B.uinv;
   T.Zp = Zp;
+  T.wc = wait_ctl();
   const int cost = kind == GW_PEN_GAUSS ? kLtGauss
                    : (kind == GW_PEN_POWER && param == 1.0f) ? kLtSqrt
                                                              : kLtGeneric;

@@ -375,10 +375,15 @@ __global__ void marg_err_final_kernel(const double* part, int nb, double* out) {
 }
 
 // rec[GW_EN_NINNER] = iterations run, rec[GW_EN_STOPERR] = *err (or -1)
-__global__ void record_extra_kernel(double* rec, double n_inner, const double* err) {
+__global__ void record_extra_kernel(double* rec, double n_inner, const double* err,
+                                    const unsigned* gave_up, const unsigned* gave_up0) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     rec[GW_EN_NINNER] = n_inner;
     rec[GW_EN_STOPERR] = err ? *err : -1.0;
+    // a bounded wait gave up since the call began: its rows were written as
+    // NaN, and the record says why
+    if (gave_up != nullptr && gave_up0 != nullptr && *gave_up != *gave_up0)
+      rec[GW_EN_STATUS] = static_cast<double>(GW_ETIMEOUT);
   }
 }
 
@@ -725,8 +730,10 @@ int run_marginal_error(const float* f0, const float* f1, const float* a, int64_t
   return GW_OK;
 }
 
-int launch_record_extra(double* rec, int n_inner, const double* err, cudaStream_t st) {
-  record_extra_kernel<<<1, 32, 0, st>>>(rec, static_cast<double>(n_inner), err);
+int launch_record_extra(double* rec, int n_inner, const double* err, const unsigned* gave_up0,
+                        cudaStream_t st) {
+  record_extra_kernel<<<1, 32, 0, st>>>(rec, static_cast<double>(n_inner), err,
+                                        gave_up0 ? wait_ctl().gave_up : nullptr, gave_up0);
   GW_LAUNCH_CHECK();
   return GW_OK;
 }

@@ -48,6 +48,7 @@ struct PlanSmem {
 };
 
 struct PlanTask {
+  tc::WaitCtl wc;
   int64_t rows;      // targets j
   int ksteps;
   int col_tiles;     // source tiles of 64
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   tc::tc_fence_after();
   const uint32_t tbase = tmem_base;
   volatile int* ab = &abort_flag;
+  const uint64_t lim = T.wc.limit_ns;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       int issued = 0;
       for (int t = 0; t < ntiles; ++t) {
         const int s = t % S;
-        if (!tc::mbar_wait(&empty[s], ((t / S) & 1) ^ 1, ab)) break;
+        if (!tc::mbar_wait(&empty[s], ((t / S) & 1) ^ 1, ab, lim)) break;
         tc::mbar_arrive_expect_tx(&full[s], L::kStageBytes);
         unsigned char* st = Bs + s * L::kStageBytes;
         const int c0 = (tile0 + t) * kPlanBN;
@@ -159,12 +161,12 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       const uint32_t idesc = tc::f16_idesc(128, kPlanBN, BF16);
       const uint32_t idesc2 = tc::f16_idesc(128, NW, false);
       const int nks = T.ksteps;
-      bool ok = tc::mbar_wait(afull, 0, ab);
+      bool ok = tc::mbar_wait(afull, 0, ab, lim);
       // exponent tile t into TMEM buffer t & 1
       auto issue_e = [&](int t) -> bool {
         const int s = t % S, b = t & 1;
-        if (!tc::mbar_wait(&tempty[b], ((t >> 1) & 1) ^ 1, ab)) return false;
-        if (!tc::mbar_wait(&full[s], (t / S) & 1, ab)) return false;
+        if (!tc::mbar_wait(&tempty[b], ((t >> 1) & 1) ^ 1, ab, lim)) return false;
+        if (!tc::mbar_wait(&full[s], (t / S) & 1, ab, lim)) return false;
         *reinterpret_cast<volatile int*>(&consumed) = t + 1;   // this stage's copies landed
         tc::tc_fence_after();
         const unsigned char* Bst = Bs + s * L::kStageBytes;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       // W += q_hi U_hi + q_hi U_lo + q_lo U_hi for tile t (P written by the epilogue)
       auto issue_w = [&](int t) -> bool {
         const int s = t % S;
-        if (!tc::mbar_wait(pfull, t & 1, ab)) return false;
+        if (!tc::mbar_wait(pfull, t & 1, ab, lim)) return false;
         tc::tc_fence_after();
         const unsigned char* Ust = Bs + s * L::kStageBytes + L::kBBytes;
 #pragma unroll
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
       int got = 0;
-      if (lane == 0) got = tc::mbar_wait(&tfull[b], (t >> 1) & 1, ab) ? 1 : 0;
+      if (lane == 0) got = tc::mbar_wait(&tfull[b], (t >> 1) & 1, ab, lim) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) {
         ok = false;
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       }
       // the P tile is free once the W MMAs of the previous tile are done
       if (t > 0) {
-        if (lane == 0) got = tc::mbar_wait(pempty, (t - 1) & 1, ab) ? 1 : 0;
+        if (lane == 0) got = tc::mbar_wait(pempty, (t - 1) & 1, ab, lim) ? 1 : 0;
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) {
           ok = false;
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     // final W rows: one warp per (half, lane quarter) reads its 32 rows
     int got = 1;
     if (ok) {
-      if (lane == 0) got = tc::mbar_wait(wdone, 0, ab) ? 1 : 0;
+      if (lane == 0) got = tc::mbar_wait(wdone, 0, ab, lim) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
       ok = got != 0;
     }
@@ -324,6 +326,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
+  if (threadIdx.x == 0) tc::note_gave_up(T.wc, ab);
   if (warp == 0) {
     __syncwarp();
     tc::tc_fence_after();
@@ -542,6 +545,7 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int
   T.uinv = B.uinv;
   T.Wp = B.Wp;
   T.flag = B.flag;
+  T.wc = wait_ctl();
   const int blocks = Lt.row_tiles * Lt.splits;
   int rc;
   if (shp.KP == 64) {

@@ -95,8 +95,17 @@ struct Job {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Below ~8e6 cells an iteration of the tensor-core forms is bound by its
+// ~10 small launches (operand refresh, two passes, merges); the FP32 kernels
+// are faster there and at least as accurate.  The one rule for the
+// precision a request runs in (sizing and solve).
+bool small_request(const gw_request& r) {
+  return static_cast<double>(r.n) * static_cast<double>(r.m) < kSmallCells;
+}
+int run_prec(const gw_request& r) { return small_request(r) ? GW_PREC_FP32 : r.prec; }
+
 // Device bytes a request needs (inputs, features, state, the larger of the
-// lift and solve workspaces).
+// lift and solve workspaces, the solve's sized for the precision it runs in).
 size_t request_bytes(const gw_request& r) {
   const int D = r.kind == GW_PEN_SQEUCLID ? r.d : r.D;
   size_t b = 0;
@@ -105,7 +114,7 @@ size_t request_bytes(const gw_request& r) {
   b += align256(sizeof(float) * r.n * D) + align256(sizeof(float) * r.m * D);       // X, Y
   b += align256(sizeof(float) * r.n) + align256(sizeof(float) * r.m);               // f, g
   b += 2 * align256(sizeof(double) * D * D) + align256(sizeof(double) * GW_EN_LEN);  // Gamma x2, energy
-  size_t ws = gw_workspace_size(GW_OP_SOLVE, r.n, r.m, D, D, r.prec);
+  size_t ws = gw_workspace_size(GW_OP_SOLVE, r.n, r.m, D, D, run_prec(r));
   if (r.kind != GW_PEN_SQEUCLID) {
     ws = std::max(ws, gw_workspace_size(GW_OP_LIFT, r.n, r.n, D, r.d, GW_PREC_FP32));
     ws = std::max(ws, gw_workspace_size(GW_OP_LIFT, r.m, r.m, D, r.d, GW_PREC_FP32));
@@ -197,11 +206,8 @@ void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
     O.n_outer = r.n_outer;
     O.n_inner = r.n_inner;
     O.symmetric = 1;
-    // Below ~8e6 cells an iteration of the tensor-core forms is bound by its
-    // ~10 small launches (operand refresh, two passes, merges); the FP32
-    // kernels are faster there and at least as accurate.
-    const bool small = static_cast<double>(r.n) * static_cast<double>(r.m) < kSmallCells;
-    O.prec = small ? GW_PREC_FP32 : r.prec;
+    const bool small = small_request(r);
+    O.prec = run_prec(r);
     O.record = 0;
     // A request's graph runs once: below the threshold its capture and
     // instantiation cost more host time than launching the kernels directly.
@@ -214,7 +220,8 @@ void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
       rc = GW_ECUDA;
       break;
     }
-    if (out.energy[GW_EN_STATUS] != 0.0) rc = GW_ENONFINITE;
+    const double es = out.energy[GW_EN_STATUS];
+    if (es != 0.0) rc = es == static_cast<double>(GW_ETIMEOUT) ? GW_ETIMEOUT : GW_ENONFINITE;
   } while (false);
   if (rc != GW_OK) cudaStreamSynchronize(st);
   out.status = rc;

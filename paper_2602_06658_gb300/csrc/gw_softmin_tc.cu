@@ -59,6 +59,7 @@ constexpr float kSumLo = 8.673617e-19f;      // 2^-60: a total below this underf
 constexpr float kSumHi = 1.3292280e36f;      // 2^120: a sum above this (or inf/NaN) overflowed
 
 struct TcTask {
+  tc::WaitCtl wc;         // pipeline wait limit and the give-up counter
   int64_t n, m;           // real rows / columns
   int ksteps;             // MMA K-steps of 16 that hold non-zero operand columns
   const float* est;       // per-row shift estimate (fast pass), or null
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   tc::tc_fence_after();
   const uint32_t tbase = tmem_base;
   volatile int* ab = &abort_flag;
+  const uint64_t lim = T.wc.limit_ns;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       int issued = 0;
       for (int t = 0; t < ntiles; ++t) {
         const int s = t % S;
-        if (!tc::mbar_wait(&empty[s], ((t / S) & 1) ^ 1, ab)) break;
+        if (!tc::mbar_wait(&empty[s], ((t / S) & 1) ^ 1, ab, lim)) break;
         tc::mbar_arrive_expect_tx(&full[s], L::kStageBytes);
         for (int kb = 0; kb < KB; ++kb)
           tc::tma_load_2d(Bs + s * L::kStageBytes + kb * L::kBBlock, mB, kb * 64, (tile0 + t) * BN,
@@ -257,11 +259,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     if (lane == 0) {
       // ------------------------------------------------------- MMA issuer
       const uint32_t idesc = tc::f16_idesc(128, BN, BF16);
-      bool ok = tc::mbar_wait(afull, 0, ab);
+      bool ok = tc::mbar_wait(afull, 0, ab, lim);
       for (int t = 0; ok && t < ntiles; ++t) {
         const int s = t % S, b = t & 1;
-        if (!tc::mbar_wait(&tempty[b], ((t >> 1) & 1) ^ 1, ab)) break;
-        if (!tc::mbar_wait(&full[s], (t / S) & 1, ab)) break;
+        if (!tc::mbar_wait(&tempty[b], ((t >> 1) & 1) ^ 1, ab, lim)) break;
+        if (!tc::mbar_wait(&full[s], (t / S) & 1, ab, lim)) break;
         tc::tc_fence_after();
         const unsigned char* Bst = Bs + s * L::kStageBytes;
         const int nks = T.ksteps;
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       const int b = t & 1;
       // one lane waits, the warp follows: tcgen05.ld needs a converged warp
       int got = 0;
-      if (lane == 0) got = tc::mbar_wait(&tfull[b], (t >> 1) & 1, ab) ? 1 : 0;
+      if (lane == 0) got = tc::mbar_wait(&tfull[b], (t >> 1) & 1, ab, lim) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) {
         ok = false;
@@ -390,6 +392,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
+  if (threadIdx.x == 0) tc::note_gave_up(T.wc, ab);
   if (warp == 0) {
     __syncwarp();
     tc::tc_fence_after();
@@ -613,6 +616,7 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     K.out = T.out;
     K.pm = T.pm;
     K.ps = T.ps;
+    K.wc = wait_ctl();
   }
   if (tasks[0].reuse_ops) {
     float* part = ws.take<float>(static_cast<size_t>(2 * 2 * kSmCount));

@@ -6,11 +6,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gw_internal.cuh"
+
 namespace gw {
 namespace tc {
 
-// A wait gives up after this many nanoseconds of %globaltimer (then the
-// kernel records an error and winds down instead of hanging the GPU).
+// The wind-down of a CTA that gave up (waiting for its own copies and MMAs
+// already in flight) is bounded by this many nanoseconds of %globaltimer.
+// The ordinary pipeline waits take their limit from the launch (WaitCtl).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ uint64_t globaltimer() {
@@ -56,19 +59,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of parity `parity`.  Returns false on timeout
-// or when *abort became non-zero (another role gave up).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// Bounded wait for the phase of parity `parity`.  Returns false after
+// limit_ns of %globaltimer (and sets *abort) or when *abort became non-zero
+// (another role gave up).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (globaltimer() - t0 > kWaitLimitNs) {
+    if (globaltimer() - t0 > limit_ns) {
       *abort = 1;
       return false;
     }
   }
+}
+
+// Called by one thread of a CTA at its end: counts the CTA once when one of
+// its waits gave up.
+__device__ __forceinline__ void note_gave_up(const WaitCtl& w, volatile int* abort) {
+  if (*abort && w.gave_up != nullptr) atomicAdd(w.gave_up, 1u);
 }
 
 // ------------------------------------------------------------------- TMA

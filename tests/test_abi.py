@@ -76,9 +76,10 @@ def test_batched_solver_validates_on_the_host():
     lib.gw_last_error.restype = ctypes.c_char_p
     d = p(0x1000)
 
-    def call(nprob=2, n_max=100, m_max=100, D=2, E=2, n_outer=2, n_inner=3, X=d, ws_bytes=4096):
+    def call(nprob=2, n_max=100, m_max=100, D=2, E=2, n_outer=2, n_inner=3, X=d, ws_bytes=4096,
+             ws=d):
         return lib.gw_solve_batch(nprob, d, d, n_max, m_max, D, E, X, d, d, d, d, d, d, None,
-                                  n_outer, n_inner, 1, d, d, d, d, d, None, d, ws_bytes, None)
+                                  n_outer, n_inner, 1, d, d, d, d, d, None, ws, ws_bytes, None)
 
     assert lib.gw_solve_batch_workspace_size() >= 4
     assert call(nprob=0) == 1                      # GW_EINVAL: empty batch
@@ -89,3 +90,22 @@ def test_batched_solver_validates_on_the_host():
     assert call(n_max=40000, m_max=40000) == 6     # shared memory of one problem does not fit
     assert b"shared memory" in lib.gw_last_error()
     assert call(ws_bytes=8) == 2                   # GW_ENOMEM: workspace too small
+    assert call(ws=p(0x1010)) == 2                 # GW_ENOMEM: workspace not 256-byte aligned
+    assert b"aligned" in lib.gw_last_error()
+
+
+def test_wait_limit_is_validated_on_the_host():
+    """The bounded-wait limit is a host setting: out-of-range values are
+    refused, a valid one is kept (no device is touched)."""
+    lib = ctypes.CDLL(builder().build())
+    lib.gw_set_wait_limit_ns.argtypes = [ctypes.c_ulonglong]
+    lib.gw_set_wait_limit_ns.restype = ctypes.c_int
+    lib.gw_wait_limit_ns.restype = ctypes.c_ulonglong
+    prev = lib.gw_wait_limit_ns()
+    assert prev == 2_000_000_000                   # default 2 s
+    assert lib.gw_set_wait_limit_ns(0) == 1        # GW_EINVAL
+    assert lib.gw_set_wait_limit_ns(601 * 10**9) == 1
+    assert lib.gw_wait_limit_ns() == prev
+    assert lib.gw_set_wait_limit_ns(5_000_000) == 0
+    assert lib.gw_wait_limit_ns() == 5_000_000
+    assert lib.gw_set_wait_limit_ns(prev) == 0
