@@ -35,7 +35,7 @@ namespace {
 constexpr int kBt = 512;                 // threads per CTA
 constexpr int kBw = kBt / 32;            // warps per CTA
 constexpr int kBChunk = 8;               // columns per online-max update
-constexpr int kBRed = 16 + 5;            // doubles reduced at once (D E <= 16, + stats)
+constexpr int kBRed = 16 + 6;            // doubles reduced at once (D E <= 16, + stats)
 
 struct BatchArgs {
   int nprob;
@@ -365,6 +365,7 @@ __device__ void solve_one(const BatchArgs& A, int q, int64_t x0, int64_t y0, int
       }
       float W[DP + 2];
       for (int k = 0; k < DP + 2; ++k) W[k] = 0.0f;
+      float Wz = 0.0f, Wla = 0.0f;   // sum_i pi_ij log2 pi_ij, sum_i pi_ij log a_i
       for (int i = 0; i < n; ++i) {
         const float4 r = rp0[i];
         float z = fmaf(r.y * beta, tj, r.x + cb);
@@ -387,9 +388,14 @@ __device__ void solve_one(const BatchArgs& A, int q, int64_t x0, int64_t y0, int
         }
         W[DP] = fmaf(p, r.y, W[DP]);
         W[DP + 1] += p;
+        Wz = fmaf(p, fmaxf(z, -1000.0f), Wz);          // p = 0 where z = -inf
+        Wla = fmaf(p, fmaxf(la[i], -1.0e30f), Wla);
       }
       const double col = W[DP + 1];
       const double bj = A.b[y0 + j];
+      // KL(pi | a x b) over this column: sum_i pi_ij log(pi_ij / (a_i b_j))
+      v[DE + 5] += 0.6931471805599453 * (static_cast<double>(Wz) - log2(bj) * col) -
+                   static_cast<double>(Wla);
       for (int d = 0; d < D; ++d)
         for (int e = 0; e < E; ++e)
           v[d * E + e] = fma(static_cast<double>(W[d]), static_cast<double>(A.Y[(y0 + j) * E + e]),
@@ -400,10 +406,10 @@ __device__ void solve_one(const BatchArgs& A, int q, int64_t x0, int64_t y0, int
       v[DE + 3] += fabs(col - bj);
       v[DE + 4] = fmax(v[DE + 4], fabs(col - bj) / bj);
     }
-    block_reduce(v, DE + 5, 1u << (DE + 4), red, rr);
+    block_reduce(v, DE + 6, 1u << (DE + 4), red, rr);
     if (tid < DE) Gn[tid] = rr[tid];
-    const double T = rr[DE], gcol = rr[DE + 1], mass = rr[DE + 2], cl1 = rr[DE + 3],
-                 crmax = rr[DE + 4];
+    const double T = rr[DE], mass = rr[DE + 2], cl1 = rr[DE + 3], crmax = rr[DE + 4],
+                 KLd = rr[DE + 5];
     __syncthreads();
 
     const bool last = t == A.n_outer - 1;
@@ -421,24 +427,24 @@ __device__ void solve_one(const BatchArgs& A, int q, int64_t x0, int64_t y0, int
         const double ai = A.a[x0 + i];
         const double r = ai * exp((static_cast<double>(f[i]) - static_cast<double>(fhat[i])) /
                                   static_cast<double>(eps));
-        w3[0] += static_cast<double>(f[i]) * r;
         w3[1] += fabs(r - ai);
         w3[2] = fmax(w3[2], fabs(r - ai) / ai);
       }
       block_reduce(w3, 3, 4u, red, rr);
       if (tid == 0) {
-        double g2 = 0.0, gdot = 0.0, dg2 = 0.0;
+        double g2 = 0.0, dg2 = 0.0;
         for (int k = 0; k < DE; ++k) {
           g2 += Gn[k] * Gn[k];
-          gdot += Gt[k] * Gn[k];
           dg2 += (Gn[k] - Gt[k]) * (Gn[k] - Gt[k]);
         }
-        const double epsKL = rr[0] + gcol + 16.0 * gdot + 4.0 * T;
+        // KL summed over the plan's own entries (the potential form, f r +
+        // g c + 16 <Gamma_t, Gamma_{t+1}> + 4 T over eps, cancels terms of
+        // size |f| / eps)
         const double L = C - 8.0 * g2 - 4.0 * T;
         double en[GW_EN_LEN];
-        en[GW_EN_E] = L + epsKL;
+        en[GW_EN_E] = L + static_cast<double>(eps) * KLd;
         en[GW_EN_L] = L;
-        en[GW_EN_KL] = epsKL / static_cast<double>(eps);
+        en[GW_EN_KL] = KLd;
         en[GW_EN_C] = C;
         en[GW_EN_GAMMA2] = g2;
         en[GW_EN_T] = T;

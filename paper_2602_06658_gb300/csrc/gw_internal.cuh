@@ -252,8 +252,11 @@ int launch_record_extra(double* rec, int n_inner, const double* err, const unsig
 // the device when the FP32 kernel has to recompute them.
 bool plan_tc_supported(int D, int prec);
 size_t plan_tc_ws_bytes(int64_t n, int64_t m, int D, int prec);
-int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int* splits_out,
-                int* rows_per_split_out, int** flag_out, Carver& ws, cudaStream_t st);
+// Ep_out (or null): the KL partials [splits][m][2] of the energy
+// (A_j = sum_i pi_ij log2(pi_ij / b_j), B_j = sum_i pi_ij log a_i).
+int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, float** Ep_out,
+                int* splits_out, int* rows_per_split_out, int** flag_out, Carver& ws,
+                cudaStream_t st);
 
 // Color / UV transfer (gw_transfer.cu)
 size_t transfer_ws_bytes(int64_t n, int64_t m, int D, int k);

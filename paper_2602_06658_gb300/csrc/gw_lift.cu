@@ -10,12 +10,14 @@
 // (matrix-free: C is never stored, each product is one N x N tiled pass on
 // the tensor cores, gw_lift_tc.cu),
 // re-orthonormalised by Cholesky QR, and a final Rayleigh-Ritz step.  The
-// small r x r Cholesky and eigen-problems run on the host in float64 (cyclic
-// Jacobi); every N-sized step runs in the kernels below.
+// small r x r Cholesky, triangular inverse and eigen-problem (cyclic Jacobi)
+// run on the device too, one block each in float64, so a lift makes no host
+// round trip until the one read of its status at the end.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "gw_internal.cuh"
@@ -240,6 +242,181 @@ __global__ void center_points_kernel(const float* x, const float* w, int64_t n, 
   }
 }
 
+// ---- the small dense steps on the device (one block each, float64) ----
+// Cholesky QR step: G (RP x RP Gram, global) -> M = R^{-1} with G + delta I =
+// R^T R (upper R), delta = 1e-13 tr(G) / RP keeping the factorisation defined
+// when a direction vanishes.  A trace that is not positive and finite, or a
+// pivot that is not positive, sets *status = 1 and leaves M = I (the result is
+// then discarded by the caller).  Dynamic shared memory: RP x RP doubles.
+__global__ void __launch_bounds__(256) chol_inv_kernel(const double* G, int RP, double* M,
+                                                       int* status) {
+  extern __shared__ double R[];   // [RP][RP]
+  __shared__ double red[8];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  const int RR = RP * RP;
+  double tr = 0.0;
+  for (int e = tid; e < RR; e += blockDim.x) {
+    R[e] = G[e];
+    if (e / RP == e % RP) tr += G[e];
+  }
+  tr = warp_sum(tr);
+  if ((tid & 31) == 0) red[tid >> 5] = tr;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < static_cast<int>(blockDim.x >> 5); ++q) t += red[q];
+    red[0] = t;
+    if (!(t > 0.0) || !isfinite(t)) bad = 1;
+  }
+  __syncthreads();
+  const double shift = 1e-13 * red[0] / RP;
+  for (int i = tid; i < RP; i += blockDim.x) R[i * RP + i] += shift;
+  __syncthreads();
+  // right-looking: pivot j, then row j of R, then the trailing update
+  for (int j = 0; j < RP && !bad; ++j) {
+    if (tid == 0) {
+      const double d = R[j * RP + j];
+      if (!(d > 0.0)) bad = 1;
+      else R[j * RP + j] = sqrt(d);
+    }
+    __syncthreads();
+    if (bad) break;
+    const double dj = R[j * RP + j];
+    for (int i = j + 1 + tid; i < RP; i += blockDim.x) R[j * RP + i] /= dj;
+    __syncthreads();
+    for (int e = tid; e < RR; e += blockDim.x) {
+      const int r = e / RP, c = e % RP;
+      if (r > j && c >= r) R[r * RP + c] -= R[j * RP + r] * R[j * RP + c];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    for (int e = tid; e < RR; e += blockDim.x) M[e] = (e / RP == e % RP) ? 1.0 : 0.0;
+    if (tid == 0) *status = 1;
+    return;
+  }
+  // M = R^{-1}: column c by back substitution (one thread per column)
+  for (int c = tid; c < RP; c += blockDim.x) {
+    for (int i = RP - 1; i >= 0; --i) {
+      double acc = (i == c) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= c; ++k) acc -= R[i * RP + k] * M[k * RP + c];
+      M[i * RP + c] = i <= c ? acc / R[i * RP + i] : 0.0;
+    }
+  }
+}
+
+// Rayleigh-Ritz on the device: T (RP x RP, global) is symmetrised and
+// diagonalised by cyclic Jacobi rotations in the round-robin order (RP / 2
+// disjoint pairs per step, rotated at once); U (global, RP x RP) accumulates
+// the vectors.  Then the D largest eigenvalues (ties: lower index) give
+// Msel (RP x D, their vectors), lam and sqrt(max(lam, 0)).  Sweeps stop when
+// the off-diagonal mass is below 1e-30 of the total (at most 100).
+// Dynamic shared memory: RP x RP doubles.
+__global__ void __launch_bounds__(256) ritz_eig_kernel(const double* T, int RP, int D, double* U,
+                                                       double* Msel, float* lam, float* sl) {
+  extern __shared__ double A[];   // [RP][RP]
+  __shared__ double cs[64][2];
+  __shared__ double red[2][8];
+  __shared__ int done;
+  const int tid = threadIdx.x;
+  const int RR = RP * RP;
+  const int half = RP / 2;
+  for (int e = tid; e < RR; e += blockDim.x) {
+    const int r = e / RP, c = e % RP;
+    A[e] = 0.5 * (T[r * RP + c] + T[c * RP + r]);
+    U[e] = r == c ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < RR; e += blockDim.x) {
+      const double v = A[e] * A[e];
+      tot += v;
+      if (e / RP != e % RP) off += v;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = off;
+      red[1][tid >> 5] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double o = 0.0, t = 0.0;
+      for (int q = 0; q < static_cast<int>(blockDim.x >> 5); ++q) {
+        o += red[0][q];
+        t += red[1][q];
+      }
+      done = (o <= 1e-30 * t) ? 1 : 0;
+    }
+    __syncthreads();
+    if (done) break;
+    for (int step = 0; step < RP - 1; ++step) {
+      // pair i: positions i and RP-1-i of the arrangement [0, 1 + (k - 1 + step) mod (RP - 1)]
+      if (tid < half) {
+        const int i = tid;
+        const int p0 = i == 0 ? 0 : 1 + (i - 1 + step) % (RP - 1);
+        const int q0 = 1 + (RP - 2 - i + step) % (RP - 1);
+        const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
+        const double apq = A[p * RP + q];
+        double c = 1.0, sn = 0.0;
+        if (fabs(apq) >= 1e-300) {
+          const double theta = (A[q * RP + q] - A[p * RP + p]) / (2.0 * apq);
+          const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          sn = t * c;
+        }
+        cs[i][0] = c;
+        cs[i][1] = sn;
+      }
+      __syncthreads();
+      // rows p, q of every pair: A <- J^T A
+      for (int w = tid; w < half * RP; w += blockDim.x) {
+        const int i = w / RP, k = w % RP;
+        const int p0 = i == 0 ? 0 : 1 + (i - 1 + step) % (RP - 1);
+        const int q0 = 1 + (RP - 2 - i + step) % (RP - 1);
+        const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
+        const double c = cs[i][0], sn = cs[i][1];
+        const double apk = A[p * RP + k], aqk = A[q * RP + k];
+        A[p * RP + k] = c * apk - sn * aqk;
+        A[q * RP + k] = sn * apk + c * aqk;
+      }
+      __syncthreads();
+      // columns p, q: A <- A J, U <- U J
+      for (int w = tid; w < half * RP; w += blockDim.x) {
+        const int i = w / RP, k = w % RP;
+        const int p0 = i == 0 ? 0 : 1 + (i - 1 + step) % (RP - 1);
+        const int q0 = 1 + (RP - 2 - i + step) % (RP - 1);
+        const int p = p0 < q0 ? p0 : q0, q = p0 < q0 ? q0 : p0;
+        const double c = cs[i][0], sn = cs[i][1];
+        const double akp = A[k * RP + p], akq = A[k * RP + q];
+        A[k * RP + p] = c * akp - sn * akq;
+        A[k * RP + q] = sn * akp + c * akq;
+        const double ukp = U[k * RP + p], ukq = U[k * RP + q];
+        U[k * RP + p] = c * ukp - sn * ukq;
+        U[k * RP + q] = sn * ukp + c * ukq;
+      }
+      __syncthreads();
+    }
+  }
+  // the D largest eigenvalues, in decreasing order
+  for (int k = tid; k < RP; k += blockDim.x) {
+    const double lk = A[k * RP + k];
+    int rank = 0;
+    for (int j = 0; j < RP; ++j) {
+      const double lj = A[j * RP + j];
+      rank += (lj > lk || (lj == lk && j < k)) ? 1 : 0;
+    }
+    if (rank < D) {
+      lam[rank] = static_cast<float>(lk);
+      sl[rank] = static_cast<float>(sqrt(lk > 0.0 ? lk : 0.0));
+      for (int r = 0; r < RP; ++r) Msel[r * D + rank] = U[r * RP + k];
+    }
+  }
+}
+
 int rpad(int D) {
   const int want = D + 8;
   const int opts[] = {16, 32, 48, 64, 80, 96, 128};
@@ -248,81 +425,10 @@ int rpad(int D) {
   return 128;
 }
 
-// ---- host-side small dense linear algebra (float64) ----
-// Cholesky G = R^T R (upper R); returns false if G is not positive definite.
-bool cholesky_upper(std::vector<double>& G, int r) {
-  for (int j = 0; j < r; ++j) {
-    double s = G[j * r + j];
-    for (int k = 0; k < j; ++k) s -= G[k * r + j] * G[k * r + j];
-    if (!(s > 0.0)) return false;
-    const double d = sqrt(s);
-    G[j * r + j] = d;
-    for (int i = j + 1; i < r; ++i) {
-      double t = G[j * r + i];
-      for (int k = 0; k < j; ++k) t -= G[k * r + j] * G[k * r + i];
-      G[j * r + i] = t / d;
-    }
-    for (int i = 0; i < j; ++i) G[j * r + i] = 0.0;
-  }
-  return true;
-}
-
-// inverse of an upper-triangular matrix
-std::vector<double> inv_upper(const std::vector<double>& R, int r) {
-  std::vector<double> W(static_cast<size_t>(r) * r, 0.0);
-  for (int j = 0; j < r; ++j) {
-    W[j * r + j] = 1.0 / R[j * r + j];
-    for (int i = j - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= j; ++k) s += R[i * r + k] * W[k * r + j];
-      W[i * r + j] = -s / R[i * r + i];
-    }
-  }
-  return W;
-}
-
-// Cyclic Jacobi eigen-decomposition of a symmetric r x r matrix A (row-major).
-// On return A's diagonal holds the eigenvalues and U's columns the vectors.
-void jacobi_eig(std::vector<double>& A, std::vector<double>& U, int r) {
-  U.assign(static_cast<size_t>(r) * r, 0.0);
-  for (int i = 0; i < r; ++i) U[i * r + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < r; ++i)
-      for (int j = 0; j < r; ++j) {
-        tot += A[i * r + j] * A[i * r + j];
-        if (i != j) off += A[i * r + j] * A[i * r + j];
-      }
-    if (off <= 1e-30 * tot) break;
-    for (int p = 0; p < r - 1; ++p)
-      for (int q = p + 1; q < r; ++q) {
-        const double apq = A[p * r + q];
-        if (fabs(apq) < 1e-300) continue;
-        const double theta = (A[q * r + q] - A[p * r + p]) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < r; ++k) {
-          const double akp = A[k * r + p], akq = A[k * r + q];
-          A[k * r + p] = c * akp - s * akq;
-          A[k * r + q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < r; ++k) {
-          const double apk = A[p * r + k], aqk = A[q * r + k];
-          A[p * r + k] = c * apk - s * aqk;
-          A[q * r + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < r; ++k) {
-          const double ukp = U[k * r + p], ukq = U[k * r + q];
-          U[k * r + p] = c * ukp - s * ukq;
-          U[k * r + q] = s * ukp + c * ukq;
-        }
-      }
-  }
-}
-
 struct LiftBufs {
-  float *Q, *P, *Z, *Zp, *V, *sl;
+  float *Q, *P, *Z, *Zp, *V, *sl, *lam;
   double *cs_part, *cs, *g_part, *G, *M;
+  int* status;
   int splits, RP;
   LiftTcBufs tc;
 };
@@ -339,11 +445,13 @@ LiftBufs carve_lift(Carver& c, int64_t n, int D) {
   B.Zp = B.splits > 1 ? c.take<float>(nr * B.splits) : nullptr;
   B.V = c.take<float>(static_cast<size_t>(n) * D);
   B.sl = c.take<float>(static_cast<size_t>(D));
+  B.lam = c.take<float>(static_cast<size_t>(D));
   B.cs_part = c.take<double>(static_cast<size_t>(kGramBlocks) * B.RP);
   B.cs = c.take<double>(B.RP);
   B.g_part = c.take<double>(static_cast<size_t>(kGramBlocks) * B.RP * B.RP);
   B.G = c.take<double>(static_cast<size_t>(B.RP) * B.RP);
   B.M = c.take<double>(static_cast<size_t>(B.RP) * B.RP);
+  B.status = c.take<int>(4);
   return B;
 }
 
@@ -376,37 +484,40 @@ int apply_kernel(int64_t n, int d, const float* w, CostParams cp, LiftBufs& B, c
   return GW_OK;
 }
 
-int gram(const float* U, const float* Z, int64_t n, int RP, LiftBufs& B, std::vector<double>& G,
-         cudaStream_t st) {
+// G = U^T Z on the device (float64, fixed-order partials)
+int gram(const float* U, const float* Z, int64_t n, int RP, LiftBufs& B, cudaStream_t st) {
   const size_t shb = sizeof(float) * 2 * 32 * RP;
   const bool sym = U == Z;
   gram_partial_kernel<<<kGramBlocks, 256, shb, st>>>(U, Z, n, RP, sym, B.g_part);
   GW_LAUNCH_CHECK();
   gram_final_kernel<<<ceil_div(RP * RP, 256), 256, 0, st>>>(B.g_part, kGramBlocks, RP, sym, B.G);
   GW_LAUNCH_CHECK();
-  G.resize(static_cast<size_t>(RP) * RP);
-  GW_CUDA_TRY(cudaMemcpyAsync(G.data(), B.G, sizeof(double) * RP * RP, cudaMemcpyDeviceToHost, st));
-  GW_CUDA_TRY(cudaStreamSynchronize(st));
   return GW_OK;
 }
 
-// Q <- Z R^{-1} with Z^T Z = R^T R (Cholesky QR)
+// the dense r x r kernels take up to 128 x 128 doubles of shared memory
+int small_kernel_attrs() {
+  static std::once_flag once;
+  static cudaError_t rc = cudaSuccess;
+  std::call_once(once, [] {
+    rc = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              128 * 128 * 8);
+    if (rc == cudaSuccess)
+      rc = cudaFuncSetAttribute(ritz_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                128 * 128 * 8);
+  });
+  GW_CUDA_TRY(rc);
+  return GW_OK;
+}
+
+// Q <- Z R^{-1} with Z^T Z = R^T R (Cholesky QR), all on the device
 int orthonormalize(int64_t n, LiftBufs& B, cudaStream_t st) {
   const int RP = B.RP;
-  std::vector<double> G;
-  GW_TRY(gram(B.Z, B.Z, n, RP, B, G, st));
-  // tiny diagonal shift keeps the factorisation defined when a direction vanishes
-  double tr = 0.0;
-  for (int i = 0; i < RP; ++i) tr += G[i * RP + i];
-  GW_REQUIRE(tr > 0.0 && isfinite(tr), GW_ENONFINITE, "Kernel PCA: degenerate block (trace %g)", tr);
-  for (int i = 0; i < RP; ++i) G[i * RP + i] += 1e-13 * tr / RP;
-  GW_REQUIRE(cholesky_upper(G, RP), GW_ENONFINITE,
-             "Kernel PCA: Gram matrix is not positive definite");
-  std::vector<double> W = inv_upper(G, RP);
-  GW_CUDA_TRY(cudaMemcpyAsync(B.M, W.data(), sizeof(double) * RP * RP, cudaMemcpyHostToDevice, st));
+  GW_TRY(gram(B.Z, B.Z, n, RP, B, st));
+  chol_inv_kernel<<<1, 256, sizeof(double) * RP * RP, st>>>(B.G, RP, B.M, B.status);
+  GW_LAUNCH_CHECK();
   right_mult_kernel<<<ceil_div(n * RP, 256), 256, 0, st>>>(B.Z, n, RP, B.M, RP, RP, B.Q);
   GW_LAUNCH_CHECK();
-  GW_CUDA_TRY(cudaStreamSynchronize(st));   // W (host) must outlive the copy
   return GW_OK;
 }
 
@@ -434,6 +545,8 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
   GW_REQUIRE(n > RP, GW_EINVAL, "Kernel PCA with D=%d needs more than %d points (n=%lld)", D, RP,
              static_cast<long long>(n));
   CostParams cp{kind, param};
+  GW_TRY(small_kernel_attrs());
+  GW_CUDA_TRY(cudaMemsetAsync(B.status, 0, sizeof(int) * 4, st));
   GW_TRY(lift_tc_prepare(x, n, d, kind, param, RP, B.tc, st));
   const int iters = n_iter > 0 ? n_iter : 40;
   random_block_kernel<<<ceil_div(n * RP, 256), 256, 0, st>>>(B.Q, n * RP, seed);
@@ -442,31 +555,12 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
     GW_TRY(apply_kernel(n, d, w, cp, B, st));
     GW_TRY(orthonormalize(n, B, st));
   }
-  // Rayleigh-Ritz: T = Q^T K~ Q, eigenpairs of T, V = Q U_{1:D}
+  // Rayleigh-Ritz: T = Q^T K~ Q, eigenpairs of T, V = Q U_{1:D} (device)
   GW_TRY(apply_kernel(n, d, w, cp, B, st));
-  std::vector<double> T;
-  GW_TRY(gram(B.Q, B.Z, n, RP, B, T, st));
-  for (int i = 0; i < RP; ++i)
-    for (int j = i + 1; j < RP; ++j) {
-      const double v = 0.5 * (T[i * RP + j] + T[j * RP + i]);
-      T[i * RP + j] = T[j * RP + i] = v;
-    }
-  std::vector<double> U;
-  jacobi_eig(T, U, RP);
-  std::vector<int> order(RP);
-  for (int i = 0; i < RP; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(),
-            [&](int a, int b) { return T[a * RP + a] > T[b * RP + b]; });
-  std::vector<double> Msel(static_cast<size_t>(RP) * D);
-  std::vector<float> lam(D), sl(D);
-  for (int c2 = 0; c2 < D; ++c2) {
-    const int k = order[c2];
-    lam[c2] = static_cast<float>(T[k * RP + k]);
-    sl[c2] = static_cast<float>(sqrt(std::max(0.0, T[k * RP + k])));
-    for (int r = 0; r < RP; ++r) Msel[r * D + c2] = U[r * RP + k];
-  }
-  GW_CUDA_TRY(cudaMemcpyAsync(B.M, Msel.data(), sizeof(double) * RP * D, cudaMemcpyHostToDevice, st));
-  GW_CUDA_TRY(cudaMemcpyAsync(B.sl, sl.data(), sizeof(float) * D, cudaMemcpyHostToDevice, st));
+  GW_TRY(gram(B.Q, B.Z, n, RP, B, st));
+  ritz_eig_kernel<<<1, 256, sizeof(double) * RP * RP, st>>>(B.G, RP, D, B.g_part, B.M, B.lam,
+                                                             B.sl);
+  GW_LAUNCH_CHECK();
   right_mult_kernel<<<ceil_div(n * D, 256), 256, 0, st>>>(B.Q, n, RP, B.M, D, D, B.V);
   GW_LAUNCH_CHECK();
   sign_partial_kernel<<<kGramBlocks, 128, 0, st>>>(B.V, n, D, B.g_part, B.g_part + kGramBlocks * D);
@@ -480,9 +574,15 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
     GW_CUDA_TRY(cudaMemcpyAsync(basis, B.V, sizeof(float) * n * D, cudaMemcpyDeviceToDevice, st));
   }
   if (eigvals) {
-    GW_CUDA_TRY(cudaMemcpyAsync(eigvals, lam.data(), sizeof(float) * D, cudaMemcpyHostToDevice, st));
+    GW_CUDA_TRY(cudaMemcpyAsync(eigvals, B.lam, sizeof(float) * D, cudaMemcpyDeviceToDevice, st));
   }
+  // the one host read of the lift: did a Cholesky step fail?
+  int status = 0;
+  GW_CUDA_TRY(cudaMemcpyAsync(&status, B.status, sizeof(int), cudaMemcpyDeviceToHost, st));
   GW_CUDA_TRY(cudaStreamSynchronize(st));
+  GW_REQUIRE(status == 0, GW_ENONFINITE,
+             "Kernel PCA: degenerate block (the Gram matrix of a subspace iterate is not positive "
+             "definite)");
   return GW_OK;
 }
 

@@ -56,16 +56,20 @@ struct ColSumArgs {
   int D;
   int rows_per_split;
   float* Wp;       // [splits][m][D+2]
+  float* Ep;       // [splits][m][2]: A_j, B_j of the KL term (or null)
   const int* cond; // run only when *cond != 0 (null: always)
 };
 
-// W_j = sum_i pi_ij [X_i, s_i, 1] over one row split, one column per thread.
+// W_j = sum_i pi_ij [X_i, s_i, 1] over one row split, one column per thread;
+// with P.Ep also the KL partials A_j = sum_i pi_ij log2(pi_ij / b_j) and
+// B_j = sum_i pi_ij log a_i (KL(pi | a x b) = sum_j ln2 A_j - B_j).
 template <int DP>
 __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
   __shared__ __align__(16) float Xs[kBR][DP];
   __shared__ float rb[kBR];
   __shared__ float us[kBR];
   __shared__ float ss[kBR];
+  __shared__ float la[kBR];
   if (P.cond != nullptr && *P.cond == 0) return;   // the tensor-core pass succeeded
 
   const int tid = threadIdx.x;
@@ -85,7 +89,8 @@ __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
   uint64_t acc2[DP / 2];
 #pragma unroll
   for (int k = 0; k < DP / 2; ++k) acc2[k] = pk2(0.0f, 0.0f);
-  float acc_s = 0.0f, acc_1 = 0.0f;
+  float acc_s = 0.0f, acc_1 = 0.0f, acc_z = 0.0f, acc_la = 0.0f;
+  const bool ent = P.Ep != nullptr;
 
   const int64_t r_begin = static_cast<int64_t>(blockIdx.y) * P.rows_per_split;
   const int64_t r_end = r_begin + P.rows_per_split < P.n ? r_begin + P.rows_per_split : P.n;
@@ -102,10 +107,12 @@ __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
         rb[tid] = P.f[i] * hs + log2f(P.a[i]);
         us[tid] = P.s[i] * beta;
         ss[tid] = P.s[i];
+        la[tid] = P.a[i] > 0.0f ? logf(P.a[i]) : 0.0f;   // zero weight: p = 0
       } else {
         rb[tid] = kNegBig;
         us[tid] = 0.0f;
         ss[tid] = 0.0f;
+        la[tid] = 0.0f;
       }
     }
     __syncthreads();
@@ -123,7 +130,12 @@ __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
       }
       float z0, z1;
       upk2(z2, z0, z1);
-      const float p = ex2(fminf(z0 + z1, 126.0f));
+      const float z = z0 + z1;   // log2 pi_ij
+      const float p = ex2(fminf(z, 126.0f));
+      if (ent) {
+        acc_z = fmaf(p, fmaxf(z, -1000.0f), acc_z);   // z = -inf (zero weight) has p = 0
+        acc_la = fmaf(p, la[ii], acc_la);
+      }
       const uint64_t pp = pk2(p, p);
 #pragma unroll
       for (int k4 = 0; k4 < DP / 4; ++k4) {
@@ -146,6 +158,37 @@ __global__ void __launch_bounds__(kThreads) plan_colsum_kernel(ColSumArgs P) {
   }
   out[P.D] = acc_s;
   out[P.D + 1] = acc_1;
+  if (ent) {
+    // sum_i pi_ij (log2 pi_ij - log2 b_j) = acc_z - log2(b_j) acc_1
+    float* e2 = P.Ep + (static_cast<int64_t>(blockIdx.y) * P.m + j) * 2;
+    e2[0] = acc_z - (P.b[j] > 0.0f ? log2f(P.b[j]) : 0.0f) * acc_1;
+    e2[1] = acc_la;
+  }
+}
+
+// KL partials: per block of kRedBlocks, sum over its targets j (splits added
+// in order, FP64) of ln2 A_j - B_j.
+__global__ void __launch_bounds__(256)
+    kl_partial_kernel(const float* Ep, int splits, int64_t m, double* Kp) {
+  double v = 0.0;
+  for (int64_t j = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; j < m;
+       j += static_cast<int64_t>(gridDim.x) * 256) {
+    double A = 0.0, B = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      A += static_cast<double>(Ep[(static_cast<int64_t>(s) * m + j) * 2 + 0]);
+      B += static_cast<double>(Ep[(static_cast<int64_t>(s) * m + j) * 2 + 1]);
+    }
+    v += 0.6931471805599453 * A - B;
+  }
+  __shared__ double red[8];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q];
+    Kp[blockIdx.x] = t;
+  }
 }
 
 // W[j][k] = sum over row splits (float64, fixed order).
@@ -396,6 +439,8 @@ struct FinalizeArgs {
   double* stats_out;      // kStats or null
   const double* Rp;       // row stats partials or null (no energy)
   int rblocks;
+  const double* Kp;       // KL partials (kl_partial_kernel)
+  int kblocks;
   const double* MpX;      // moments partials or null (use C_pre)
   const double* MpY;
   int mblocks;
@@ -485,14 +530,23 @@ __global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs F) {
     rl1 += F.Rp[b * 4 + 1];
     rmax = fmax(rmax, F.Rp[b * 4 + 2]);
   }
-  const double T = st[0], gc = st[1];
+  const double T = st[0];
   const double eps = F.eps;
-  const double epsKL = fr + gc + 16.0 * gdot + 4.0 * T;
+  // KL as the plan's own sum of pi log(pi / (a b)) (partials of the plan
+  // pass).  Through the potentials it would be (sum f r + sum g c + 16
+  // <Gamma_t, Gamma_{t+1}> + 4 T) / eps, whose terms are ~|f| / eps each and
+  // cancel: at small eps the FP32 rounding of the row sums r behind it moved
+  // KL by ~0.3%.
+  (void)fr;
+  (void)gdot;
+  double KL = 0.0;
+  for (int b = 0; b < F.kblocks; ++b) KL += F.Kp[b];
+  const double epsKL = eps * KL;
   const double L = C - 8.0 * g2 - 4.0 * T;
   double* en = F.energy;
   en[GW_EN_E] = L + epsKL;
   en[GW_EN_L] = L;
-  en[GW_EN_KL] = epsKL / eps;
+  en[GW_EN_KL] = KL;
   en[GW_EN_C] = C;
   en[GW_EN_GAMMA2] = g2;
   en[GW_EN_T] = T;
@@ -549,9 +603,11 @@ int colsum_row_splits(int64_t n, int64_t m) {
 struct CrossCovLayout {
   float* V;
   float* Wp;
+  float* Ep;       // KL partials (energy only)
   double* W;
   double* Gp;
-  int splits;
+  double* Kp;      // [kRedBlocks] (energy only)
+  int splits;      // row splits of the partials actually written
   int rows_per_split;
 };
 
@@ -565,6 +621,8 @@ CrossCovLayout carve_cross_cov(Carver& c, int64_t n, int64_t m, int D, int E, bo
   L.Wp = c.take<float>(static_cast<size_t>(L.splits) * m * (D + 2));
   L.W = need_W ? c.take<double>(static_cast<size_t>(m) * (D + 2)) : nullptr;
   L.Gp = c.take<double>(static_cast<size_t>(kRedBlocks) * (D * E + kStats));
+  L.Ep = c.take<float>(static_cast<size_t>(L.splits) * m * 2);
+  L.Kp = c.take<double>(static_cast<size_t>(kRedBlocks));
   return L;
 }
 
@@ -598,7 +656,7 @@ static void launch_colsum(const ColSumArgs& A, dim3 grid, cudaStream_t st) {
 
 // Enqueue everything up to the Gamma partials; the caller finalizes.
 static int cross_cov_stage(const PlanArgs& p, int prec, double* W_user, Carver& ws,
-                           cudaStream_t st, CrossCovLayout* out) {
+                           cudaStream_t st, CrossCovLayout* out, bool want_kl = false) {
   GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_F16X3, GW_EUNSUPPORTED, "precision %d", prec);
   CrossCovLayout L = carve_cross_cov(ws, p.n, p.m, p.D, p.E, W_user == nullptr);
   GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for cross-covariance");
@@ -618,6 +676,7 @@ static int cross_cov_stage(const PlanArgs& p, int prec, double* W_user, Carver& 
   A.m = p.m;
   A.D = p.D;
   A.cond = nullptr;
+  A.Ep = nullptr;
   const int64_t count = p.m * (p.D + 2);
   if (plan_tc_supported(p.D, prec)) {
     // both contractions on the tensor cores; the FP32 kernel recomputes the
@@ -625,20 +684,29 @@ static int cross_cov_stage(const PlanArgs& p, int prec, double* W_user, Carver& 
     float* Wp = nullptr;
     int splits = 0, rps = 0;
     int* flag = nullptr;
-    GW_TRY(run_plan_tc(p, prec, L.V, &Wp, &splits, &rps, &flag, ws, st));
+    float* Ep = nullptr;
+    GW_TRY(run_plan_tc(p, prec, L.V, &Wp, want_kl ? &Ep : nullptr, &splits, &rps, &flag, ws, st));
     A.rows_per_split = rps;
     A.Wp = Wp;
+    A.Ep = Ep;
     A.cond = flag;
     launch_colsum(A, dim3(ceil_div(p.m, kThreads), splits), st);
     GW_LAUNCH_CHECK();
     reduce_splits_kernel<<<ceil_div(count, 256), 256, 0, st>>>(Wp, splits, count, L.W);
     GW_LAUNCH_CHECK();
+    L.Ep = Ep;
+    L.splits = splits;
   } else {
     A.rows_per_split = L.rows_per_split;
     A.Wp = L.Wp;
+    A.Ep = want_kl ? L.Ep : nullptr;
     launch_colsum(A, dim3(ceil_div(p.m, kThreads), L.splits), st);
     GW_LAUNCH_CHECK();
     reduce_splits_kernel<<<ceil_div(count, 256), 256, 0, st>>>(L.Wp, L.splits, count, L.W);
+    GW_LAUNCH_CHECK();
+  }
+  if (want_kl) {
+    kl_partial_kernel<<<kRedBlocks, 256, 0, st>>>(L.Ep, L.splits, p.m, L.Kp);
     GW_LAUNCH_CHECK();
   }
   const size_t shbytes = sizeof(double) * 32 * (p.D + 2 + p.E);
@@ -741,7 +809,7 @@ int launch_record_extra(double* rec, int n_inner, const double* err, const unsig
 int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* logb_pre,
                double* energy, double* Gamma_out, Carver& ws, cudaStream_t st) {
   CrossCovLayout L;
-  GW_TRY(cross_cov_stage(p, prec, nullptr, ws, st, &L));
+  GW_TRY(cross_cov_stage(p, prec, nullptr, ws, st, &L, true));
   double *MpX = nullptr, *MpY = nullptr;
   if (!C_pre) GW_TRY(moments_stage(p.X, p.a, p.n, p.D, p.Y, p.b, p.m, p.E, ws, st, &MpX, &MpY));
   float* fhat = ws.take<float>(static_cast<size_t>(p.n));
@@ -778,6 +846,8 @@ int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* lo
   F.stats_out = nullptr;
   F.Rp = Rp;
   F.rblocks = kRedBlocks;
+  F.Kp = L.Kp;
+  F.kblocks = kRedBlocks;
   F.MpX = MpX;
   F.MpY = MpY;
   F.mblocks = kRedBlocks;

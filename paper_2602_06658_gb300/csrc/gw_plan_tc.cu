@@ -15,7 +15,12 @@
 //      stored feature-major so its tiles are K-major B operands).
 // Each CTA owns 256 targets (two M = 128 halves) and one split of the source
 // tiles; the split partials go to Wp[split][j][D + 2] in FP32 and are reduced
-// in a fixed order (deterministic).  A q that does not fit f16 (an estimate
+// in a fixed order (deterministic).  For the energy's KL term the same pass
+// also gives, per split and target, A_j = sum_i pi_ij log2(pi_ij / b_j) (the
+// epilogue accumulates q (out - 12) beside the exponentials) and
+// B_j = sum_i pi_ij log a_i (a fourth U column, log a): KL = sum_j ln2 A_j - B_j,
+// a sum of plan entries times their own small log-ratios, with no large
+// potentials cancelling.  A q that does not fit f16 (an estimate
 // far from the potential) or a wait that gives up sets *flag, and the FP32
 // kernel then recomputes every partial (the launch that follows reads it).
 #include "gw_tc_ops.cuh"
@@ -44,7 +49,8 @@ struct PlanSmem {
   static constexpr int kPBytes = 128 * 128;           // 128 rows x 64 f16 (one half, hi or lo)
   static constexpr int kPOff = kABytes + S * kStageBytes;
   static constexpr int kBarOff = kPOff + 4 * kPBytes;
-  static constexpr int kBytes = kBarOff + 256 + 1024;
+  static constexpr int kXeOff = kBarOff + 256;        // [256] floats: column-half merge
+  static constexpr int kBytes = kXeOff + 1024 + 1024; // + alignment slack of the base
 };
 
 struct PlanTask {
@@ -58,6 +64,7 @@ struct PlanTask {
   const float* b;    // target weights
   const float* uinv; // per W column: c_d / 2^12
   float* Wp;         // [splits][rows][D + 2]
+  float* Ep;         // [splits][rows][2]: A_j, B_j of the KL term (or null)
   int* flag;
 };
 
@@ -228,6 +235,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     const int rloc = q * 32 + lane;
     bool ok = true;
     uint32_t qbits = 0;
+    float ent = 0.0f;   // sum over this warp's sources of q (out - 12)
     unsigned char* Ph = Ps + (h * 2 + 0) * L::kPBytes;
     unsigned char* Pl = Ps + (h * 2 + 1) * L::kPBytes;
     const uint32_t prow = static_cast<uint32_t>((rloc >> 3) * 1024 + (rloc & 7) * 128);
@@ -257,6 +265,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       for (int k = 0; k < 32; k += 2) {
         const float q0 = ex2(__uint_as_float(r[k]));
         const float q1 = ex2(__uint_as_float(r[k + 1]));
+        ent = fmaf(q0, __uint_as_float(r[k]) - kPlanShiftBias, ent);
+        ent = fmaf(q1, __uint_as_float(r[k + 1]) - kPlanShiftBias, ent);
         const uint32_t b0 = __float_as_uint(q0), b1 = __float_as_uint(q1);
         qbits = max(qbits, max(b0, b1));   // q > 0: bit order = value order (inf, NaN above)
         const float h0 = __uint_as_float(b0 & 0xFFFFE000u);
@@ -291,6 +301,15 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(pfull);
     }
+    // the two column halves of a target row merge their q (out - 12) sums
+    // (named barrier of the epilogue warps only; every one of them gets here)
+    {
+      float* xe = reinterpret_cast<float*>(smem + L::kXeOff);
+      const int slot = h * 128 + rloc;
+      if (ch == 1) xe[slot] = ent;
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kPlanEpiWarps) : "memory");
+      if (ch == 0) ent += xe[slot];
+    }
     // final W rows: one warp per (half, lane quarter) reads its 32 rows
     int got = 1;
     if (ok) {
@@ -317,6 +336,13 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
             const float v = __uint_as_float(d < 32 ? w0[d] : w1[d - 32]);
             out[d] = v * bj * T.uinv[d];
           }
+          if (T.Ep != nullptr) {
+            const int d = T.D + 2;   // the log a column
+            const float v = __uint_as_float(d < 32 ? w0[d] : w1[d - 32]);
+            float* e2 = T.Ep + (static_cast<int64_t>(sp) * T.rows + j) * 2;
+            e2[0] = ent * bj * (1.0f / kPlanQScale);
+            e2[1] = v * bj * T.uinv[d];
+          }
         }
       }
     }
@@ -334,30 +360,37 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
   }
 }
 
-// per W column d (X_d, then s, then 1): max |U_id| -> umax[d]
-__global__ void u_absmax_kernel(const float* X, const float* s, int64_t n, int D, unsigned* umax) {
+// per W column d (X_d, then s, then 1, then log a): max |U_id| -> umax[d]
+// (the constant column D + 1 needs none)
+__global__ void u_absmax_kernel(const float* X, const float* s, const float* loga, int64_t n, int D,
+                                unsigned* umax) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int d = 0; d < D + 1; ++d) {
+  for (int d = 0; d < D + 3; ++d) {
+    if (d == D + 1) continue;
     float v = 0.f;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
-      v = fmaxf(v, fabsf(d < D ? X[i * D + d] : s[i]));
+      v = fmaxf(v, fabsf(d < D ? X[i * D + d] : (d == D ? s[i] : (isfinite(loga[i]) ? loga[i] : 0.0f))));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) atomicMax(&umax[d], __float_as_uint(v));
   }
 }
 
-// Uh / Ul [NW][n_pad]: U_id / c_d split into f16 hi + lo; uinv[d] = c_d / 2^12
-__global__ void u_prep_kernel(const float* X, const float* s, int64_t n, int64_t n_pad, int D,
-                              int NW, const unsigned* umax, __half* Uh, __half* Ul, float* uinv) {
+// Uh / Ul [NW][n_pad]: U_id / c_d split into f16 hi + lo; uinv[d] = c_d / 2^12;
+// U = [X, s, 1, log a]
+__global__ void u_prep_kernel(const float* X, const float* s, const float* loga, int64_t n,
+                              int64_t n_pad, int D, int NW, const unsigned* umax, __half* Uh,
+                              __half* Ul, float* uinv) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= static_cast<int64_t>(NW) * n_pad) return;
   const int d = static_cast<int>(q / n_pad);
   const int64_t i = q % n_pad;
   float c = 1.0f;
-  if (d <= D) c = pow2_scale(__uint_as_float(umax[d]));
+  if (d <= D || d == D + 2) c = pow2_scale(__uint_as_float(umax[d]));
   float u = 0.0f;
-  if (i < n && d < D + 2) u = (d < D ? X[i * D + d] : (d == D ? s[i] : 1.0f)) / c;
+  if (i < n && d < D + 3)
+    u = (d < D ? X[i * D + d]
+               : (d == D ? s[i] : (d == D + 1 ? 1.0f : (isfinite(loga[i]) ? loga[i] : 0.0f)))) / c;
   const __half hi = __float2half_rn(u);
   Uh[q] = hi;
   Ul[q] = __float2half_rn(u - __half2float(hi));
@@ -378,7 +411,7 @@ int make_u_map(CUtensorMap* map, void* ptr, int64_t n_pad, int NW) {
   return GW_OK;
 }
 
-int plan_nw(int D) { return D + 2 <= 16 ? 16 : D + 2 <= 32 ? 32 : D + 2 <= 48 ? 48 : 64; }
+int plan_nw(int D) { return D + 3 <= 16 ? 16 : D + 3 <= 32 ? 32 : D + 3 <= 48 ? 48 : 64; }
 
 template <int KP, int S, int NW, bool BF16>
 int launch_plan(const CUtensorMap* maps, const PlanTask& T, int blocks, cudaStream_t st) {
@@ -448,6 +481,7 @@ struct PlanBufs {
   __half *Uh, *Ul;
   int* flag;
   float* Wp;
+  float* Ep;
 };
 
 PlanBufs carve_plan(Carver& c, int64_t n, int64_t m, int D, int prec) {
@@ -465,6 +499,7 @@ PlanBufs carve_plan(Carver& c, int64_t n, int64_t m, int D, int prec) {
   B.Ul = c.take<__half>(static_cast<size_t>(NW) * Lt.cols_pad);
   B.flag = c.take<int>(4);
   B.Wp = c.take<float>(static_cast<size_t>(Lt.splits) * m * (D + 2));
+  B.Ep = c.take<float>(static_cast<size_t>(Lt.splits) * m * 2);
   return B;
 }
 
@@ -472,7 +507,7 @@ PlanBufs carve_plan(Carver& c, int64_t n, int64_t m, int D, int prec) {
 
 bool plan_tc_supported(int D, int prec) {
   if (prec != GW_PREC_BF16 && prec != GW_PREC_BF16X3 && prec != GW_PREC_F16X3) return false;
-  return D + 2 <= 64 && tc_shape(D, prec).KP <= 128;
+  return D + 3 <= 64 && tc_shape(D, prec).KP <= 128;
 }
 
 size_t plan_tc_ws_bytes(int64_t n, int64_t m, int D, int prec) {
@@ -481,8 +516,9 @@ size_t plan_tc_ws_bytes(int64_t n, int64_t m, int D, int prec) {
   return c.used();
 }
 
-int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int* splits_out,
-                int* rows_per_split_out, int** flag_out, Carver& ws, cudaStream_t st) {
+int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, float** Ep_out,
+                int* splits_out, int* rows_per_split_out, int** flag_out, Carver& ws,
+                cudaStream_t st) {
   GW_REQUIRE(plan_tc_supported(p.D, prec), GW_EUNSUPPORTED, "tensor-core plan sums: D=%d prec=%d",
              p.D, prec);
   const TcOperandShape shp = tc_shape(p.D, prec);
@@ -522,12 +558,12 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int
         reinterpret_cast<__half*>(B.opB));
     GW_LAUNCH_CHECK();
   }
-  // U = [X, s, 1], feature-major, per-column power-of-two scales
+  // U = [X, s, 1, log a], feature-major, per-column power-of-two scales
   GW_CUDA_TRY(cudaMemsetAsync(B.umax, 0, 64 * sizeof(unsigned), st));
-  u_absmax_kernel<<<kSmCount, 256, 0, st>>>(p.X, p.s, p.n, p.D, B.umax);
+  u_absmax_kernel<<<kSmCount, 256, 0, st>>>(p.X, p.s, B.loga, p.n, p.D, B.umax);
   GW_LAUNCH_CHECK();
   u_prep_kernel<<<ceil_div(static_cast<int64_t>(NW) * Lt.cols_pad, 256), 256, 0, st>>>(
-      p.X, p.s, p.n, Lt.cols_pad, p.D, NW, B.umax, B.Uh, B.Ul, B.uinv);
+      p.X, p.s, B.loga, p.n, Lt.cols_pad, p.D, NW, B.umax, B.Uh, B.Ul, B.uinv);
   GW_LAUNCH_CHECK();
   CUtensorMap maps[4];
   GW_TRY(make_map(&maps[0], B.opA, Lt.rows_pad, shp.KP, bf16, 128));
@@ -544,6 +580,7 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int
   T.b = p.b;
   T.uinv = B.uinv;
   T.Wp = B.Wp;
+  T.Ep = Ep_out ? B.Ep : nullptr;
   T.flag = B.flag;
   T.wc = wait_ctl();
   const int blocks = Lt.row_tiles * Lt.splits;
@@ -557,6 +594,7 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, int
   }
   GW_TRY(rc);
   *Wp_out = B.Wp;
+  if (Ep_out) *Ep_out = B.Ep;
   *splits_out = Lt.splits;
   *rows_per_split_out = Lt.tiles_per_split * kPlanBN;
   *flag_out = B.flag;

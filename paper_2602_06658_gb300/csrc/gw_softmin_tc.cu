@@ -60,6 +60,8 @@ constexpr float kSumHi = 1.3292280e36f;      // 2^120: a sum above this (or inf/
 
 struct TcTask {
   tc::WaitCtl wc;         // pipeline wait limit and the give-up counter
+  const int* gate;        // layout decision (device); the launch runs only when
+  int gate_on;            // *gate == gate_on (gate null: always)
   int64_t n, m;           // real rows / columns
   int ksteps;             // MMA K-steps of 16 that hold non-zero operand columns
   const float* est;       // per-row shift estimate (fast pass), or null
@@ -200,6 +202,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const int tile0 = sp * T.tiles_per_split;
   const int ntiles = min(T.tiles_per_split, T.col_tiles - tile0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the operands are in the other layout: that launch does the work
+  if (T.gate != nullptr && *T.gate != T.gate_on) return;
   // the safe pass only recomputes the row tiles the fast pass marked
   if (!FAST && T.flags != nullptr && T.flags[rt] == 0) return;
 
@@ -400,6 +404,47 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   }
 }
 
+// Per-dim maxima of |A_ik| -> out[k] (block: 128 x 2 threads, k = x).
+__global__ void tc_dimmax_kernel(const float* A, int64_t n, int K, unsigned* out) {
+  const int k = threadIdx.x;
+  if (k >= K) return;
+  float v = 0.0f;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.y)
+    v = fmaxf(v, fabsf(A[i * K + k]));
+  atomicMax(&out[k], __float_as_uint(v));
+}
+
+// Layout decision of the split precisions (one block of 128 threads):
+// P_k = max|A_k| max|B_k| bounds every product of dim k; the dims are ordered
+// by P_k (largest first, ties by index) into lay[2 .. 2 + K), and lay[0] = 1
+// (the narrow layout) when at most ks_max dims have P_k above tau max P: the
+// others then run as one product within the split products' error bound.
+__global__ void tc_layout_kernel(const unsigned* mxA, const unsigned* mxB, int K, float tau,
+                                 int ks_max, int* lay) {
+  __shared__ float P[128];
+  const int k = threadIdx.x;
+  float pk = -1.0f;
+  if (k < K) {
+    pk = __uint_as_float(mxA[k]) * __uint_as_float(mxB[k]);
+    if (!(pk == pk)) pk = -1.0f;   // NaN sorts last
+  }
+  P[k] = pk;
+  __syncthreads();
+  float pmax = 0.0f;
+  for (int j = 0; j < K; ++j) pmax = fmaxf(pmax, P[j]);
+  const int big = __syncthreads_count(k < K && pk > tau * pmax);
+  if (k < K) {
+    int rank = 0;
+    for (int j = 0; j < K; ++j) rank += (P[j] > pk || (P[j] == pk && j < k)) ? 1 : 0;
+    lay[2 + rank] = k;
+  }
+  if (k == 0) {
+    lay[0] = big <= ks_max ? 1 : 0;
+    lay[1] = big;
+  }
+}
+
 // Merge split partials.  mode 0: every row; mode 1 (after the fast pass):
 // rows of unflagged tiles whose total is in range are written, the others
 // flag their tile; mode 2 (after the safe pass): rows of flagged tiles only.
@@ -501,6 +546,12 @@ bool softmin_tc_supported(int K, int prec) {
   return tc_shape(K, prec).KP <= 256;
 }
 
+// The narrow split layout is tried for the split precisions when the full
+// layout needs 192 or more operand columns (K >= 40): it holds the dims of
+// largest product bound as three products and the rest as one, in 128 columns.
+constexpr int kNarrowKP = 128;
+bool narrow_enabled(const TcOperandShape& f) { return f.mult == 3 && f.KP >= 192; }
+
 size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
   const TcOperandShape shp = tc_shape(K, prec);
   const int64_t n_pad = ((n + kBM - 1) / kBM) * kBM;
@@ -515,24 +566,37 @@ size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
   c.take<float>(static_cast<size_t>(s) * n);
   c.take<float>(static_cast<size_t>(s) * n);
   c.take<int>(static_cast<size_t>(n_pad / kBM));       // recompute flags per row tile
+  if (narrow_enabled(shp)) {
+    c.take<unsigned>(256);                             // per-dim maxima of A and B
+    c.take<int>(2 + 128);                              // layout decision
+  }
   c.take<float>(static_cast<size_t>(2 * 2 * kSmCount));  // per-block maxima of the refresh
   return c.used();
 }
 
 // Prepare operands for one or two tasks and launch the tensor-core kernel.
 // Fills tasks[q].splits / pm / ps so the caller can merge split partials.
+// For K >= 40 in the split precisions both layouts are launched: the narrow
+// one (tc_shape_split, 128 columns) and the full one; the device's layout
+// decision (tc_layout_kernel, made from the first task's maxima when the
+// operands are prepared) lets exactly one of them run, the other returns at
+// once.  Both use the same column splits, so their partials merge alike.
 int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cudaStream_t st) {
   GW_REQUIRE(softmin_tc_supported(tasks[0].K, prec), GW_EUNSUPPORTED,
              "tensor-core softmin does not support K=%d with precision %d", tasks[0].K, prec);
   const bool bf16 = tc_is_bf16(prec);
-  CUtensorMap maps[4];
-  TcTask tt[2];
+  CUtensorMap maps[4], maps_a[4];
+  TcTask tt[2], ta[2];
   memset(tt, 0, sizeof(tt));
+  memset(ta, 0, sizeof(ta));
   const TcOperandShape shp = tc_shape(tasks[0].K, prec);
+  const bool narrow = narrow_enabled(shp);
+  const TcOperandShape shp_a = narrow ? tc_shape_split(tasks[0].K, prec, kNarrowKP) : shp;
+  const int bn_f = tile_cols(shp.KP), bn_a = tile_cols(kNarrowKP);
   int row_tiles[2] = {0, 0}, col_tiles[2] = {0, 0};
   for (int q = 0; q < ntasks; ++q) {
     row_tiles[q] = ceil_div(tasks[q].n, kBM);
-    col_tiles[q] = ceil_div(tasks[q].m, tile_cols(shp.KP));
+    col_tiles[q] = ceil_div(tasks[q].m, bn_f);
   }
   // the fast pass needs an estimate for every task (not aliased to the output)
   bool all_est = true;
@@ -542,18 +606,24 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
   const int splits = tc_splits(row_tiles[0], col_tiles[0], ntasks == 2 ? row_tiles[1] : 0);
   RefreshTask refresh[2];
   memset(refresh, 0, sizeof(refresh));
+  int* lay = nullptr;
   for (int q = 0; q < ntasks; ++q) {
     SoftminTask& T = tasks[q];
     const int64_t n_pad = static_cast<int64_t>(row_tiles[q]) * kBM;
-    const int64_t m_pad = static_cast<int64_t>(col_tiles[q]) * tile_cols(shp.KP);
+    const int64_t m_pad = static_cast<int64_t>(col_tiles[q]) * bn_f;
+    const int col_tiles_a = ceil_div(T.m, bn_a);
+    const int64_t m_pad_a = static_cast<int64_t>(col_tiles_a) * bn_a;
     uint16_t* opA = ws.take<uint16_t>(static_cast<size_t>(n_pad) * shp.KP);
     uint16_t* opB = ws.take<uint16_t>(static_cast<size_t>(m_pad) * shp.KP);
     unsigned* mx = ws.take<unsigned>(8);
     int s = splits < col_tiles[q] ? splits : col_tiles[q];
-    const int tps = ceil_div(col_tiles[q], s);
+    int tps = ceil_div(col_tiles[q], s);
+    // the narrow layout's tiles are bn_a / bn_f full tiles wide: an even
+    // count of full tiles per split gives both layouts the same splits
+    if (narrow && bn_a != bn_f && (tps % 2) != 0) tps += 1;
     s = ceil_div(col_tiles[q], tps);
     T.splits = s;
-    T.cols_per_split = tps * tile_cols(shp.KP);
+    T.cols_per_split = tps * bn_f;
     T.pm = T.ps = nullptr;
     if (s > 1) {
       T.pm = ws.take<float>(static_cast<size_t>(s) * T.n);
@@ -561,7 +631,15 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     }
     const bool use_est = all_est;
     int* flags = ws.take<int>(static_cast<size_t>(row_tiles[q]));
+    unsigned* mxd = nullptr;
+    if (narrow && q == 0) {
+      mxd = ws.take<unsigned>(256);
+      lay = ws.take<int>(2 + 128);
+    }
     GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
+    const int tps_a = narrow ? tps * bn_f / bn_a : tps;
+    GW_REQUIRE(!narrow || ceil_div(col_tiles_a, tps_a) == s, GW_ECUDA,
+               "internal: split layouts disagree (%d tiles, %d per split)", col_tiles_a, tps_a);
     const float inv_eps = 1.0f / T.eps;
     if (T.reuse_ops) {
       // main, rank-one and mask columns are unchanged: the bias and shift
@@ -569,37 +647,51 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
       refresh[q] = RefreshTask{T.h, T.logw, use_est ? T.est : nullptr, T.n, T.m, inv_eps, flags,
                                row_tiles[q], opA, opB};
     } else {
-    GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q], st));
-    GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 8 * sizeof(unsigned), st));
-    tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
-                                                   T.sB, T.m, T.h, T.logw,
-                                                   use_est ? T.est : nullptr, inv_eps, mx);
-    GW_LAUNCH_CHECK();
-    const float alpha = 16.0f * kLog2e * inv_eps;
-    const float beta = 4.0f * kLog2e * inv_eps;
-    dim3 blk(64, 4);
-    if (bf16) {
-      tc_prep_kernel<__nv_bfloat16><<<ceil_div(n_pad, 4), blk, 0, st>>>(
-          T.A, T.sA, nullptr, nullptr, use_est ? T.est : nullptr, T.n, n_pad, shp, 0, alpha, beta,
-          inv_eps, mx, reinterpret_cast<__nv_bfloat16*>(opA));
+      GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q], st));
+      GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 8 * sizeof(unsigned), st));
+      tc_absmax_kernel<<<2 * kSmCount, 256, 0, st>>>(T.A, T.n * T.K, T.B, T.m * T.K, T.sA, T.n,
+                                                     T.sB, T.m, T.h, T.logw,
+                                                     use_est ? T.est : nullptr, inv_eps, mx);
       GW_LAUNCH_CHECK();
-      tc_prep_kernel<__nv_bfloat16><<<ceil_div(m_pad, 4), blk, 0, st>>>(
-          T.B, T.sB, T.h, T.logw, nullptr, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
-          reinterpret_cast<__nv_bfloat16*>(opB));
-      GW_LAUNCH_CHECK();
-    } else {
-      tc_prep_kernel<__half><<<ceil_div(n_pad, 4), blk, 0, st>>>(
-          T.A, T.sA, nullptr, nullptr, use_est ? T.est : nullptr, T.n, n_pad, shp, 0, alpha, beta,
-          inv_eps, mx, reinterpret_cast<__half*>(opA));
-      GW_LAUNCH_CHECK();
-      tc_prep_kernel<__half><<<ceil_div(m_pad, 4), blk, 0, st>>>(
-          T.B, T.sB, T.h, T.logw, nullptr, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
-          reinterpret_cast<__half*>(opB));
-      GW_LAUNCH_CHECK();
-    }
+      if (mxd != nullptr) {
+        // the layout decision, from this task's per-dim maxima (the other
+        // task's are the same products with the roles exchanged)
+        GW_CUDA_TRY(cudaMemsetAsync(mxd, 0, 256 * sizeof(unsigned), st));
+        tc_dimmax_kernel<<<kSmCount, dim3(128, 2), 0, st>>>(T.A, T.n, T.K, mxd);
+        GW_LAUNCH_CHECK();
+        tc_dimmax_kernel<<<kSmCount, dim3(128, 2), 0, st>>>(T.B, T.m, T.K, mxd + 128);
+        GW_LAUNCH_CHECK();
+        tc_layout_kernel<<<1, 128, 0, st>>>(mxd, mxd + 128, T.K, split_threshold(prec),
+                                            shp_a.Ks, lay);
+        GW_LAUNCH_CHECK();
+      }
+      const float alpha = 16.0f * kLog2e * inv_eps;
+      const float beta = 4.0f * kLog2e * inv_eps;
+      const int64_t mrows = m_pad > m_pad_a ? m_pad : m_pad_a;
+      dim3 blk(64, 4);
+      if (bf16) {
+        tc_prep_kernel<__nv_bfloat16><<<ceil_div(n_pad, 4), blk, 0, st>>>(
+            T.A, T.sA, nullptr, nullptr, use_est ? T.est : nullptr, T.n, n_pad, shp, 0, alpha,
+            beta, inv_eps, mx, reinterpret_cast<__nv_bfloat16*>(opA), kShiftBias, lay, shp_a,
+            n_pad);
+        GW_LAUNCH_CHECK();
+        tc_prep_kernel<__nv_bfloat16><<<ceil_div(mrows, 4), blk, 0, st>>>(
+            T.B, T.sB, T.h, T.logw, nullptr, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
+            reinterpret_cast<__nv_bfloat16*>(opB), kShiftBias, lay, shp_a, m_pad_a);
+        GW_LAUNCH_CHECK();
+      } else {
+        tc_prep_kernel<__half><<<ceil_div(n_pad, 4), blk, 0, st>>>(
+            T.A, T.sA, nullptr, nullptr, use_est ? T.est : nullptr, T.n, n_pad, shp, 0, alpha,
+            beta, inv_eps, mx, reinterpret_cast<__half*>(opA), kShiftBias, lay, shp_a, n_pad);
+        GW_LAUNCH_CHECK();
+        tc_prep_kernel<__half><<<ceil_div(mrows, 4), blk, 0, st>>>(
+            T.B, T.sB, T.h, T.logw, nullptr, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
+            reinterpret_cast<__half*>(opB), kShiftBias, lay, shp_a, m_pad_a);
+        GW_LAUNCH_CHECK();
+      }
     }
     GW_TRY(make_map(&maps[2 * q], opA, n_pad, shp.KP, bf16, 128));
-    GW_TRY(make_map(&maps[2 * q + 1], opB, m_pad, shp.KP, bf16, tile_cols(shp.KP)));
+    GW_TRY(make_map(&maps[2 * q + 1], opB, m_pad, shp.KP, bf16, bn_f));
     TcTask& K = tt[q];
     K.n = T.n;
     K.m = T.m;
@@ -617,6 +709,22 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     K.pm = T.pm;
     K.ps = T.ps;
     K.wc = wait_ctl();
+    K.gate = nullptr;
+    K.gate_on = 0;
+    if (narrow) {
+      // the narrow layout over the same buffers (its rows are kNarrowKP wide)
+      GW_TRY(make_map(&maps_a[2 * q], opA, n_pad, kNarrowKP, bf16, 128));
+      GW_TRY(make_map(&maps_a[2 * q + 1], opB, m_pad_a, kNarrowKP, bf16, bn_a));
+      TcTask& A = ta[q];
+      A = K;
+      A.ksteps = (shp_a.used + 15) / 16;
+      A.col_tiles = col_tiles_a;
+      A.tiles_per_split = tps_a;
+      A.gate = lay;
+      A.gate_on = 1;
+      K.gate = lay;
+      K.gate_on = 0;
+    }
   }
   if (tasks[0].reuse_ops) {
     float* part = ws.take<float>(static_cast<size_t>(2 * 2 * kSmCount));
@@ -627,10 +735,10 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     for (int q = 0; q < ntasks; ++q) rows += refresh[q].n + refresh[q].m;
     if (bf16) {
       tc_refresh_multi_kernel<__nv_bfloat16><<<ceil_div(rows, 256), 256, 0, st>>>(
-          refresh[0], refresh[1], ntasks, shp, part, kSmCount);
+          refresh[0], refresh[1], ntasks, shp, part, kSmCount, lay, shp_a);
     } else {
       tc_refresh_multi_kernel<__half><<<ceil_div(rows, 256), 256, 0, st>>>(
-          refresh[0], refresh[1], ntasks, shp, part, kSmCount);
+          refresh[0], refresh[1], ntasks, shp, part, kSmCount, lay, shp_a);
     }
     GW_LAUNCH_CHECK();
   }
@@ -639,16 +747,26 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     maps[3] = maps[1];
     tt[1] = tt[0];
     tt[1].blocks = 0;
+    maps_a[2] = maps_a[0];
+    maps_a[3] = maps_a[1];
+    ta[1] = ta[0];
+    ta[1].blocks = 0;
   }
+  // one pass in the layout the device chose (the other launch returns at once)
+  auto pass = [&](bool fast) -> int {
+    if (narrow) GW_TRY(run_tc(bf16, fast, kNarrowKP, maps_a, ta[0], ta[1], st));
+    return run_tc(bf16, fast, shp.KP, maps, tt[0], tt[1], st);
+  };
   if (!all_est) {
     // no usable estimate: one safe pass over every CTA
     tt[0].flags = tt[1].flags = nullptr;
-    GW_TRY(run_tc(bf16, false, shp.KP, maps, tt[0], tt[1], st));
+    ta[0].flags = ta[1].flags = nullptr;
+    GW_TRY(pass(false));
     return run_combine(tt[0], tt[1], 0, st);
   }
-  GW_TRY(run_tc(bf16, true, shp.KP, maps, tt[0], tt[1], st));
+  GW_TRY(pass(true));
   GW_TRY(run_combine(tt[0], tt[1], 1, st));
-  GW_TRY(run_tc(bf16, false, shp.KP, maps, tt[0], tt[1], st));
+  GW_TRY(pass(false));
   return run_combine(tt[0], tt[1], 2, st);
 }
 

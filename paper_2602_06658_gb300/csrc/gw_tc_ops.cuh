@@ -27,6 +27,7 @@ constexpr float kShiftBias = 30.0f;          // fast-pass shift sits this far be
 struct TcOperandShape {
   int K;        // feature dimension
   int mult;     // 1 or 3 products in the dot
+  int Ks;       // mult == 3: dims taken as three products (the rest as one)
   int KP;       // padded operand width
   int col_u;    // first rank-one column
   int col_w;    // first column-bias column
@@ -39,6 +40,7 @@ TcOperandShape tc_shape(int K, int prec) {
   TcOperandShape s;
   s.K = K;
   s.mult = prec == GW_PREC_BF16 ? 1 : 3;
+  s.Ks = K;
   s.col_u = s.mult * K;
   s.col_w = s.col_u + 3;
   s.col_e = s.col_w + 3;
@@ -46,6 +48,33 @@ TcOperandShape tc_shape(int K, int prec) {
   s.used = s.col_k + 1;
   s.KP = ((s.used + 63) / 64) * 64;
   return s;
+}
+
+// Split layout of a fixed width KP for the split precisions: the Ks dims of
+// largest product bound as three products, the other K - Ks as one product
+// (the most dims KP holds beside the 10 bias, shift and mask columns).
+TcOperandShape tc_shape_split(int K, int prec, int KP) {
+  TcOperandShape s = tc_shape(K, prec);
+  int ks = (KP - 10 - K) / 2;
+  if (ks > K) ks = K;
+  if (ks < 0) ks = 0;
+  s.Ks = ks;
+  s.col_u = 3 * ks + (K - ks);
+  s.col_w = s.col_u + 3;
+  s.col_e = s.col_w + 3;
+  s.col_k = s.col_e + 3;
+  s.used = s.col_k + 1;
+  s.KP = KP;
+  return s;
+}
+
+// Relative error of a single 16-bit product X_k V_k (both operands rounded
+// once): 2^-10 in f16, 2^-7 in bf16.  A dim may run as one product when its
+// bound P_k = max|X_k| max|V_k| is at most TERM_REL / single_rel times the
+// largest P: its error then stays below TERM_REL times the largest term, the
+// bound the split products keep (2^-20 for F16X3, 2^-15 for BF16X3).
+__host__ __device__ inline float split_threshold(int prec) {
+  return prec == GW_PREC_F16X3 ? 9.765625e-04f /* 2^-10 */ : 3.90625e-03f /* 2^-8 */;
 }
 
 bool tc_is_bf16(int prec) { return prec != GW_PREC_F16X3; }
@@ -126,12 +155,20 @@ __device__ __forceinline__ void balance(float prod, float mxa, float mxb, float*
 // Operand rows.  role 0 = A side (row operand), role 1 = B side (column
 // operand, bias columns included).  Rows >= rows_valid are padding: zeros,
 // and for the B side a bias of -65504 * kBiasConst so they add nothing.
+// With `lay` (the device's layout decision, tc_layout_kernel) and lay[0] set,
+// the rows take the split layout shp_a (dims in the order lay[2..]) padded to
+// rows_pad_a; otherwise shp padded to rows_pad.
 template <class T>
 __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, const float* logw,
-                               const float* est, int64_t rows_valid, int64_t rows_pad,
-                               TcOperandShape shp, int role, float alpha, float beta,
+                               const float* est, int64_t rows_valid, int64_t rows_pad_f,
+                               TcOperandShape shp_f, int role, float alpha, float beta,
                                float inv_eps, const unsigned* mx, T* op,
-                               float shift_bias = kShiftBias) {
+                               float shift_bias = kShiftBias, const int* lay = nullptr,
+                               TcOperandShape shp_a = TcOperandShape{}, int64_t rows_pad_a = 0) {
+  const bool ad = lay != nullptr && lay[0] != 0;
+  const TcOperandShape shp = ad ? shp_a : shp_f;
+  const int64_t rows_pad = ad ? rows_pad_a : rows_pad_f;
+  const int* perm = ad ? lay + 2 : nullptr;
   const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
   if (r >= rows_pad) return;
   const float mA = __uint_as_float(mx[0]), mB = __uint_as_float(mx[1]);
@@ -150,11 +187,21 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
     float v = 0.0f;
     if (valid) {
       if (k < shp.col_u) {
-        const int part = k / K, kk = k % K;
+        // three-product dims: slots [0, Ks) as parts 0, 1, 2; one-product
+        // dims after them (mult 1: every dim once)
+        const int Ks = shp.mult == 3 ? shp.Ks : 0;
+        int part = 0, slot = k;
+        if (k < 3 * Ks) {
+          part = k / Ks;
+          slot = k % Ks;
+        } else {
+          slot = Ks + (k - 3 * Ks);
+        }
+        const int kk = perm ? perm[slot] : slot;
         const float x = X[r * K + kk] * sc;
         const float hi = from16(to16<T>(x));
         // A side [hi, hi, lo], B side [hi, lo, hi]: hi*hi + hi*lo + lo*hi
-        const bool lo = shp.mult == 3 && ((role == 0 && part == 2) || (role == 1 && part == 1));
+        const bool lo = k < 3 * Ks && ((role == 0 && part == 2) || (role == 1 && part == 1));
         v = lo ? x - hi : hi;
       } else if (k < shp.col_w) {
         const int part = k - shp.col_u;
@@ -248,7 +295,10 @@ __global__ void tc_refresh_max_kernel(RefreshTask t0, RefreshTask t1, int ntasks
 
 template <class T>
 __global__ void tc_refresh_multi_kernel(RefreshTask t0, RefreshTask t1, int ntasks,
-                                        TcOperandShape shp, const float* part, int nparts) {
+                                        TcOperandShape shp_f, const float* part, int nparts,
+                                        const int* lay = nullptr,
+                                        TcOperandShape shp_a = TcOperandShape{}) {
+  const TcOperandShape shp = (lay != nullptr && lay[0] != 0) ? shp_a : shp_f;
   __shared__ float cw[2], ce[2];
   if (threadIdx.x < 32) {
     for (int q = 0; q < ntasks; ++q) {

@@ -157,28 +157,36 @@ def test_batch_rejects_what_it_cannot_hold(gw):
     assert e.value.code == 6
 
 
-def test_exact_fallback_when_the_shift_is_far_off(gw):
-    """Unit-scale features: in the first iteration (f = g = 0) the shifted
-    sums overflow (beta s_i t_j reaches ~1e3 in base 2 at eps = 0.05), so
-    the entries go through the exact running-max form; the outer step (the
-    one that starts from f = g = 0) still matches gw_solve's FP32 path, in
-    energy and potentials.  Later outer steps of this data are not compared:
-    with s t up to ~9 the energy falls from ~26 to ~13 in three unconverged
-    outer steps and the Gamma updates amplify FP32 differences (4e-4 between
-    the two FP32 paths); at eps = 0.005 even the first step differs by 0.2%."""
+@pytest.mark.parametrize("eps", [0.05, 0.005])
+def test_exact_fallback_when_the_shift_is_far_off(gw, eps):
+    """Unit-scale features: in the first iterations (f = g = 0) the shifted
+    sums overflow (beta s_i t_j reaches ~1e3 in base 2 at eps = 0.05), so the
+    entries go through the exact running-max form.  Over the whole schedule
+    (3 outer steps of 40 iterations) both FP32 paths, the batched solver and
+    gw_solve, are held to the FP64 oracle: per outer step within the larger
+    of the 1e-4 bar and the energy spread of the oracle's own solve under
+    fresh noise at the FP32 exponent's per-cell error bound
+    (helpers.noisy_cnt_gw, three seeds).  With s t up to ~9 these unconverged
+    steps are sensitive to that noise: the spread reaches ~3e-3 at eps = 0.05
+    and ~5e-2 at eps = 0.005."""
+    from helpers import noisy_cnt_gw
     probs = [random_problem(n, m, 3, 3, seed=500 + n, scale=1.0) for n, m in [(120, 90), (64, 200)]]
     packed = gw.pack_problems(probs)
-    out = gw.gw_solve_batch(packed, 0.05, 1, 40, record=True)
+    out = gw.gw_solve_batch(packed, eps, 3, 40, record=True)
     hist = host(out["history"])
-    fs, gs = split(packed, out["f"], "x"), split(packed, out["g"], "y")
     for q, P in enumerate(probs):
         s_max, t_max = P["s"].max(), P["t"].max()
         assert 4.0 / 0.05 * np.log2(np.e) * s_max * t_max > 200.0   # the shift starts far off
-        ref = solve_alone(gw, P, 0.05, 1, 40)
-        rh = host(ref["history"])
+        ref = O.cnt_gw(P["a"], P["b"], P["X"], P["Y"], eps, 3, 40, symmetric=True)
+        E0 = np.array([h["E"] for h in ref["history"]])
+        spread = np.zeros(3)
+        for seed in (1, 2, 3):
+            h = noisy_cnt_gw(P["a"], P["b"], P["X"], P["Y"], eps, 3, 40, 0, seed)
+            spread = np.maximum(spread, np.abs(np.array([r["E"] for r in h]) - E0) / np.abs(E0))
+        bound = np.maximum(1e-4, spread)
+        rh = host(solve_alone(gw, P, eps, 3, 40)["history"])
         assert np.all(hist[q, :, gw.EN["status"]] == 0), q
-        assert np.all(np.abs(hist[q, :, gw.EN["E"]] - rh[:, gw.EN["E"]])
-                      <= 5e-5 * np.abs(rh[:, gw.EN["E"]]) + 1e-9), (q, hist[q, :, 0], rh[:, 0])
-        fr, gr = host(ref["f"]), host(ref["g"])
-        assert np.abs(fs[q] - fr).max() <= 1e-4 * (np.abs(fr).max() + 0.05), q
-        assert np.abs(gs[q] - gr).max() <= 1e-4 * (np.abs(gr).max() + 0.05), q
+        rel_b = np.abs(hist[q, :, gw.EN["E"]] - E0) / np.abs(E0)
+        rel_s = np.abs(rh[:, gw.EN["E"]] - E0) / np.abs(E0)
+        assert np.all(rel_b <= bound), (q, rel_b, bound)
+        assert np.all(rel_s <= bound), (q, rel_s, bound)

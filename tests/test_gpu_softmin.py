@@ -215,3 +215,72 @@ def test_sinkhorn_iteration_matches_oracle_and_reuse(gw, prec, symmetric):
                                       f32(g), eps, prec=prec, symmetric=symmetric, reuse=True,
                                       ws=ws)
     assert bool((fr == fo).all()) and bool((gr == go).all())
+
+
+def decaying_inputs(n, m, K, seed, eps):
+    """Features with a decaying spectrum, as Kernel PCA features and
+    V = Gamma Y have: A_k ~ (k + 1)^-1.5, B_k ~ (k + 1)^-3."""
+    g = W.rng(seed)
+    k = np.arange(K) + 1.0
+    A = 0.6 * g.standard_normal((n, K)) * k ** -1.5
+    B = 0.3 * g.standard_normal((m, K)) * k ** -3.0
+    sA, sB = (A * A).sum(1), (B * B).sum(1)
+    h = 0.05 * g.standard_normal(m)
+    logw = np.log(W.random_weights(m, seed + 1))
+    r = lambda x: np.asarray(x, np.float32).astype(np.float64)
+    return r(A), r(B), r(sA), r(sB), r(h), r(logw)
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("K", [48, 64])
+@pytest.mark.parametrize("eps", [0.5, 0.02])
+def test_tensor_core_narrow_layout_matches_oracle(gw, prec, K, eps):
+    """K >= 40 in the split precisions: with a decaying spectrum only the few
+    dims of largest product bound need three products, so the 128-column
+    layout runs (the rest as one product each).  Ragged sizes, a far-off
+    estimate on some rows (safe pass) and the bound of helpers
+    (softmin_tolerance_prec, which adds the one-product dims' error)."""
+    from helpers import softmin_tolerance_prec
+    n, m = 2051, 1537
+    A, B, sA, sB, h, logw = decaying_inputs(n, m, K, seed=K + 3, eps=eps)
+    ref = oracle_softmin(A, B, sA, sB, h, logw, eps)
+    g = W.rng(5)
+    prev = ref + np.where(g.random(n) < 0.03, 300.0 * eps, 0.01 * eps)
+    prev = np.asarray(prev, np.float32).astype(np.float64)
+    out = gw.gw_sinkhorn_softmin(f32(A), f32(B), f32(sA), f32(sB), f32(h), f32(logw), eps,
+                                 prec=prec, avg_with=f32(prev))
+    want = 0.5 * (prev + ref)
+    tol = 0.5 * softmin_tolerance_prec(A, B, sA, sB, h, logw, eps, prec) + 1e-7 * np.abs(want)
+    err = np.abs(host(out) - want)
+    assert np.all(err <= tol), (prec, K, err.max(), np.argmax(err - tol))
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_narrow_layout_iteration_and_reuse(gw, prec):
+    """The fused iteration (both half-steps, both tasks in one launch) at
+    K = 64 with decaying spectra, and the per-iteration refresh of the bias
+    and shift columns in the narrow layout (reuse = 1 equals a fresh
+    preparation bitwise)."""
+    from helpers import softmin_tolerance_prec
+    n, m, K, eps = 1500, 1300, 64, 0.05
+    A, B, sA, sB, _, _ = decaying_inputs(n, m, K, seed=11, eps=eps)
+    g0 = W.rng(6)
+    la = np.log(np.asarray(W.random_weights(n, 7), np.float32)).astype(np.float64)
+    lb = np.log(np.asarray(W.random_weights(m, 8), np.float32)).astype(np.float64)
+    f = np.asarray(0.05 * g0.standard_normal(n), np.float32).astype(np.float64)
+    g = np.asarray(0.05 * g0.standard_normal(m), np.float32).astype(np.float64)
+    fo, go = gw.gw_sinkhorn_iteration(f32(A), f32(B), f32(sA), f32(sB), f32(la), f32(lb), f32(f),
+                                      f32(g), eps, prec=prec)
+    C = -16.0 * A @ B.T - 4.0 * np.outer(sA, sB)
+    want_f = 0.5 * (f + O.softmin(eps, lb, g, C))
+    want_g = 0.5 * (g + O.softmin(eps, la, f, C.T))
+    tol_f = 0.5 * softmin_tolerance_prec(A, B, sA, sB, g, lb, eps, prec) + 1e-7 * np.abs(want_f)
+    tol_g = 0.5 * softmin_tolerance_prec(B, A, sB, sA, f, la, eps, prec) + 1e-7 * np.abs(want_g)
+    assert np.all(np.abs(host(fo) - want_f) <= tol_f)
+    assert np.all(np.abs(host(go) - want_g) <= tol_g)
+    ws = gw.workspace(gw.gw_workspace_size(gw.OP_ITERATION, n, m, K, 1, prec), "cuda")
+    gw.gw_sinkhorn_iteration(f32(A), f32(B), f32(sA), f32(sB), f32(la), f32(lb), f32(0.5 * f),
+                             f32(-g), eps, prec=prec, ws=ws)
+    fr, gr = gw.gw_sinkhorn_iteration(f32(A), f32(B), f32(sA), f32(sB), f32(la), f32(lb), f32(f),
+                                      f32(g), eps, prec=prec, reuse=True, ws=ws)
+    assert bool((fr == fo).all()) and bool((gr == go).all())
