@@ -4,12 +4,19 @@ Kernel PCA to D = 32, eps geometric 0.1 -> 1e-3 over 20 outer x 100
 symmetric Sinkhorn iterations) at N = M = 1000, where the oracle solves it
 in about a minute.  The features come from the oracle's own Kernel PCA.
 
-The energy's relative error per outer step, measured once and asserted here
-as the statement: FP32 stays within 1e-4 (the parity bar) while eps >= 2.5e-3
-and F16X3 within 2e-4; at the end of the schedule (eps down to 1e-3, where
-the O(1) terms of E cancel to ~6e-3 and 100 iterations no longer converge
-Sinkhorn) both reach ~2.5e-3, and 5e-3 bounds them.
+The bound of each outer step is the larger of the 1e-4 parity bar and the
+energy spread the precision's arithmetic implies for this solve:
+tests/golden/accuracy_spread.json, written by make_accuracy_spread.py from
+the oracle alone (its solve with fresh noise at the per-cell error bound of
+the precision's exponent, helpers.noisy_cnt_gw, three seeds).  Down to
+eps ~ 3e-3 that spread is below the bar; at the end of the schedule (eps
+1.6e-3 .. 1e-3, 100 iterations far from Sinkhorn convergence, O(1) terms of
+E cancelling to ~6e-3) FP32-level exponent noise alone moves the oracle's
+energy by up to ~1e-2, and the GPU is held to that.
 """
+
+import json
+import os
 
 import numpy as np
 import pytest
@@ -21,6 +28,8 @@ from helpers import f32, host
 pytestmark = pytest.mark.gpu
 
 r32 = lambda x: np.asarray(x, np.float32).astype(np.float64)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "accuracy_spread.json")
 
 
 @pytest.fixture(scope="module")
@@ -32,12 +41,19 @@ def annealed_case():
     Y = r32(O.lift(w["y"], a, "power", 1.0, D=D)["X"])
     a = r32(a)
     ref = O.cnt_gw(a, a, X, Y, 0.1, 20, 100, eps_final=1e-3, symmetric=True)
-    return X, Y, a, ref
+    with open(GOLDEN) as fh:
+        spread = json.load(fh)
+    return X, Y, a, ref, spread
 
 
-@pytest.mark.parametrize("prec,early", [(0, 1e-4), (3, 2e-4)])
-def test_annealed_energy_error_statement(gw, annealed_case, prec, early):
-    X, Y, a, ref = annealed_case
+@pytest.mark.parametrize("prec,name", [(0, "fp32"), (3, "f16x3")])
+def test_annealed_energy_error_statement(gw, annealed_case, prec, name):
+    X, Y, a, ref, spread = annealed_case
+    E_golden = np.array(spread["E_oracle"])
+    E_ref = np.array([r["E"] for r in ref["history"]])
+    # the stored spread belongs to this very solve
+    assert np.allclose(E_ref, E_golden, rtol=1e-7, atol=0)
+    bound = np.maximum(1e-4, np.array(spread["spread"][name]["max"]))
     s, t = r32((X * X).sum(1)), r32((Y * Y).sum(1))
     out = gw.gw_solve(f32(X), f32(Y), f32(s), f32(t), f32(a), f32(a), 0.1, 20, 100,
                       eps_final=1e-3, prec=prec, record=True)
@@ -45,6 +61,5 @@ def test_annealed_energy_error_statement(gw, annealed_case, prec, early):
     assert np.all(h[:, gw.EN["status"]] == 0)
     for k, r in enumerate(ref["history"]):
         rel = abs(h[k, gw.EN["E"]] - r["E"]) / abs(r["E"])
-        bound = early if r["eps"] >= 2.5e-3 else 5e-3
-        assert rel <= bound, (prec, k, r["eps"], rel)
+        assert rel <= bound[k], (prec, k, r["eps"], rel, bound[k])
         assert abs(h[k, gw.EN["eps"]] - r["eps"]) <= 1e-6 * r["eps"]
