@@ -64,7 +64,7 @@ def parse():
                     help="skip the timed whole solve (lifts included) behind solves_per_s")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the extra records (config-1 batch, 250k D=64 iteration, "
-                         "128-request serving stream)")
+                         "128-request serving stream, 20k adjoint)")
     ap.add_argument("--workload", default="gmm8",
                     choices=["gmm8", "sphere", "serving", "square-batch", "grad", "multiscale",
                              "lift"],
@@ -326,6 +326,8 @@ def run_gw(args, rank, world, local):
         del fl
         torch.cuda.empty_cache()
         extra["serving_128"] = serving_stream(args, gw, local, 128, 0.8, prec, args.seed)
+        extra["grad_20k_D32"] = grad_timing(gw, torch, dev, 20_000, 32, prec, 0.1, 1e-3, 20, 100,
+                                            args.seed, 5)
     if world > 1:
         e2e_t, e2e_u = aggregate(e2e["seconds"], e2e["cells"], world, dev) if e2e else (None, None)
     else:
@@ -870,26 +872,20 @@ def run_lift(args, rank, world, local):
         }), flush=True)
 
 
-def run_grad(args, rank, world, local):
+def grad_timing(gw, torch, dev, n, D, prec, eps0, eps1, n_outer, n_inner, seed, steps):
     """The adjoint after a solve: 3D 8-blob clouds, ||x - x'|| lifted by Kernel
     PCA (D features), eps annealed over n_outer x n_inner iterations in
-    --prec; then gw_grad_x (row-direction plan sums, closed-form feature
+    prec; then gw_grad_x (row-direction plan sums, closed-form feature
     gradient, centering adjoint and the N x N Kernel-Proj VJP to the raw
-    points) timed with CUDA events after warm-up."""
-    import torch
-    import paper_2602_06658_gb300 as gw
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    prec = PREC[args.prec]
-    n, D = args.n, args.D
-    w = W.gmm_rigid(n, seed=args.seed + rank)
+    points) timed with CUDA events after warm-up (median of `steps`)."""
+    w = W.gmm_rigid(n, seed=seed)
     a = torch.full((n,), 1.0 / n, device=dev)
     xt = torch.tensor(w["x"], dtype=torch.float32, device=dev)
     lx = gw.gw_lift(xt, D, kind=gw.PEN_POWER, param=1.0, w=a, want_basis=True)
     ly = gw.gw_lift(torch.tensor(w["y"], dtype=torch.float32, device=dev), D, kind=gw.PEN_POWER,
                     param=1.0, w=a)
-    o = gw.gw_solve(lx["X"], ly["X"], lx["s"], ly["s"], a, a, args.eps0, args.n_outer,
-                    args.n_inner, eps_final=args.eps1, prec=prec, record=False)
+    o = gw.gw_solve(lx["X"], ly["X"], lx["s"], ly["s"], a, a, eps0, n_outer, n_inner,
+                    eps_final=eps1, prec=prec, record=False)
     eps_T = float(o["energy"][12].item())
     ws = gw.workspace(gw.gw_workspace_size(gw.OP_GRAD, n, n, D, D, prec), dev)
 
@@ -903,7 +899,7 @@ def run_grad(args, rank, world, local):
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     times = []
-    for _ in range(args.steps):
+    for _ in range(max(1, steps)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         dX, dx = grad()
@@ -911,18 +907,29 @@ def run_grad(args, rank, world, local):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     dt = statistics.median(times)
-    if rank == 0:
-        print(json.dumps({
-            "metric": "adjoint time (gradient w.r.t. source points)", "value": dt, "unit": "s",
-            "higher_is_better": False, "n_gpus": world, "steps": args.steps, "warmup": 3,
-            "dtype": DTYPE[args.prec], "data": "synthetic",
-            "pairs_per_s": (float(n) * n + float(n) * n) / dt,
+    return {"seconds": dt, "pairs_per_s": (float(n) * n + float(n) * n) / dt,
             "grad_finite": bool(torch.isfinite(dx).all().item()),
             "energy": float(o["energy"][0].item()), "eps_final": eps_T,
-            "config": {"workload": f"grad: gmm8-3d N=M={n} ||x-x'|| Kernel-PCA D={D}, eps "
-                                   f"{args.eps0}->{args.eps1} over {args.n_outer} x {args.n_inner}",
-                       "work": "N x M plan sums + N x N Kernel-Proj VJP per gradient"}}),
-              flush=True)
+            "workload": f"grad: gmm8-3d N=M={n} ||x-x'|| Kernel-PCA D={D}, eps {eps0}->{eps1} "
+                        f"over {n_outer} x {n_inner}; N x M plan sums + N x N Kernel-Proj VJP "
+                        "per gradient"}
+
+
+def run_grad(args, rank, world, local):
+    """The adjoint as its own bench line (see grad_timing)."""
+    import torch
+    import paper_2602_06658_gb300 as gw
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    r = grad_timing(gw, torch, dev, args.n, args.D, PREC[args.prec], args.eps0, args.eps1,
+                    args.n_outer, args.n_inner, args.seed + rank, args.steps)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "adjoint time (gradient w.r.t. source points)", "value": r["seconds"],
+            "unit": "s", "higher_is_better": False, "n_gpus": world, "steps": args.steps,
+            "warmup": 3, "dtype": DTYPE[args.prec], "data": "synthetic",
+            **{k: v for k, v in r.items() if k not in ("seconds", "workload")},
+            "config": {"workload": r["workload"]}}), flush=True)
 
 
 def run_multiscale(args, rank, world, local):

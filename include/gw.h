@@ -380,9 +380,10 @@ size_t gw_transfer_workspace_size(int64_t n, int64_t m, int D, int k);
  * Sinkhorn iterations on C (Algorithm 3, or 2 with symmetric = 0), warm
  * started, then pi = a b^T exp((f + g - C)/eps).  Options used: eps,
  * eps_final, n_outer, n_inner, symmetric, record, f0, g0 (prec, Gamma0 and
- * the adaptive / stop fields are ignored).  The two GEMMs per step run in
- * cuBLAS with FP32-emulating BF16x9 tensor-core arithmetic (opened at first
- * use; GW_EUNSUPPORTED if libcublas is absent).  Outputs (device): pi
+ * the adaptive / stop fields are ignored).  The two dense products per step
+ * run on the tensor cores at FP32 accuracy (split f16 operands, three
+ * products per term, FP32 accumulation), in this library's own kernel.
+ * Outputs (device): pi
  * (n x m), f, g, energy (GW_EN_LEN record of the final plan, Lemma in kernel
  * form), history (n_outer x GW_EN_LEN when record = 1).  Enqueued on
  * `stream`.  Memory: O(n m + n^2 + m^2), n m <= 2^31.

@@ -264,6 +264,15 @@ int run_transfer(const gw_problem& p, const float* f, const float* g, const doub
                  float eps, const float* U, int k, float* out, float* mass, Carver& ws,
                  cudaStream_t st);
 
+// Dense FP32-accuracy product on the tensor cores (gw_gemm_tc.cu):
+// out[r][s] = scale sum_k A[s][k] Bt[r][k] + coef u[r] v[s] (out R x S
+// row-major; A logical S x K stored row-major, or K x S when a_trans; Bt
+// logical R x K, or K x R when b_trans; u, v may be null).
+size_t gemm_tc_ws_bytes(int64_t S, int64_t R, int64_t K);
+int gemm_tc_f16x3(const float* A, bool a_trans, const float* Bt, bool b_trans, int64_t S,
+                  int64_t R, int64_t K, float scale, const float* u, const float* v, float coef,
+                  float* out, Carver& ws, cudaStream_t st);
+
 // Kernel-GW exact mode (gw_kernelgw.cu)
 size_t kernel_gw_ws_bytes(int64_t n, int64_t m);
 int run_kernel_gw(const float* CX, const float* CY, const float* a, const float* b, int64_t n,

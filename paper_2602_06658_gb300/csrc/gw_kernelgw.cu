@@ -4,21 +4,18 @@
 // step builds the dense cost C = -4 K^X_ii K^Y_jj - 16 K^X pi K^Y, runs
 // Sinkhorn on it and forms the plan pi = a b^T exp((f + g - C)/eps).
 //
-// The two products K^X (pi K^Y) are plain dense GEMMs (O(N^2 M + N M^2) per
-// step): they go to cuBLAS with the FP32-emulating BF16x9 compute type, i.e.
-// the tensor cores at FP32 accuracy.  cuBLAS is opened with dlopen on first
-// use, so the library itself depends only on the CUDA driver; without cuBLAS
-// this entry point returns GW_EUNSUPPORTED.  Everything else (centering,
-// softmins over the dense cost, plan, energy) runs in the kernels below.
+// The two products K^X (pi K^Y) (O(N^2 M + N M^2) per step) run on the
+// tensor cores at FP32 accuracy in this library's own split-f16 product
+// (gw_gemm_tc.cu), the rank-one term -4 k l^T fused into the second one's
+// epilogue.  Everything else (centering, softmins over the dense cost, plan,
+// energy) runs in the kernels below.
 //
 // Energy of pi_{t+1} (Lemma, Appendix C.1, in kernel form): with
 // k_i = K^X_ii, l_j = K^Y_jj and C_{t+1} the next step's cost,
 //   T = sum pi k l,  ||Gamma||^2 = <pi, K^X pi K^Y> = -(4 T + <pi, C_{t+1}>) / 16,
 //   eps KL = sum pi (f + g - C_t),  C(alpha, beta) from the kernel moments.
-#include <dlfcn.h>
 #include <math.h>
 
-#include <cublas_v2.h>
 #include <mutex>
 
 #include "gw_internal.cuh"
@@ -26,64 +23,6 @@
 namespace gw {
 
 namespace {
-
-// ------------------------------------------------------------ cuBLAS (lazy)
-// the C entry point of cublasGemmEx (the header adds a C++ overload)
-typedef cublasStatus_t (*GemmExFn)(cublasHandle_t, cublasOperation_t, cublasOperation_t, int, int,
-                                   int, const void*, const void*, cudaDataType, int, const void*,
-                                   cudaDataType, int, const void*, void*, cudaDataType, int,
-                                   cublasComputeType_t, cublasGemmAlgo_t);
-
-struct Blas {
-  decltype(&cublasCreate_v2) create = nullptr;
-  decltype(&cublasSetStream_v2) set_stream = nullptr;
-  GemmExFn gemm = nullptr;
-  bool ok = false;
-};
-
-const Blas& blas() {
-  static Blas b;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* h = dlopen("libcublas.so.13", RTLD_NOW | RTLD_LOCAL);
-    if (!h) h = dlopen("/usr/local/cuda/lib64/libcublas.so.13", RTLD_NOW | RTLD_LOCAL);
-    if (!h) h = dlopen("libcublas.so", RTLD_NOW | RTLD_LOCAL);
-    if (!h) return;
-    b.create = reinterpret_cast<decltype(b.create)>(dlsym(h, "cublasCreate_v2"));
-    b.set_stream = reinterpret_cast<decltype(b.set_stream)>(dlsym(h, "cublasSetStream_v2"));
-    b.gemm = reinterpret_cast<decltype(b.gemm)>(dlsym(h, "cublasGemmEx"));
-    b.ok = b.create && b.set_stream && b.gemm;
-  });
-  return b;
-}
-
-// one handle per host thread and device (handles are not thread-safe)
-int blas_handle(cublasHandle_t* out) {
-  const Blas& B = blas();
-  GW_REQUIRE(B.ok, GW_EUNSUPPORTED, "Kernel-GW needs cuBLAS (libcublas.so.13), which was not found");
-  int dev = 0;
-  GW_CUDA_TRY(cudaGetDevice(&dev));
-  thread_local cublasHandle_t handles[64] = {};
-  GW_REQUIRE(dev >= 0 && dev < 64, GW_EUNSUPPORTED, "device index %d out of range", dev);
-  if (!handles[dev]) {
-    cublasHandle_t h = nullptr;
-    GW_REQUIRE(B.create(&h) == CUBLAS_STATUS_SUCCESS, GW_ECUDA, "cublasCreate failed");
-    handles[dev] = h;
-  }
-  *out = handles[dev];
-  return GW_OK;
-}
-
-// column-major C (rows x cols) = alpha A (rows x inner) B (inner x cols) + beta C
-int gemm(cublasHandle_t h, int rows, int cols, int inner, float alpha, const float* A,
-         const float* Bm, float beta, float* C) {
-  const cublasStatus_t s =
-      blas().gemm(h, CUBLAS_OP_N, CUBLAS_OP_N, rows, cols, inner, &alpha, A, CUDA_R_32F, rows, Bm,
-                  CUDA_R_32F, inner, &beta, C, CUDA_R_32F, rows, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                  CUBLAS_GEMM_DEFAULT);
-  GW_REQUIRE(s == CUBLAS_STATUS_SUCCESS, GW_ECUDA, "cublasGemmEx failed (%d)", static_cast<int>(s));
-  return GW_OK;
-}
 
 // ------------------------------------------------------------ Algorithm 4
 // K0_ij = (C_i0 + C_0j - C_ij) / 2
@@ -183,12 +122,6 @@ __global__ void kg_moment_total_kernel(const double* part, int64_t n, double* ou
 }
 
 // ------------------------------------------------------------ dense cost and Sinkhorn
-// C_ij = -4 k_i l_j (the GEMM adds -16 K^X pi K^Y)
-__global__ void kg_rank1_kernel(const float* k, const float* l, int64_t n, int64_t m, float* C) {
-  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q < n * m) C[q] = -4.0f * k[q / m] * l[q % m];
-}
-
 __global__ void kg_outer_kernel(const float* a, const float* b, int64_t n, int64_t m, float* P) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q < n * m) P[q] = a[q / m] * b[q % m];
@@ -403,6 +336,8 @@ __global__ void kg_set_ninner_kernel(double* en, double v) {
 struct KgBufs {
   float *KX, *KY, *k, *l, *loga, *logb, *P, *C[2], *T, *f[2], *g[2], *pm, *ps;
   double *rows, *cols, *tot, *mpart, *MX, *MY, *rp, *cs, *state, *en;
+  char* gemm_ws;           // split operands of the tensor-core products
+  size_t gemm_ws_bytes;
 };
 
 int col_splits(int64_t n, int64_t m) {
@@ -445,6 +380,9 @@ KgBufs carve_kg(Carver& c, int64_t n, int64_t m) {
   B.cs = c.take<double>(m);
   B.state = c.take<double>(2);
   B.en = c.take<double>(GW_EN_LEN);
+  const size_t g1 = gemm_tc_ws_bytes(m, n, m), g2 = gemm_tc_ws_bytes(m, n, n);
+  B.gemm_ws_bytes = g1 > g2 ? g1 : g2;
+  B.gemm_ws = c.take<char>(B.gemm_ws_bytes);
   return B;
 }
 
@@ -468,16 +406,15 @@ int kernel_from_cost_dev(const float* Cm, const float* w, int64_t n, float* K, f
   return GW_OK;
 }
 
-// C = -4 k l^T - 16 K^X P K^Y  (row-major buffers read as column-major transposes:
-// T^T = K^Y^T P^T, then C^T += -16 T^T K^X^T)
-int dense_cost(cublasHandle_t h, const KgBufs& B, const float* P, float* C, int64_t n, int64_t m,
-               cudaStream_t st) {
-  kg_rank1_kernel<<<ceil_div(n * m, 256), 256, 0, st>>>(B.k, B.l, n, m, C);
-  GW_LAUNCH_CHECK();
-  GW_TRY(gemm(h, static_cast<int>(m), static_cast<int>(n), static_cast<int>(m), 1.0f, B.KY, P, 0.0f,
-              B.T));
-  GW_TRY(gemm(h, static_cast<int>(m), static_cast<int>(n), static_cast<int>(n), -16.0f, B.T, B.KX,
-              1.0f, C));
+// C = -4 k l^T - 16 K^X P K^Y (n x m row-major): T = P K^Y, then
+// C = -16 K^X T - 4 k l^T, both through gemm_tc_f16x3 (out[r][s] =
+// scale sum_k A[s][k] Bt[r][k] + coef u[r] v[s]); the kernels are symmetric,
+// so K^Y serves as its own transpose, and T is read transposed.
+int dense_cost(const KgBufs& B, const float* P, float* C, int64_t n, int64_t m, cudaStream_t st) {
+  Carver g(B.gemm_ws, B.gemm_ws_bytes);
+  GW_TRY(gemm_tc_f16x3(B.KY, false, P, false, m, n, m, 1.0f, nullptr, nullptr, 0.0f, B.T, g, st));
+  Carver g2(B.gemm_ws, B.gemm_ws_bytes);
+  GW_TRY(gemm_tc_f16x3(B.T, true, B.KX, false, m, n, n, -16.0f, B.k, B.l, -4.0f, C, g2, st));
   return GW_OK;
 }
 
@@ -497,9 +434,6 @@ int run_kernel_gw(const float* CX, const float* CY, const float* a, const float*
   GW_TRY(check_ws(c, ws));
   GW_REQUIRE(n * m <= (int64_t(1) << 31) && n <= (int64_t(1) << 30) && m <= (int64_t(1) << 30),
              GW_EUNSUPPORTED, "Kernel-GW is the small-N exact mode (n m <= 2^31)");
-  cublasHandle_t h = nullptr;
-  GW_TRY(blas_handle(&h));
-  GW_REQUIRE(blas().set_stream(h, st) == CUBLAS_STATUS_SUCCESS, GW_ECUDA, "cublasSetStream failed");
   // Algorithm 4 on both sides (the kernels of Algorithm 5)
   GW_TRY(kernel_from_cost_dev(CX, a, n, B.KX, B.k, B.MX, B, st));
   GW_TRY(kernel_from_cost_dev(CY, b, m, B.KY, B.l, B.MY, B, st));
@@ -520,7 +454,7 @@ int run_kernel_gw(const float* CX, const float* CY, const float* a, const float*
   kg_outer_kernel<<<ceil_div(n * m, 256), 256, 0, st>>>(a, b, n, m, B.P);
   GW_LAUNCH_CHECK();
   int cc = 0, fc = 0, gc = 0;
-  GW_TRY(dense_cost(h, B, B.P, B.C[cc], n, m, st));
+  GW_TRY(dense_cost(B, B.P, B.C[cc], n, m, st));
   const int S = col_splits(n, m);
   const int rows_per_split = static_cast<int>((n + S - 1) / S);
   for (int t = 0; t < o.n_outer; ++t) {
@@ -559,7 +493,7 @@ int run_kernel_gw(const float* CX, const float* CY, const float* a, const float*
     // pi^{t+1} (Algorithm 5) and the cost it induces, C_{t+1}
     kg_plan_kernel<<<ceil_div(n * m, 256), 256, 0, st>>>(C, a, b, B.f[fc], B.g[gc], n, m, eps, B.P);
     GW_LAUNCH_CHECK();
-    GW_TRY(dense_cost(h, B, B.P, B.C[cc ^ 1], n, m, st));
+    GW_TRY(dense_cost(B, B.P, B.C[cc ^ 1], n, m, st));
     const bool last = t == o.n_outer - 1;
     double* rec = (o.record && history) ? history + static_cast<size_t>(t) * GW_EN_LEN : B.en;
     kg_energy_rows_kernel<<<ceil_div(n * 32, 256), 256, 0, st>>>(B.P, C, B.C[cc ^ 1], B.k, B.l,

@@ -77,3 +77,23 @@ def test_kernel_gw_rejects_bad_options(gw):
     with pytest.raises(gw.GWError) as e:
         gw.gw_kernel_gw(f32(CX), f32(CY), f32(a), f32(b), -1.0, 2, 5)
     assert e.value.code == 1
+
+
+def test_kernel_gw_at_a_thousand_points(gw):
+    """n = 1100, m = 900: many 128-wide tiles and 64-wide K blocks of the
+    tensor-core products (K' = 3 x 1152 / 3 x 960), ragged in every
+    direction; the same bars as the small case."""
+    n, m = 1100, 900
+    x, y, a, b, CX, CY = problem(n, m, 11)
+    eps = 0.05
+    pi, f, g = O.kernel_gw(a, b, CX, CY, eps, 4, 40, symmetric=True)
+    LX = O.lift(x, a, "power", 1.0, D=n - 1)
+    LY = O.lift(y, b, "power", 1.0, D=m - 1)
+    E_ref = O.egw_energy(pi, LX["X"], LY["X"], a, b, eps)["E"]
+    out = gw.gw_kernel_gw(f32(CX), f32(CY), f32(a), f32(b), eps, 4, 40)
+    P = host(out["pi"])
+    assert np.abs(P - pi).max() <= 1e-3 * pi.max()
+    en = host(out["energy"])
+    assert en[gw.EN["status"]] == 0
+    assert abs(en[gw.EN["E"]] - E_ref) <= 1e-4 * abs(E_ref)
+    np.testing.assert_allclose(P.sum(0), pi.sum(0), rtol=0, atol=1e-3 * b.max())
