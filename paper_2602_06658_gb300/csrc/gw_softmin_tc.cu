@@ -61,7 +61,8 @@ constexpr float kSumHi = 1.3292280e36f;      // 2^120: a sum above this (or inf/
 struct TcTask {
   tc::WaitCtl wc;         // pipeline wait limit and the give-up counter
   const int* gate;        // layout decision (device); the launch runs only when
-  int gate_on;            // *gate == gate_on (gate null: always)
+  int gate_on;            // *gate == gate_on (gate null: always); gate_on = 1 is the
+  int K;                  // split layout, whose K-steps follow its dim count gate[1]
   int64_t n, m;           // real rows / columns
   int ksteps;             // MMA K-steps of 16 that hold non-zero operand columns
   const float* est;       // per-row shift estimate (fast pass), or null
@@ -204,6 +205,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the operands are in the other layout: that launch does the work
   if (T.gate != nullptr && *T.gate != T.gate_on) return;
+  // the split layout holds 2 gate[1] + K + 10 non-zero operand columns
+  const int nks_run =
+      (T.gate != nullptr && T.gate_on == 1) ? (2 * T.gate[1] + T.K + 10 + 15) / 16 : T.ksteps;
   // the safe pass only recomputes the row tiles the fast pass marked
   if (!FAST && T.flags != nullptr && T.flags[rt] == 0) return;
 
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (!tc::mbar_wait(&full[s], (t / S) & 1, ab, lim)) break;
         tc::tc_fence_after();
         const unsigned char* Bst = Bs + s * L::kStageBytes;
-        const int nks = T.ksteps;
+        const int nks = nks_run;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
 #pragma unroll
@@ -417,9 +421,10 @@ __global__ void tc_dimmax_kernel(const float* A, int64_t n, int K, unsigned* out
 
 // Layout decision of the split precisions (one block of 128 threads):
 // P_k = max|A_k| max|B_k| bounds every product of dim k; the dims are ordered
-// by P_k (largest first, ties by index) into lay[2 .. 2 + K), and lay[0] = 1
-// (the narrow layout) when at most ks_max dims have P_k above tau max P: the
-// others then run as one product within the split products' error bound.
+// by P_k (largest first, ties by index) into lay[2 .. 2 + K), lay[1] = the
+// count of dims with P_k above tau max P (those run as three products, the
+// others as one, within the split products' error bound), and lay[0] = 1
+// (the split layout) when that count fits the layout (at most ks_max).
 __global__ void tc_layout_kernel(const unsigned* mxA, const unsigned* mxB, int K, float tau,
                                  int ks_max, int* lay) {
   __shared__ float P[128];
@@ -550,7 +555,13 @@ bool softmin_tc_supported(int K, int prec) {
 // layout needs 192 or more operand columns (K >= 40): it holds the dims of
 // largest product bound as three products and the rest as one, in 128 columns.
 constexpr int kNarrowKP = 128;
+// (measured: on K = 32 lifted features the split layout in the full 128
+// columns, 5 instead of 7 K-steps, made the fused iteration slower, 3.43 ms
+// against 3.22 ms at N = M = 100k: the kernel is bound by its epilogue there)
 bool narrow_enabled(const TcOperandShape& f) { return f.mult == 3 && f.KP >= 192; }
+// width of the split layout: 128 columns when the full one needs more,
+// else the full width (then every dim count fits and one launch does)
+int narrow_kp(const TcOperandShape& f) { return f.KP > kNarrowKP ? kNarrowKP : f.KP; }
 
 size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
   const TcOperandShape shp = tc_shape(K, prec);
@@ -576,11 +587,14 @@ size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
 
 // Prepare operands for one or two tasks and launch the tensor-core kernel.
 // Fills tasks[q].splits / pm / ps so the caller can merge split partials.
-// For K >= 40 in the split precisions both layouts are launched: the narrow
-// one (tc_shape_split, 128 columns) and the full one; the device's layout
-// decision (tc_layout_kernel, made from the first task's maxima when the
-// operands are prepared) lets exactly one of them run, the other returns at
-// once.  Both use the same column splits, so their partials merge alike.
+// The split precisions take the device's layout decision (tc_layout_kernel,
+// made from the first task's maxima when the operands are prepared): the dims
+// of large product bound as three products, the rest as one, in the split
+// layout (tc_shape_split; the MMA runs only its non-zero K-steps).  Where the
+// full layout is wider than 128 columns (K >= 40) it stays as the fallback
+// for spectra too flat for 128 columns: both kernels are launched and the
+// device's decision lets exactly one run, the other returns at once; both use
+// the same column splits, so their partials merge alike.
 int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cudaStream_t st) {
   GW_REQUIRE(softmin_tc_supported(tasks[0].K, prec), GW_EUNSUPPORTED,
              "tensor-core softmin does not support K=%d with precision %d", tasks[0].K, prec);
@@ -591,8 +605,11 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
   memset(ta, 0, sizeof(ta));
   const TcOperandShape shp = tc_shape(tasks[0].K, prec);
   const bool narrow = narrow_enabled(shp);
-  const TcOperandShape shp_a = narrow ? tc_shape_split(tasks[0].K, prec, kNarrowKP) : shp;
-  const int bn_f = tile_cols(shp.KP), bn_a = tile_cols(kNarrowKP);
+  const TcOperandShape shp_a = narrow ? tc_shape_split(tasks[0].K, prec, narrow_kp(shp)) : shp;
+  const int kp_a = shp_a.KP;
+  // the split layout in the full width needs no second launch
+  const bool two_launches = narrow && kp_a != shp.KP;
+  const int bn_f = tile_cols(shp.KP), bn_a = tile_cols(kp_a);
   int row_tiles[2] = {0, 0}, col_tiles[2] = {0, 0};
   for (int q = 0; q < ntasks; ++q) {
     row_tiles[q] = ceil_div(tasks[q].n, kBM);
@@ -711,10 +728,11 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     K.wc = wait_ctl();
     K.gate = nullptr;
     K.gate_on = 0;
+    K.K = T.K;
     if (narrow) {
-      // the narrow layout over the same buffers (its rows are kNarrowKP wide)
-      GW_TRY(make_map(&maps_a[2 * q], opA, n_pad, kNarrowKP, bf16, 128));
-      GW_TRY(make_map(&maps_a[2 * q + 1], opB, m_pad_a, kNarrowKP, bf16, bn_a));
+      // the split layout over the same buffers (its rows are kp_a wide)
+      GW_TRY(make_map(&maps_a[2 * q], opA, n_pad, kp_a, bf16, 128));
+      GW_TRY(make_map(&maps_a[2 * q + 1], opB, m_pad_a, kp_a, bf16, bn_a));
       TcTask& A = ta[q];
       A = K;
       A.ksteps = (shp_a.used + 15) / 16;
@@ -754,7 +772,8 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
   }
   // one pass in the layout the device chose (the other launch returns at once)
   auto pass = [&](bool fast) -> int {
-    if (narrow) GW_TRY(run_tc(bf16, fast, kNarrowKP, maps_a, ta[0], ta[1], st));
+    if (narrow) GW_TRY(run_tc(bf16, fast, kp_a, maps_a, ta[0], ta[1], st));
+    if (narrow && !two_launches) return GW_OK;
     return run_tc(bf16, fast, shp.KP, maps, tt[0], tt[1], st);
   };
   if (!all_est) {

@@ -68,6 +68,19 @@ TcOperandShape tc_shape_split(int K, int prec, int KP) {
   return s;
 }
 
+// The split layout of shape s (its KP kept) with ks dims as three products.
+__host__ __device__ inline TcOperandShape shape_ks(TcOperandShape s, int ks) {
+  if (ks > s.K) ks = s.K;
+  if (ks < 0) ks = 0;
+  s.Ks = ks;
+  s.col_u = 3 * ks + (s.K - ks);
+  s.col_w = s.col_u + 3;
+  s.col_e = s.col_w + 3;
+  s.col_k = s.col_e + 3;
+  s.used = s.col_k + 1;
+  return s;
+}
+
 // Relative error of a single 16-bit product X_k V_k (both operands rounded
 // once): 2^-10 in f16, 2^-7 in bf16.  A dim may run as one product when its
 // bound P_k = max|X_k| max|V_k| is at most TERM_REL / single_rel times the
@@ -166,7 +179,7 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
                                float shift_bias = kShiftBias, const int* lay = nullptr,
                                TcOperandShape shp_a = TcOperandShape{}, int64_t rows_pad_a = 0) {
   const bool ad = lay != nullptr && lay[0] != 0;
-  const TcOperandShape shp = ad ? shp_a : shp_f;
+  const TcOperandShape shp = ad ? shape_ks(shp_a, lay[1]) : shp_f;
   const int64_t rows_pad = ad ? rows_pad_a : rows_pad_f;
   const int* perm = ad ? lay + 2 : nullptr;
   const int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
@@ -298,7 +311,7 @@ __global__ void tc_refresh_multi_kernel(RefreshTask t0, RefreshTask t1, int ntas
                                         TcOperandShape shp_f, const float* part, int nparts,
                                         const int* lay = nullptr,
                                         TcOperandShape shp_a = TcOperandShape{}) {
-  const TcOperandShape shp = (lay != nullptr && lay[0] != 0) ? shp_a : shp_f;
+  const TcOperandShape shp = (lay != nullptr && lay[0] != 0) ? shape_ks(shp_a, lay[1]) : shp_f;
   __shared__ float cw[2], ce[2];
   if (threadIdx.x < 32) {
     for (int q = 0; q < ntasks; ++q) {

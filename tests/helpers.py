@@ -62,7 +62,7 @@ SINGLE_REL = {2: 2.0 ** -7, 3: 2.0 ** -10}
 
 def narrow_layout_bound(A, B, prec):
     """Per-row bound (output units) of the dims the split precisions may run
-    as one product when the full operand layout is 192 columns or wider
+    as one product when their full operand layout is wider than 128 columns
     (K >= 40): those with P_k = max|A_k| max|B_k| at most
     TERM_REL[prec] / SINGLE_REL[prec] times the largest P.  Each of their
     terms carries SINGLE_REL[prec] relative error; in the output

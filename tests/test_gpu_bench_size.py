@@ -20,7 +20,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from helpers import TERM_REL, f32, f64, host
+from helpers import SINGLE_REL, TERM_REL, f32, f64, host
 
 pytestmark = pytest.mark.gpu
 
@@ -87,13 +87,20 @@ def sampled(n, k, seed, must=()):
 
 def tol_rows(A, B, sA, sB, h, logw, eps, prec, rows):
     """helpers.softmin_tolerance_prec for the sampled rows only (the same
-    derivation: TERM_REL[prec] per exponent term, bias columns, ex2, sum)."""
+    derivation: TERM_REL[prec] per exponent term, the dims the split
+    precisions may run as one product, bias columns, ex2, sum)."""
     Ar = np.abs(A[rows])
     lw = np.where(np.isfinite(logw), np.abs(logw), 0.0)
     S = (16.0 * Ar @ np.abs(B).T + 4.0 * np.abs(np.outer(sA[rows], sB))
          + np.abs(h)[None, :] + eps * lw[None, :]).max(axis=1)
+    single = np.zeros(len(rows))
+    if prec in (2, 3) and 3 * A.shape[1] + 10 > 128:
+        P = np.abs(A).max(axis=0) * np.abs(B).max(axis=0)
+        small = P <= TERM_REL[prec] / SINGLE_REL[prec] * P.max() * (1.0 + 1e-6)
+        if small.any():
+            single = 16.0 * SINGLE_REL[prec] * (Ar[:, small] @ np.abs(B[:, small]).T).max(axis=1)
     m = len(B)
-    return 2.0 * ((A.shape[1] + 2) * TERM_REL[prec] * S
+    return 2.0 * ((A.shape[1] + 2) * TERM_REL[prec] * S + single
                   + eps * (2.0 ** -8 + 2.0 ** -21 + math.sqrt(m) * 2.0 ** -22))
 
 
