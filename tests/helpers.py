@@ -142,3 +142,15 @@ def noisy_cnt_gw(a, b, X, Y, eps0, n_outer, n_inner, prec, seed, eps_final=None,
         hist.append({"eps": e, "E": en["E"], "L": en["L"], "KL": en["KL"]})
         Gamma = O.cross_covariance(pi, X, Y)
     return hist
+
+
+def grad_tolerance(pi, X, Y, a, eps):
+    """Relative bound (times the largest term) of the FP32 adjoint's feature
+    gradient: each plan entry carries ~(D+4) 2^-24 |C| / eps of relative error
+    from its exponent, each sum over N or M terms ~sqrt(N) 2^-24; a factor 8
+    for the closed form's combination of terms."""
+    X = np.asarray(X, np.float64)
+    Y = np.asarray(Y, np.float64)
+    scale = 16 * np.abs(X).max() * np.abs(Y).max() + 8 * (X * X).sum(1).max() * (Y * Y).sum(1).max()
+    rel = (X.shape[1] + 4) * 2.0 ** -24 * scale / eps + np.sqrt(max(X.shape[0], Y.shape[0])) * 2.0 ** -22
+    return 8.0 * rel

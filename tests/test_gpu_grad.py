@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from helpers import f32, f64, host
+from helpers import f32, f64, grad_tolerance, host
 
 pytestmark = pytest.mark.gpu
 
@@ -23,15 +23,6 @@ def converged_state(X, Y, a, b, eps, G0, n_outer=60):
     f, g = r32(f), r32(g)
     pi = O.plan(a, b, f, g, C, eps)
     return Gt, f, g, pi
-
-
-def grad_tolerance(pi, X, Y, a, eps):
-    """FP32 evaluation of the closed form: each plan entry carries a relative
-    error of ~(D+4) 2^-24 |C|/eps from its exponent, each sum over N or M
-    terms ~sqrt(N) 2^-24; scaled by the largest gradient term."""
-    scale = 16 * np.abs(X).max() * np.abs(Y).max() + 8 * (X * X).sum(1).max() * (Y * Y).sum(1).max()
-    rel = (X.shape[1] + 4) * 2.0 ** -24 * scale / eps + np.sqrt(max(X.shape[0], Y.shape[0])) * 2.0 ** -22
-    return 8.0 * rel
 
 
 @pytest.mark.parametrize("n,m,d,eps", [(200, 200, 2, 0.05), (300, 250, 3, 0.1)])

@@ -10,7 +10,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from helpers import f32, host
+from helpers import grad_tolerance, f32, host
 
 pytestmark = pytest.mark.gpu
 
@@ -67,8 +67,8 @@ def test_sgw_gradient_matches_oracle(gw):
     device gradient of SGW with respect to the (centered) features against
     the oracle's closed form followed by the centering adjoint.  SGW's
     gradient is a difference of three adjoint gradients, so the FP32 error
-    bound of the adjoint (2e-3 of a gradient's largest entry, as for
-    gw_grad_x) applies to each term: 2e-3 (|g_ab| + |g_src| / 2 + |g_tgt| / 2)."""
+    bound of the adjoint (helpers.grad_tolerance, as for gw_grad_x) applies
+    to each term: sum_t rel_t |g_t| with weights 1, 1/2, 1/2."""
     x, y, a, b = clouds(200, 180, 11)
     X, Y = r32(O.center(x, a)), r32(O.center(y, b))
     eps = 0.05
@@ -85,8 +85,10 @@ def test_sgw_gradient_matches_oracle(gw):
     terms = [O.grad_features(pi_ab, O.cross_covariance(pi_ab, X, Y), X, Y, a, b),
              O.grad_features(pi_aa, O.cross_covariance(pi_aa, X, X), X, X, a, a),
              O.grad_features(pi_aa.T, O.cross_covariance(pi_aa.T, X, X), X, X, a, a)]
-    tol = 2e-3 * (np.abs(terms[0]).max() + 0.5 * np.abs(terms[1]).max()
-                  + 0.5 * np.abs(terms[2]).max())
+    rel_ab = grad_tolerance(pi_ab, X, Y, a, eps)
+    rel_aa = grad_tolerance(pi_aa, X, X, a, eps)
+    tol = (rel_ab * np.abs(terms[0]).max() + 0.5 * rel_aa * np.abs(terms[1]).max()
+           + 0.5 * rel_aa * np.abs(terms[2]).max())
     out = run(gw, X, Y, a, b, eps, 40, 300, symmetric=False, grad=True)
     dX = host(out["dX"])
     assert np.abs(dX - want).max() <= tol

@@ -379,6 +379,49 @@ def test_kernel_proj_vjp_matches_finite_differences():
     assert np.allclose(vjp, fd, atol=1e-7)
 
 
+def test_kernel_proj_vjp_matches_finite_differences_gaussian_cost():
+    """The same finite-difference pin for the Gaussian CNT cost
+    2 (1 - exp(-||x - x'||^2 / (2 sigma^2))), whose cost gradient (the
+    chain rule through the exponential) the power cost does not exercise."""
+    g = W.rng(75)
+    x = g.standard_normal((20, 3)) * 0.7
+    a = W.uniform_weights(20)
+    L = O.lift(x, a, "gauss", 0.8, D=5)
+    xq = g.standard_normal((4, 3)) * 0.7
+    G = g.standard_normal((4, 5))
+    vjp = O.kernel_proj_vjp(G, xq, x, a, L["V"], L["lam"], "gauss", 0.8)
+    h = 1e-6
+    fd = np.zeros_like(xq)
+    for q in range(4):
+        for d in range(3):
+            xp, xm = xq.copy(), xq.copy()
+            xp[q, d] += h
+            xm[q, d] -= h
+            Pp = O.kernel_proj(xp, x, a, L["V"], L["lam"], "gauss", 0.8)
+            Pm = O.kernel_proj(xm, x, a, L["V"], L["lam"], "gauss", 0.8)
+            fd[q, d] = np.sum(G * (Pp - Pm)) / (2 * h)
+    assert np.abs(vjp).max() > 1e-3          # the check is not vacuous
+    assert np.allclose(vjp, fd, atol=1e-7)
+
+
+def test_gaussian_cost_gradient_matches_finite_differences():
+    """cnt_cost_grad1 of the Gaussian cost against central differences of
+    cnt_cost (the derivative both the adjoint and the VJP take)."""
+    g = W.rng(76)
+    x = g.standard_normal((5, 3))
+    y = g.standard_normal((6, 3))
+    h = 1e-6
+    for i in range(5):
+        Gd = O.cnt_cost_grad1(x[i], y, "gauss", 0.9)    # (6, 3): d c(x_i, y_k) / d x_i
+        assert np.abs(Gd).max() > 1e-3
+        for d in range(3):
+            xp, xm = x[i:i + 1].copy(), x[i:i + 1].copy()
+            xp[0, d] += h
+            xm[0, d] -= h
+            fd = (O.cnt_cost(xp, y, "gauss", 0.9) - O.cnt_cost(xm, y, "gauss", 0.9))[0] / (2 * h)
+            assert np.allclose(Gd[:, d], fd, atol=1e-8)
+
+
 # ------------------------------------------------------------- gradients
 
 def _converged_state(x, y, a, b, eps, G0, kind="sqeuclid", n_outer=60):
