@@ -313,6 +313,14 @@ def run_gw(args, rank, world, local):
         rf32 = roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, 0, flush, reps=3)
         rf["fp32_cells_per_s"] = rf32["cells_per_s"]
         rf["speedup_vs_fp32"] = rf["cells_per_s"] / rf32["cells_per_s"]
+        if prec != PREC["bf16"]:
+            # the single-product BF16 form on the same state (a speed reference;
+            # its error is stated separately)
+            rfb = roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, PREC["bf16"], flush,
+                                   reps=3, ex2_peak=ex2_peak)
+            rf["bf16_cells_per_s"] = rfb["cells_per_s"]
+            rf["bf16_ex2_frac"] = rfb["frac"]
+            rf["bf16_speedup_vs_fp32"] = rfb["cells_per_s"] / rf32["cells_per_s"]
     e2e = None if args.no_e2e else run_e2e(args, gw, torch, dev, X, Y, s, t, a, b, prec, ws, flush)
     full = None if args.no_full or world > 1 else run_full_solve(args, gw, torch, dev, prec, seed)
     extra = None

@@ -273,8 +273,14 @@ int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, s
  *   x: n x d raw points (float32); w: n weights or NULL (uniform).
  *   Outputs: X (n x D), sqn (n) = ||X_i||^2, basis_opt (n x D, V) and
  *   eigvals_opt (D, Lambda) may be NULL.  `seed` seeds the start block.
- *   Synchronous: returns after the work completes (the Rayleigh-Ritz steps
- *   run a small dense eigen-solve on the host).
+ *   Asynchronous on `stream` like the other calls: every step, the small
+ *   r x r Cholesky, triangular inverse and Rayleigh-Ritz eigen-solve
+ *   included, runs on the device, and nothing is read back (a first call
+ *   outside any stream capture sets the kernels' shared-memory limits; later
+ *   calls may be captured).  A degenerate block (the Gram matrix of a
+ *   subspace iterate not positive definite, e.g. from NaN points) leaves X,
+ *   sqn (and basis_opt) as NaN, which a solve on them reports as
+ *   GW_ENONFINITE.
  * Errors: GW_EINVAL, GW_ENOMEM, GW_EUNSUPPORTED, GW_ECUDA.
  */
 int gw_lift(const float* x, int64_t n, int d, const float* w, int kind, float param, int D,

@@ -12,7 +12,7 @@
 // re-orthonormalised by Cholesky QR, and a final Rayleigh-Ritz step.  The
 // small r x r Cholesky, triangular inverse and eigen-problem (cyclic Jacobi)
 // run on the device too, one block each in float64, so a lift makes no host
-// round trip until the one read of its status at the end.
+// round trip at all: it is asynchronous on its stream.
 #include <math.h>
 #include <string.h>
 
@@ -213,33 +213,21 @@ __global__ void sign_apply_kernel(float* V, int64_t n, int D, const double* flip
   if (lane == 0) sqn[i] = s;
 }
 
-// Squared lift: X = x - sum w x; sqn = ||X||^2 (one block, d <= 128)
-__global__ void center_points_kernel(const float* x, const float* w, int64_t n, int d, float* X,
-                                     float* sqn) {
-  __shared__ double mean[128];
-  __shared__ double red[256];
+// Squared lift: X = x - sum w x; sqn = ||X||^2.  The weighted mean comes from
+// per-block partials over row chunks (kGramBlocks blocks, blockDim.x = d)
+// summed in a fixed order (colsum_partial / colsum_final), then
+// every row is centered in parallel.
+__global__ void center_apply_kernel(const float* x, const double* mean, int64_t n, int d,
+                                    float* X, float* sqn) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
   for (int c = 0; c < d; ++c) {
-    double a = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-      a += (w ? static_cast<double>(w[i]) : 1.0 / static_cast<double>(n)) * x[i * d + c];
-    red[threadIdx.x] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int t = 0; t < static_cast<int>(blockDim.x); ++t) s += red[t];
-      mean[c] = s;
-    }
-    __syncthreads();
+    const float v = static_cast<float>(static_cast<double>(x[i * d + c]) - mean[c]);
+    X[i * d + c] = v;
+    s = fmaf(v, v, s);
   }
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    float s = 0.f;
-    for (int c = 0; c < d; ++c) {
-      const float v = static_cast<float>(static_cast<double>(x[i * d + c]) - mean[c]);
-      X[i * d + c] = v;
-      s = fmaf(v, v, s);
-    }
-    sqn[i] = s;
-  }
+  sqn[i] = s;
 }
 
 // ---- the small dense steps on the device (one block each, float64) ----
@@ -417,6 +405,20 @@ __global__ void __launch_bounds__(256) ritz_eig_kernel(const double* T, int RP, 
   }
 }
 
+// A lift whose Cholesky step failed (*status != 0) fills its outputs with NaN.
+__global__ void lift_poison_kernel(const int* status, int64_t n, int D, float* X, float* sqn,
+                                   float* basis) {
+  if (*status == 0) return;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float nan = __int_as_float(0x7fc00000);
+  sqn[i] = nan;
+  for (int c = 0; c < D; ++c) {
+    X[i * D + c] = nan;
+    if (basis) basis[i * D + c] = nan;
+  }
+}
+
 int rpad(int D) {
   const int want = D + 8;
   const int opts[] = {16, 32, 48, 64, 80, 96, 128};
@@ -533,9 +535,17 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
              int n_iter, uint64_t seed, float* X, float* sqn, float* basis, float* eigvals,
              void* ws, size_t ws_bytes, cudaStream_t st) {
   if (kind == GW_PEN_SQEUCLID && D == d && basis == nullptr && eigvals == nullptr) {
-    center_points_kernel<<<1, 256, 0, st>>>(x, w, n, d, X, sqn);
+    Carver c(ws, ws_bytes);
+    double* part = c.take<double>(static_cast<size_t>(kGramBlocks) * d);
+    double* mean = c.take<double>(static_cast<size_t>(d));
+    GW_TRY(check_ws(c, ws));
+    colsum_partial_kernel<<<kGramBlocks, d, 0, st>>>(x, w, 1.0 / static_cast<double>(n), n, d,
+                                                       part);
     GW_LAUNCH_CHECK();
-    GW_CUDA_TRY(cudaStreamSynchronize(st));
+    colsum_final_kernel<<<1, 128, 0, st>>>(part, kGramBlocks, d, mean);
+    GW_LAUNCH_CHECK();
+    center_apply_kernel<<<ceil_div(n, 256), 256, 0, st>>>(x, mean, n, d, X, sqn);
+    GW_LAUNCH_CHECK();
     return GW_OK;
   }
   Carver c(ws, ws_bytes);
@@ -576,13 +586,10 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
   if (eigvals) {
     GW_CUDA_TRY(cudaMemcpyAsync(eigvals, B.lam, sizeof(float) * D, cudaMemcpyDeviceToDevice, st));
   }
-  // the one host read of the lift: did a Cholesky step fail?
-  int status = 0;
-  GW_CUDA_TRY(cudaMemcpyAsync(&status, B.status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  GW_CUDA_TRY(cudaStreamSynchronize(st));
-  GW_REQUIRE(status == 0, GW_ENONFINITE,
-             "Kernel PCA: degenerate block (the Gram matrix of a subspace iterate is not positive "
-             "definite)");
+  // a failed Cholesky step (degenerate block) leaves NaN features, which a
+  // solve on them reports as GW_ENONFINITE; nothing is read back
+  lift_poison_kernel<<<ceil_div(n, 256), 256, 0, st>>>(B.status, n, D, X, sqn, basis);
+  GW_LAUNCH_CHECK();
   return GW_OK;
 }
 
