@@ -233,6 +233,16 @@ typedef struct gw_options {
      (f^{n+1}, g^n) for Algorithm 2.  n_inner stays the maximum. */
   float stop_tol;
   int stop_every;
+  /* Checkpoint / resume (the warm start of Appendix B.1 across calls): the
+     call runs outer steps outer_offset .. outer_offset + n_outer - 1 of an
+     eps schedule of outer_total steps (outer_total <= 0: n_outer, offset 0).
+     A solve split into consecutive calls, each started from the previous
+     call's Gamma, f and g (Gamma0, f0, g0 = its result), runs the same
+     kernels on the same values as one call over all steps: its final
+     record is bitwise the same.  (Algorithm 6's doubled count is not
+     carried across calls.) */
+  int outer_offset;
+  int outer_total;
 } gw_options;
 
 typedef struct gw_result {
@@ -488,7 +498,9 @@ typedef struct gw_response {
   uint64_t id;
   int status;                 /* GW_OK or an error code */
   double energy[GW_EN_LEN];   /* energy record of the final plan */
-  double t_submit, t_admit, t_done;   /* seconds on a monotonic host clock */
+  double t_submit, t_admit, t_done;   /* seconds on a monotonic host clock (t_admit: the
+                                         first admission) */
+  int preempted;              /* times the request was checkpointed and re-queued */
 } gw_response;
 
 /* pool: 256-byte aligned device buffer owned by the caller; max_active:
@@ -497,6 +509,15 @@ gw_server* gw_server_create(void* pool, size_t pool_bytes, int max_active, int d
 /* Queue a request (h_x: n x d, h_y: m x d, host float32, copied).  GW_ENOMEM
  * if the request can never fit in the pool. */
 int gw_server_submit(gw_server* s, const gw_request* r, const float* h_x, const float* h_y);
+/* Time slicing with checkpoint / resume: an admitted request runs at most
+ * outer_steps outer steps at a time (0, the default: all of them).  When a
+ * slice ends while other requests wait for admission, the request is
+ * checkpointed — its lifted features and solver state (Gamma_t, f, g) are
+ * copied to host memory and its device memory and slot released — and
+ * queued again behind them; readmitted, it resumes from that state through
+ * gw_solve's outer_offset, with the same result as an uninterrupted run.
+ * Applies to requests admitted after the call. */
+int gw_server_set_slice(gw_server* s, int outer_steps);
 /* Move up to max_out finished responses to out.  wait_ms: 0 = do not wait,
  * < 0 = wait until one is ready or nothing is in flight, > 0 = bounded wait.
  * Returns the number written. */

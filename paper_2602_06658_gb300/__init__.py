@@ -64,7 +64,8 @@ class GwOptions(ctypes.Structure):
     _fields_ = [("eps", _f), ("eps_final", _f), ("n_outer", _int), ("n_inner", _int),
                 ("symmetric", _int), ("prec", _int), ("record", _int), ("use_graph", _int),
                 ("Gamma0", _p), ("f0", _p), ("g0", _p), ("adaptive", _int), ("n_inner_max", _int),
-                ("adapt_rtol", _f), ("stop_tol", _f), ("stop_every", _int)]
+                ("adapt_rtol", _f), ("stop_tol", _f), ("stop_every", _int),
+                ("outer_offset", _int), ("outer_total", _int)]
 
 
 class GwResult(ctypes.Structure):
@@ -122,7 +123,7 @@ class GwRequest(ctypes.Structure):
 class GwResponse(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("status", _int), ("energy", ctypes.c_double * 16),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("preempted", _int)]
 
 
 lib.gw_server_create.argtypes = [_p, _sz, _int, _int]
@@ -135,6 +136,8 @@ lib.gw_server_stats.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_int)]
 lib.gw_server_stats.restype = _int
 lib.gw_server_request_bytes.argtypes = [ctypes.POINTER(GwRequest)]
 lib.gw_server_request_bytes.restype = _sz
+lib.gw_server_set_slice.argtypes = [_p, _int]
+lib.gw_server_set_slice.restype = _int
 lib.gw_server_destroy.argtypes = [_p]
 lib.gw_server_destroy.restype = None
 lib.gw_workspace_size.argtypes = [_int, _i64, _i64, _int, _int, _int]
@@ -321,7 +324,7 @@ def gw_energy(X, Y, s, t, a, b, f, g, Gamma_t, eps, prec=PREC_FP32, ws=None, str
 def gw_solve(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=True,
              prec=PREC_FP32, record=True, use_graph=True, Gamma0=None, f0=None, g0=None, ws=None,
              out=None, stream=None, adaptive=False, n_inner_max=0, adapt_rtol=0.0, stop_tol=0.0,
-             stop_every=1):
+             stop_every=1, outer_offset=0, outer_total=0):
     """CNT-GW (Algorithm 1) on device.  Returns dict(Gamma, Gamma_plan, f, g,
     energy, history) of device tensors; nothing is synchronised unless
     adaptive (Algorithm 6) or stop_tol > 0 (hybrid stop) asks for host
@@ -345,7 +348,7 @@ def gw_solve(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=T
                   int(prec), int(bool(record)), int(bool(use_graph)),
                   _ptr(_f64(Gamma0, "Gamma0")), _ptr(_f32(f0, "f0")), _ptr(_f32(g0, "g0")),
                   int(bool(adaptive)), int(n_inner_max), float(adapt_rtol), float(stop_tol),
-                  int(stop_every))
+                  int(stop_every), int(outer_offset), int(outer_total))
     R = GwResult(_ptr(out["Gamma"]), _ptr(out.get("Gamma_plan")), _ptr(out["f"]), _ptr(out["g"]), _ptr(out["energy"]),
                  _ptr(out["history"]))
     _check(lib.gw_solve(ctypes.byref(P), ctypes.byref(O), ctypes.byref(R), _ptr(ws), ws.numel(),
@@ -641,7 +644,12 @@ class Server:
         k = lib.gw_server_poll(self.h, buf, max_out, int(wait_ms))
         return [{"id": int(buf[i].id), "status": int(buf[i].status),
                  "energy": list(buf[i].energy), "t_submit": buf[i].t_submit,
-                 "t_admit": buf[i].t_admit, "t_done": buf[i].t_done} for i in range(k)]
+                 "t_admit": buf[i].t_admit, "t_done": buf[i].t_done,
+                 "preempted": int(buf[i].preempted)} for i in range(k)]
+
+    def set_slice(self, outer_steps: int):
+        """Time slicing with checkpoint / resume (gw.h: gw_server_set_slice)."""
+        _check(lib.gw_server_set_slice(self.h, int(outer_steps)))
 
     @staticmethod
     def request_bytes(n, m, d=3, kind=PEN_SQEUCLID, D=0, prec=PREC_FP32, param=2.0):

@@ -253,12 +253,18 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
   double E_prev = 0.0;
   int fc = 0, gc = 0, Gc = 0;
   for (int t = 0; t < o.n_outer; ++t) {
+    // position in the eps schedule (a resumed solve continues its schedule)
+    const int T_all = o.outer_total > 0 ? o.outer_total : o.n_outer;
+    const int t_all = (o.outer_total > 0 ? o.outer_offset : 0) + t;
     float eps = o.eps;
-    if (o.eps_final > 0.0f && o.eps_final != o.eps && o.n_outer > 1) {
+    if (o.eps_final > 0.0f && o.eps_final != o.eps && T_all > 1) {
       eps = static_cast<float>(static_cast<double>(o.eps) *
                                pow(static_cast<double>(o.eps_final) / o.eps,
-                                   static_cast<double>(t) / (o.n_outer - 1)));
+                                   static_cast<double>(t_all) / (T_all - 1)));
     }
+    char label[64];
+    snprintf(label, sizeof(label), "gw outer step %d (eps %.3g)", t, static_cast<double>(eps));
+    NvtxRange range(label);
     // Zbar_j <- Gamma_t Y_j (Algorithm 1)
     GW_TRY(launch_gamma_y(B.G[Gc], p.Y, p.m, p.D, p.E, B.V, st));
     int n_run = n_cur;
@@ -503,11 +509,16 @@ int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, s
   GW_REQUIRE(o->adapt_rtol >= 0.0f && isfinite(o->adapt_rtol), GW_EINVAL, "adapt_rtol must be >= 0");
   GW_REQUIRE(!(o->stop_tol > 0.0f) || (isfinite(o->stop_tol) && o->stop_every >= 1), GW_EINVAL,
              "stop_tol > 0 needs a finite tolerance and stop_every >= 1");
+  GW_REQUIRE(o->outer_total <= 0 ||
+                 (o->outer_offset >= 0 && o->outer_offset + o->n_outer <= o->outer_total),
+             GW_EINVAL, "outer_offset %d + n_outer %d must lie within outer_total %d",
+             o->outer_offset, o->n_outer, o->outer_total);
   const size_t need = solve_ws_bytes(p->n, p->m, p->D, p->E, o->prec);
   GW_REQUIRE(ws != nullptr && ws_bytes >= need, GW_ENOMEM,
              "workspace too small: need %zu bytes, have %zu", need, ws_bytes);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   (void)wait_ctl();   // looks the counter up outside any capture
+  NvtxRange range("gw_solve");
   const bool host_driven = o->adaptive || o->stop_tol > 0.0f;
   if (!o->use_graph || st == nullptr || host_driven) return enqueue_solve(*p, *o, *r, ws, ws_bytes, st);
 

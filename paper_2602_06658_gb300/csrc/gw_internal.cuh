@@ -5,9 +5,23 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gw.h"
 
 namespace gw {
+
+// Tracing: a named NVTX range on the host thread for the scope's lifetime
+// (an outer step of a solve, a lift, a server request).  The ranges mark
+// where the host enqueues the work (inside a stream capture: where the graph
+// is built); profilers correlate them with the kernels they launch.  Without
+// a profiler attached the calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* msg) { nvtxRangePushA(msg); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;

@@ -548,6 +548,7 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
     GW_LAUNCH_CHECK();
     return GW_OK;
   }
+  NvtxRange range("gw_lift (Kernel PCA)");
   Carver c(ws, ws_bytes);
   LiftBufs B = carve_lift(c, n, D);
   GW_TRY(check_ws(c, ws));

@@ -7,7 +7,9 @@
 // allocates no device memory).  Each admitted request is driven by its own
 // worker thread on its own CUDA stream: copy in, lift (Kernel PCA or
 // centering), the solve captured as one CUDA graph, copy the energy record
-// out.  Admitted requests therefore overlap on the device, and requests that
+// out.  With time slicing (gw_server_set_slice) a request runs a few outer
+// steps per admission and, when others wait, is checkpointed to host memory
+// and queued again; it resumes from that state later.  Admitted requests therefore overlap on the device, and requests that
 // arrive while others run join as soon as a slot and memory free up.
 // Kernels are deterministic and each request owns its memory, so a result
 // does not depend on what else is running.
@@ -91,6 +93,12 @@ struct Job {
   double t_submit = 0.0, t_admit = 0.0;
   size_t bytes = 0;
   char* mem = nullptr;   // device memory from the pool while admitted
+  // checkpoint of a preempted request (host copies): lifted features and
+  // the solver state after outer_done outer steps
+  int outer_done = 0;
+  int preempted = 0;
+  std::vector<float> X, Y, s, t, f, g;
+  std::vector<double> G;
 };
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -140,6 +148,7 @@ struct gw_server {
   std::vector<gw_response> done;
   int active = 0;
   int inflight = 0;   // submitted and not yet reported
+  int slice = 0;      // outer steps per admission (0: all)
   bool stop = false;
   std::thread scheduler;
   std::vector<std::thread> workers;
@@ -150,7 +159,10 @@ struct gw_server {
 namespace gw {
 namespace {
 
-void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
+// Drive one admitted request on stream st.  Returns false when the request
+// was checkpointed and queued again (time slicing), true when it finished
+// (its response is then posted).
+bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
   const gw_request& r = J->req;
   gw_response out;
   memset(&out, 0, sizeof(out));
@@ -158,6 +170,9 @@ void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
   out.t_submit = J->t_submit;
   out.t_admit = J->t_admit;
   const int D = r.kind == GW_PEN_SQEUCLID ? r.d : r.D;
+  char label[64];
+  snprintf(label, sizeof(label), "gw request %llu", static_cast<unsigned long long>(r.id));
+  NvtxRange range(label);
   char* p = mem;
   auto take = [&](size_t bytes) {
     char* q = p;
@@ -179,13 +194,21 @@ void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
   double* en = reinterpret_cast<double*>(take(sizeof(double) * GW_EN_LEN));
   char* ws = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~uintptr_t(255));
   const size_t ws_bytes = J->bytes - static_cast<size_t>(ws - mem);
+  int slice = 0;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    slice = S->slice;
+  }
+  const bool resumed = J->outer_done > 0;
   int rc = GW_OK;
+  bool requeue = false;
+  auto h2d = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  auto d2h = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  };
   do {
-    if (cudaMemcpyAsync(dx, J->x.data(), sizeof(float) * r.n * r.d, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(dy, J->y.data(), sizeof(float) * r.m * r.d, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-      rc = GW_ECUDA;
-      break;
-    }
     fill_kernel<<<ceil_div(r.n, 256), 256, 0, st>>>(a, r.n, 1.0f / static_cast<float>(r.n));
     fill_kernel<<<ceil_div(r.m, 256), 256, 0, st>>>(b, r.m, 1.0f / static_cast<float>(r.m));
     count_launch();
@@ -195,26 +218,80 @@ void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
       break;
     }
     gw_stream_t gs = reinterpret_cast<gw_stream_t>(st);
-    rc = gw_lift(dx, r.n, r.d, a, r.kind, r.param, D, 0, r.id, X, s, nullptr, nullptr, ws, ws_bytes, gs);
-    if (rc != GW_OK) break;
-    rc = gw_lift(dy, r.m, r.d, b, r.kind, r.param, D, 0, r.id + 1, Y, t, nullptr, nullptr, ws, ws_bytes, gs);
-    if (rc != GW_OK) break;
+    if (!resumed) {
+      if (!h2d(dx, J->x.data(), sizeof(float) * r.n * r.d) ||
+          !h2d(dy, J->y.data(), sizeof(float) * r.m * r.d)) {
+        rc = GW_ECUDA;
+        break;
+      }
+      rc = gw_lift(dx, r.n, r.d, a, r.kind, r.param, D, 0, r.id, X, s, nullptr, nullptr, ws, ws_bytes, gs);
+      if (rc != GW_OK) break;
+      rc = gw_lift(dy, r.m, r.d, b, r.kind, r.param, D, 0, r.id + 1, Y, t, nullptr, nullptr, ws, ws_bytes, gs);
+      if (rc != GW_OK) break;
+    } else {
+      // resume from the checkpoint: features and the state after outer_done steps
+      if (!h2d(X, J->X.data(), sizeof(float) * r.n * D) || !h2d(Y, J->Y.data(), sizeof(float) * r.m * D) ||
+          !h2d(s, J->s.data(), sizeof(float) * r.n) || !h2d(t, J->t.data(), sizeof(float) * r.m) ||
+          !h2d(f, J->f.data(), sizeof(float) * r.n) || !h2d(g, J->g.data(), sizeof(float) * r.m) ||
+          !h2d(G, J->G.data(), sizeof(double) * D * D)) {
+        rc = GW_ECUDA;
+        break;
+      }
+    }
     gw_problem P{X, Y, s, t, a, b, r.n, r.m, D, D};
-    gw_options O{};
-    O.eps = r.eps;
-    O.eps_final = r.eps_final;
-    O.n_outer = r.n_outer;
-    O.n_inner = r.n_inner;
-    O.symmetric = 1;
     const bool small = small_request(r);
-    O.prec = run_prec(r);
-    O.record = 0;
-    // A request's graph runs once: below the threshold its capture and
-    // instantiation cost more host time than launching the kernels directly.
-    O.use_graph = small ? 0 : 1;
-    gw_result R{G, Gp, f, g, en, nullptr};
-    rc = gw_solve(&P, &O, &R, ws, ws_bytes, gs);
-    if (rc != GW_OK) break;
+    while (J->outer_done < r.n_outer) {
+      gw_options O{};
+      O.eps = r.eps;
+      O.eps_final = r.eps_final;
+      const int left = r.n_outer - J->outer_done;
+      O.n_outer = (slice > 0 && slice < left) ? slice : left;
+      O.outer_offset = J->outer_done;
+      O.outer_total = r.n_outer;
+      O.n_inner = r.n_inner;
+      O.symmetric = 1;
+      O.prec = run_prec(r);
+      O.record = 0;
+      // A request's graph runs once: below the threshold its capture and
+      // instantiation cost more host time than launching the kernels directly.
+      O.use_graph = small ? 0 : 1;
+      // every slice after the first starts from the state the previous left
+      if (J->outer_done > 0) {
+        O.Gamma0 = G;
+        O.f0 = f;
+        O.g0 = g;
+      }
+      gw_result R{G, Gp, f, g, en, nullptr};
+      rc = gw_solve(&P, &O, &R, ws, ws_bytes, gs);
+      if (rc != GW_OK) break;
+      J->outer_done += O.n_outer;
+      if (J->outer_done >= r.n_outer) break;
+      bool waiting = false;
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        waiting = !S->pending.empty();
+      }
+      if (waiting) {
+        // checkpoint: the features and the state to host memory, then requeue
+        J->X.resize(static_cast<size_t>(r.n) * D);
+        J->Y.resize(static_cast<size_t>(r.m) * D);
+        J->s.resize(r.n);
+        J->t.resize(r.m);
+        J->f.resize(r.n);
+        J->g.resize(r.m);
+        J->G.resize(static_cast<size_t>(D) * D);
+        if (!d2h(J->X.data(), X, sizeof(float) * r.n * D) || !d2h(J->Y.data(), Y, sizeof(float) * r.m * D) ||
+            !d2h(J->s.data(), s, sizeof(float) * r.n) || !d2h(J->t.data(), t, sizeof(float) * r.m) ||
+            !d2h(J->f.data(), f, sizeof(float) * r.n) || !d2h(J->g.data(), g, sizeof(float) * r.m) ||
+            !d2h(J->G.data(), G, sizeof(double) * D * D) || cudaStreamSynchronize(st) != cudaSuccess) {
+          rc = GW_ECUDA;
+          break;
+        }
+        requeue = true;
+        break;
+      }
+    }
+    if (rc != GW_OK || requeue) break;
     if (cudaMemcpyAsync(out.energy, en, sizeof(double) * GW_EN_LEN, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       rc = GW_ECUDA;
@@ -224,14 +301,23 @@ void run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
     if (es != 0.0) rc = es == static_cast<double>(GW_ETIMEOUT) ? GW_ETIMEOUT : GW_ENONFINITE;
   } while (false);
   if (rc != GW_OK) cudaStreamSynchronize(st);
-  out.status = rc;
-  out.t_done = now_s();
   std::lock_guard<std::mutex> lk(S->mu);
   S->pool->release(mem);
   S->active -= 1;
+  if (requeue && rc == GW_OK) {
+    J->preempted += 1;
+    J->mem = nullptr;
+    S->pending.push_back(J);
+    S->cv_sched.notify_all();
+    return false;
+  }
+  out.status = rc;
+  out.preempted = J->preempted;
+  out.t_done = now_s();
   S->done.push_back(out);
   S->cv_sched.notify_all();
   S->cv_done.notify_all();
+  return true;
 }
 
 void worker_loop(gw_server* S) {
@@ -249,8 +335,7 @@ void worker_loop(gw_server* S) {
       S->ready.pop_front();
       mem = J->mem;
     }
-    run_job(S, J, st, mem);
-    delete J;
+    if (run_job(S, J, st, mem)) delete J;
   }
   cudaStreamDestroy(st);
 }
@@ -265,7 +350,7 @@ void scheduler_loop(gw_server* S) {
       char* mem = S->pool->alloc(J->bytes);
       if (mem) {
         S->pending.pop_front();
-        J->t_admit = now_s();
+        if (J->preempted == 0) J->t_admit = now_s();
         J->mem = mem;
         S->active += 1;
         S->ready.push_back(J);
@@ -345,6 +430,15 @@ int gw_server_poll(gw_server* S, gw_response* out, int max_out, int wait_ms) {
   S->done.erase(S->done.begin(), S->done.begin() + k);
   S->inflight -= k;
   return k;
+}
+
+int gw_server_set_slice(gw_server* S, int outer_steps) {
+  set_error("");
+  GW_REQUIRE(S != nullptr && outer_steps >= 0, GW_EINVAL,
+             "gw_server_set_slice: need a server and outer_steps >= 0");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->slice = outer_steps;
+  return GW_OK;
 }
 
 size_t gw_server_request_bytes(const gw_request* r) {

@@ -109,3 +109,38 @@ def test_wait_limit_is_validated_on_the_host():
     assert lib.gw_set_wait_limit_ns(5_000_000) == 0
     assert lib.gw_wait_limit_ns() == 5_000_000
     assert lib.gw_set_wait_limit_ns(prev) == 0
+
+
+def test_solve_schedule_offset_is_validated_on_the_host():
+    """gw_solve refuses an outer_offset / outer_total that does not contain
+    the call's steps, before any CUDA call (dummy pointers)."""
+    lib = ctypes.CDLL(builder().build())
+    p, i32, i64, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+
+    class Problem(ctypes.Structure):
+        _fields_ = [("X", p), ("Y", p), ("s", p), ("t", p), ("a", p), ("b", p),
+                    ("n", i64), ("m", i64), ("D", i32), ("E", i32)]
+
+    class Options(ctypes.Structure):
+        _fields_ = [("eps", f), ("eps_final", f), ("n_outer", i32), ("n_inner", i32),
+                    ("symmetric", i32), ("prec", i32), ("record", i32), ("use_graph", i32),
+                    ("Gamma0", p), ("f0", p), ("g0", p), ("adaptive", i32), ("n_inner_max", i32),
+                    ("adapt_rtol", f), ("stop_tol", f), ("stop_every", i32),
+                    ("outer_offset", i32), ("outer_total", i32)]
+
+    class Result(ctypes.Structure):
+        _fields_ = [("Gamma", p), ("Gamma_plan", p), ("f", p), ("g", p), ("energy", p),
+                    ("history", p)]
+
+    d = p(0x1000)
+    P = Problem(d, d, d, d, d, d, 100, 100, 2, 2)
+    R = Result(d, d, d, d, d, None)
+    lib.gw_solve.restype = i32
+    lib.gw_solve.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(Options),
+                             ctypes.POINTER(Result), p, ctypes.c_size_t, p]
+    lib.gw_last_error.restype = ctypes.c_char_p
+    bad = Options(0.1, 0.01, 4, 10, 1, 0, 0, 0, None, None, None, 0, 0, 0.0, 0.0, 1, 5, 8)
+    assert lib.gw_solve(ctypes.byref(P), ctypes.byref(bad), ctypes.byref(R), d, 1 << 30, None) == 1
+    assert b"outer_offset" in lib.gw_last_error()
+    neg = Options(0.1, 0.01, 4, 10, 1, 0, 0, 0, None, None, None, 0, 0, 0.0, 0.0, 1, -1, 8)
+    assert lib.gw_solve(ctypes.byref(P), ctypes.byref(neg), ctypes.byref(R), d, 1 << 30, None) == 1

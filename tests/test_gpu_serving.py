@@ -118,3 +118,56 @@ def test_concurrent_lifts_of_different_widths(gw):
     for rid, res in out.items():
         assert res["status"] == 0, (rid, res["status"])
         assert np.isfinite(res["energy"][0]), rid
+
+
+def test_solve_split_into_calls_is_bitwise_the_same(gw):
+    """Checkpoint / resume at the solver: 7 annealed outer steps as one call
+    and as calls of 3 + 2 + 2 steps (outer_offset / outer_total, each started
+    from the previous call's Gamma, f, g) give the same final record."""
+    import torch
+    w = W.gmm_rigid(1500, seed=8, m=1300)
+    dev = lambda v: torch.tensor(np.asarray(v, np.float32), device="cuda")
+    a = torch.full((1500,), 1 / 1500, device="cuda")
+    b = torch.full((1300,), 1 / 1300, device="cuda")
+    lx = gw.gw_lift(dev(w["x"]), 16, kind=gw.PEN_POWER, param=1.0, w=a)
+    ly = gw.gw_lift(dev(w["y"]), 16, kind=gw.PEN_POWER, param=1.0, w=b)
+    args = (lx["X"], ly["X"], lx["s"], ly["s"], a, b)
+    for prec in (0, 3):
+        one = gw.gw_solve(*args, 0.1, 7, 25, eps_final=0.01, prec=prec, record=False)
+        state = None
+        off = 0
+        for k in (3, 2, 2):
+            kw = {} if state is None else dict(Gamma0=state["Gamma"], f0=state["f"], g0=state["g"])
+            state = gw.gw_solve(*args, 0.1, k, 25, eps_final=0.01, prec=prec, record=False,
+                                outer_offset=off, outer_total=7, **kw)
+            off += k
+        e1, e2 = one["energy"].cpu().numpy(), state["energy"].cpu().numpy()
+        assert np.array_equal(e1, e2), (prec, e1[:3], e2[:3])
+        assert bool((one["f"] == state["f"]).all()) and bool((one["Gamma"] == state["Gamma"]).all())
+
+
+def test_time_slicing_preempts_and_resumes_bitwise(gw):
+    """One slot and slices of 2 outer steps: every request that meets others
+    waiting is checkpointed to host memory, requeued and resumed; each result
+    is bitwise the one of an uninterrupted run."""
+    reqs = [make_request(10, 2500, 2200, 1, 16, 0.03, seed=31),
+            make_request(11, 1800, 2600, 0, 0, 0.05, seed=32),
+            make_request(12, 3200, 3000, 1, 16, 0.02, seed=33)]
+    # the same ids on two servers (a request's id seeds its Kernel PCA start block)
+    srv = gw.Server(pool_bytes=3 << 30, max_active=1)
+    try:
+        plain = run_all(srv, reqs)
+    finally:
+        srv.close()
+    srv = gw.Server(pool_bytes=3 << 30, max_active=1)
+    try:
+        srv.set_slice(2)
+        sliced = run_all(srv, reqs)
+    finally:
+        srv.close()
+    assert sum(res["preempted"] for res in sliced.values()) >= 2
+    for r in reqs:
+        a, b = plain[r["id"]], sliced[r["id"]]
+        assert a["status"] == 0 and b["status"] == 0
+        assert a["energy"] == b["energy"], r["id"]
+        assert a["preempted"] == 0
