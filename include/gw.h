@@ -52,6 +52,7 @@ typedef struct CUstream_st* gw_stream_t;
 #define GW_ENONFINITE 4    /* NaN/Inf met in potentials or energy */
 #define GW_ETIMEOUT 5      /* a bounded device wait expired */
 #define GW_EUNSUPPORTED 6  /* feature dimension or precision not supported */
+#define GW_ECANCELED 7     /* a server request was cancelled (gw_server_cancel) */
 
 /* cost-tile precision of the softmin / plan kernels.  The log-sum-exp, the
  * potentials and all accumulations stay float32 (Gamma and energies float64)
@@ -518,6 +519,17 @@ int gw_server_submit(gw_server* s, const gw_request* r, const float* h_x, const 
  * gw_solve's outer_offset, with the same result as an uninterrupted run.
  * Applies to requests admitted after the call. */
 int gw_server_set_slice(gw_server* s, int outer_steps);
+/* Cancel request `id`: a pending request is answered at once, a running one
+ * at its next slice boundary (with time slicing; without it, when its solve
+ * ends), in both cases with status GW_ECANCELED.  GW_EINVAL if no request
+ * with that id is in flight. */
+int gw_server_cancel(gw_server* s, uint64_t id);
+/* Host watchdog: a request not finished `seconds` after its submission
+ * (<= 0: no limit, the default) is stopped at its next slice boundary, or
+ * instead of being admitted, and answered with GW_ETIMEOUT.  With time
+ * slicing every slice ends with a stream synchronisation, so the check
+ * follows the request's progress on the device (its heartbeat). */
+int gw_server_set_deadline(gw_server* s, double seconds);
 /* Move up to max_out finished responses to out.  wait_ms: 0 = do not wait,
  * < 0 = wait until one is ready or nothing is in flight, > 0 = bounded wait.
  * Returns the number written. */

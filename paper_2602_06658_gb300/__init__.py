@@ -34,7 +34,7 @@ EN = {"E": 0, "L": 1, "KL": 2, "C": 3, "Gamma2": 4, "T": 5, "row_l1": 6, "col_l1
       "row_relmax": 8, "col_relmax": 9, "mass": 10, "dGamma": 11, "eps": 12, "status": 13,
       "n_inner": 14, "stop_err": 15}
 _STATUS = {1: "GW_EINVAL", 2: "GW_ENOMEM", 3: "GW_ECUDA", 4: "GW_ENONFINITE", 5: "GW_ETIMEOUT",
-           6: "GW_EUNSUPPORTED"}
+           6: "GW_EUNSUPPORTED", 7: "GW_ECANCELED"}
 
 
 class GWError(RuntimeError):
@@ -138,6 +138,10 @@ lib.gw_server_request_bytes.argtypes = [ctypes.POINTER(GwRequest)]
 lib.gw_server_request_bytes.restype = _sz
 lib.gw_server_set_slice.argtypes = [_p, _int]
 lib.gw_server_set_slice.restype = _int
+lib.gw_server_cancel.argtypes = [_p, ctypes.c_uint64]
+lib.gw_server_cancel.restype = _int
+lib.gw_server_set_deadline.argtypes = [_p, ctypes.c_double]
+lib.gw_server_set_deadline.restype = _int
 lib.gw_server_destroy.argtypes = [_p]
 lib.gw_server_destroy.restype = None
 lib.gw_workspace_size.argtypes = [_int, _i64, _i64, _int, _int, _int]
@@ -650,6 +654,14 @@ class Server:
     def set_slice(self, outer_steps: int):
         """Time slicing with checkpoint / resume (gw.h: gw_server_set_slice)."""
         _check(lib.gw_server_set_slice(self.h, int(outer_steps)))
+
+    def cancel(self, id):
+        """Cancel request `id` (gw.h: gw_server_cancel); answered with GW_ECANCELED."""
+        _check(lib.gw_server_cancel(self.h, int(id)))
+
+    def set_deadline(self, seconds: float):
+        """Host watchdog deadline per request (gw.h: gw_server_set_deadline)."""
+        _check(lib.gw_server_set_deadline(self.h, float(seconds)))
 
     @staticmethod
     def request_bytes(n, m, d=3, kind=PEN_SQEUCLID, D=0, prec=PREC_FP32, param=2.0):

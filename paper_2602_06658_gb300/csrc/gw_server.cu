@@ -97,6 +97,7 @@ struct Job {
   // the solver state after outer_done outer steps
   int outer_done = 0;
   int preempted = 0;
+  int stop_code = 0;     // GW_ECANCELED / GW_ETIMEOUT once asked to stop
   std::vector<float> X, Y, s, t, f, g;
   std::vector<double> G;
 };
@@ -149,6 +150,8 @@ struct gw_server {
   int active = 0;
   int inflight = 0;   // submitted and not yet reported
   int slice = 0;      // outer steps per admission (0: all)
+  double deadline = 0.0;                 // seconds after submission (0: none)
+  std::vector<gw::Job*> running;         // admitted (ready or on a worker)
   bool stop = false;
   std::thread scheduler;
   std::vector<std::thread> workers;
@@ -195,10 +198,19 @@ bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
   char* ws = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~uintptr_t(255));
   const size_t ws_bytes = J->bytes - static_cast<size_t>(ws - mem);
   int slice = 0;
+  double deadline = 0.0;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     slice = S->slice;
+    deadline = S->deadline;
   }
+  // the host watchdog: cancelled, or past its deadline?
+  auto stop_code = [&]() {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (J->stop_code == 0 && deadline > 0.0 && now_s() > J->t_submit + deadline)
+      J->stop_code = GW_ETIMEOUT;
+    return J->stop_code;
+  };
   const bool resumed = J->outer_done > 0;
   int rc = GW_OK;
   bool requeue = false;
@@ -209,6 +221,7 @@ bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) == cudaSuccess;
   };
   do {
+    if ((rc = stop_code()) != GW_OK) break;
     fill_kernel<<<ceil_div(r.n, 256), 256, 0, st>>>(a, r.n, 1.0f / static_cast<float>(r.n));
     fill_kernel<<<ceil_div(r.m, 256), 256, 0, st>>>(b, r.m, 1.0f / static_cast<float>(r.m));
     count_launch();
@@ -266,6 +279,13 @@ bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
       if (rc != GW_OK) break;
       J->outer_done += O.n_outer;
       if (J->outer_done >= r.n_outer) break;
+      // a slice boundary: wait for the slice (the heartbeat the watchdog
+      // follows), then honour a cancel or a passed deadline
+      if (cudaStreamSynchronize(st) != cudaSuccess) {
+        rc = GW_ECUDA;
+        break;
+      }
+      if ((rc = stop_code()) != GW_OK) break;
       bool waiting = false;
       {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -304,6 +324,11 @@ bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
   std::lock_guard<std::mutex> lk(S->mu);
   S->pool->release(mem);
   S->active -= 1;
+  S->running.erase(std::remove(S->running.begin(), S->running.end(), J), S->running.end());
+  if (requeue && rc == GW_OK && J->stop_code != 0) {
+    requeue = false;      // asked to stop during the checkpoint
+    rc = J->stop_code;
+  }
   if (requeue && rc == GW_OK) {
     J->preempted += 1;
     J->mem = nullptr;
@@ -345,11 +370,30 @@ void scheduler_loop(gw_server* S) {
   while (!S->stop) {
     // admit in arrival order while a slot and memory are free
     bool admitted = false;
+    if (!S->pending.empty() && S->deadline > 0.0 &&
+        now_s() > S->pending.front()->t_submit + S->deadline) {
+      // past its deadline before it could run: answered without running
+      Job* J = S->pending.front();
+      S->pending.pop_front();
+      gw_response out;
+      memset(&out, 0, sizeof(out));
+      out.id = J->req.id;
+      out.status = GW_ETIMEOUT;
+      out.t_submit = J->t_submit;
+      out.t_admit = J->t_admit;
+      out.t_done = now_s();
+      out.preempted = J->preempted;
+      S->done.push_back(out);
+      S->cv_done.notify_all();
+      delete J;
+      continue;
+    }
     if (!S->pending.empty() && S->active < S->max_active) {
       Job* J = S->pending.front();
       char* mem = S->pool->alloc(J->bytes);
       if (mem) {
         S->pending.pop_front();
+        S->running.push_back(J);
         if (J->preempted == 0) J->t_admit = now_s();
         J->mem = mem;
         S->active += 1;
@@ -358,7 +402,11 @@ void scheduler_loop(gw_server* S) {
         admitted = true;
       }
     }
-    if (!admitted) S->cv_sched.wait(lk);
+    if (!admitted) {
+      // with a deadline, look again at least every 10 ms
+      if (S->deadline > 0.0) S->cv_sched.wait_for(lk, std::chrono::milliseconds(10));
+      else S->cv_sched.wait(lk);
+    }
   }
 }
 
@@ -438,6 +486,46 @@ int gw_server_set_slice(gw_server* S, int outer_steps) {
              "gw_server_set_slice: need a server and outer_steps >= 0");
   std::lock_guard<std::mutex> lk(S->mu);
   S->slice = outer_steps;
+  return GW_OK;
+}
+
+int gw_server_cancel(gw_server* S, uint64_t id) {
+  set_error("");
+  GW_REQUIRE(S != nullptr, GW_EINVAL, "gw_server_cancel: null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
+    if ((*it)->req.id != id) continue;
+    Job* J = *it;
+    S->pending.erase(it);
+    gw_response out;
+    memset(&out, 0, sizeof(out));
+    out.id = id;
+    out.status = GW_ECANCELED;
+    out.t_submit = J->t_submit;
+    out.t_admit = J->t_admit;
+    out.t_done = now_s();
+    out.preempted = J->preempted;
+    S->done.push_back(out);
+    S->cv_done.notify_all();
+    S->cv_sched.notify_all();
+    delete J;
+    return GW_OK;
+  }
+  for (Job* J : S->running) {
+    if (J->req.id != id) continue;
+    if (J->stop_code == 0) J->stop_code = GW_ECANCELED;
+    return GW_OK;
+  }
+  set_error("gw_server_cancel: no request %llu in flight", static_cast<unsigned long long>(id));
+  return GW_EINVAL;
+}
+
+int gw_server_set_deadline(gw_server* S, double seconds) {
+  set_error("");
+  GW_REQUIRE(S != nullptr && isfinite(seconds), GW_EINVAL, "gw_server_set_deadline: bad argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->deadline = seconds > 0.0 ? seconds : 0.0;
+  S->cv_sched.notify_all();
   return GW_OK;
 }
 

@@ -144,3 +144,15 @@ def test_solve_schedule_offset_is_validated_on_the_host():
     assert b"outer_offset" in lib.gw_last_error()
     neg = Options(0.1, 0.01, 4, 10, 1, 0, 0, 0, None, None, None, 0, 0, 0.0, 0.0, 1, -1, 8)
     assert lib.gw_solve(ctypes.byref(P), ctypes.byref(neg), ctypes.byref(R), d, 1 << 30, None) == 1
+
+
+def test_server_controls_refuse_a_null_server():
+    """gw_server_cancel / gw_server_set_deadline / gw_server_set_slice check
+    their arguments on the host (no server, no device touched)."""
+    lib = ctypes.CDLL(builder().build())
+    lib.gw_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    lib.gw_server_set_deadline.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    lib.gw_server_set_slice.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.gw_server_cancel(None, 1) == 1
+    assert lib.gw_server_set_deadline(None, 1.0) == 1
+    assert lib.gw_server_set_slice(None, 1) == 1

@@ -171,3 +171,82 @@ def test_time_slicing_preempts_and_resumes_bitwise(gw):
         assert a["status"] == 0 and b["status"] == 0
         assert a["energy"] == b["energy"], r["id"]
         assert a["preempted"] == 0
+
+
+def long_request(rid, n, n_outer, seed):
+    r = make_request(rid, n, n, 0, 0, 0.05, seed=seed)
+    r["n_outer"] = n_outer
+    return r
+
+
+def wait_for(pred, seconds=60.0):
+    t_end = time.time() + seconds
+    while time.time() < t_end:
+        if pred():
+            return True
+        time.sleep(0.005)
+    return False
+
+
+def test_cancel_pending_and_running(gw):
+    """One slot, slices of one outer step: a pending request is answered
+    GW_ECANCELED at once without being admitted; a running one stops at its
+    next slice boundary with GW_ECANCELED; the request between them is
+    unaffected (bitwise its result alone); an unknown id is GW_EINVAL."""
+    A = long_request(20, 20000, 400, seed=41)
+    B = make_request(21, 2000, 1800, 0, 0, 0.05, seed=42)
+    C = long_request(22, 20000, 400, seed=43)
+    srv = gw.Server(pool_bytes=3 << 30, max_active=1)
+    try:
+        alone = run_all(srv, [B])[21]
+    finally:
+        srv.close()
+    srv = gw.Server(pool_bytes=3 << 30, max_active=1)
+    try:
+        srv.set_slice(1)
+        for r in (A, B, C):
+            srv.submit(**r)
+        assert wait_for(lambda: srv.stats()["active"] == 1)
+        srv.cancel(22)                                  # pending behind A and B
+        srv.cancel(20)                                  # admitted: stops at a slice boundary
+        with pytest.raises(gw.GWError):
+            srv.cancel(999)
+        out = {}
+        t_end = time.time() + 300
+        while len(out) < 3 and time.time() < t_end:
+            for res in srv.poll(64, wait_ms=200):
+                out[res["id"]] = res
+    finally:
+        srv.close()
+    assert out[22]["status"] == 7 and out[22]["t_admit"] == 0.0
+    assert out[20]["status"] == 7 and out[20]["t_admit"] > 0.0
+    assert out[21]["status"] == 0 and out[21]["energy"] == alone["energy"]
+    # A stopped long before its 400 steps would have ended
+    assert out[20]["t_done"] - out[20]["t_admit"] < 5.0
+
+
+def test_deadline_watchdog(gw):
+    """A 0.3 s deadline: a long request is stopped at a slice boundary with
+    GW_ETIMEOUT, one waiting behind it is answered GW_ETIMEOUT; after the
+    deadline is lifted the server answers a normal request as before."""
+    srv = gw.Server(pool_bytes=3 << 30, max_active=1)
+    try:
+        srv.set_slice(1)
+        srv.set_deadline(0.3)
+        srv.submit(**long_request(30, 20000, 400, seed=51))
+        srv.submit(**long_request(31, 20000, 400, seed=52))
+        out = {}
+        t_end = time.time() + 120
+        while len(out) < 2 and time.time() < t_end:
+            for res in srv.poll(64, wait_ms=100):
+                out[res["id"]] = res
+        assert out[30]["status"] == 5 and out[31]["status"] == 5
+        for res in out.values():
+            assert res["t_done"] - res["t_submit"] < 3.0
+        srv.set_deadline(0.0)
+        res = run_all(srv, [make_request(32, 1500, 1400, 1, 16, 0.03, seed=53)])[32]
+        assert res["status"] == 0 and np.isfinite(res["energy"][0])
+    finally:
+        srv.close()
+    with pytest.raises(gw.GWError):
+        gw.Server(pool_bytes=1 << 20, max_active=1).set_deadline(float("nan"))
