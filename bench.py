@@ -33,8 +33,8 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 METRIC = "Sinkhorn cells/s (N*M*iters/s)"
-PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2, "f16x3": 3}
-DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "f16x3": "f16x3"}
+PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2, "f16x3": 3, "fp8": 4}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "f16x3": "f16x3", "fp8": "fp8e4m3"}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -321,6 +321,14 @@ def run_gw(args, rank, world, local):
             rf["bf16_cells_per_s"] = rfb["cells_per_s"]
             rf["bf16_ex2_frac"] = rfb["frac"]
             rf["bf16_speedup_vs_fp32"] = rfb["cells_per_s"] / rf32["cells_per_s"]
+        if prec != PREC["fp8"] and D <= 128:
+            # the E4M3 form on the same state (a speed reference; its error,
+            # whole log2 units of exponent, is stated separately)
+            rf8 = roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, PREC["fp8"], flush,
+                                   reps=3, ex2_peak=ex2_peak)
+            rf["fp8_cells_per_s"] = rf8["cells_per_s"]
+            rf["fp8_ex2_frac"] = rf8["frac"]
+            rf["fp8_speedup_vs_fp32"] = rf8["cells_per_s"] / rf32["cells_per_s"]
     e2e = None if args.no_e2e else run_e2e(args, gw, torch, dev, X, Y, s, t, a, b, prec, ws, flush)
     full = None if args.no_full or world > 1 else run_full_solve(args, gw, torch, dev, prec, seed)
     extra = None
@@ -549,6 +557,9 @@ def roofline_softmin(args, gw, torch, X, Y, s, t, a, b, state, prec, flush, reps
     # 3 shift + 1 mask operand columns (the zero padding to 16 is not counted)
     mult = 1 if prec == PREC["bf16"] else 3
     used = mult * D + 10
+    if prec == PREC["fp8"]:
+        # E4M3 K-steps of 32 dims issue at the time of 16 BF16 columns
+        used = 16 * ((D + 31) // 32) + 10
     tens = float(peaks.get("bf16_tflops", 1900.0)) * 1e12
     derived = 152 * 32 * clk
     if ex2_peak is None:
@@ -1168,7 +1179,7 @@ def batch_config1(gw, torch, dev, nprob, seed, warmup):
                         "20 outer x 50 symmetric Sinkhorn, FP32, one persistent launch"}
 
 
-def sphere_iteration(args, gw, torch, dev, flush, ex2_peak, precs=("f16x3", "bf16")):
+def sphere_iteration(args, gw, torch, dev, flush, ex2_peak, precs=("f16x3", "bf16", "fp8")):
     """The large-scale workload's iteration: N = M = 250k unit-sphere samples
     vs a smooth warp, ||x - x'|| lifted to D = 64 by Kernel PCA; the state of
     a short annealed solve (2 outer x 30 iterations, eps 0.1 -> 0.05), then

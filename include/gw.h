@@ -61,6 +61,15 @@ typedef struct CUstream_st* gw_stream_t;
 #define GW_PREC_BF16 1     /* BF16 operands on tcgen05, FP32 accumulate */
 #define GW_PREC_BF16X3 2   /* split BF16 (hi*hi + hi*lo + lo*hi) on tcgen05 */
 #define GW_PREC_F16X3 3    /* split FP16 with scaling (hi*hi + hi*lo + lo*hi) on tcgen05 */
+#define GW_PREC_FP8 4      /* E4M3 features on tcgen05 (kind::f8f6f4): each feature matrix
+                            * rounded under one power-of-two scale per 128-row group (the
+                            * same rounding in the row and column softmins and the plan
+                            * sums), the rank-one, bias and shift columns as split BF16 in
+                            * the same FP32 accumulator, 16 log2(e) / eps applied in the
+                            * epilogue.  A measured mode: e4m3's 3 mantissa bits move the
+                            * exponent by whole log2 units already at eps = 0.1 on
+                            * unit-scale features (the error is stated per eps beside the
+                            * other modes); not an accuracy-preserving form. */
 
 /* CNT penalties accepted by gw_lift (Section 2, "Embeddable costs") */
 #define GW_PEN_SQEUCLID 0  /* ||x - x'||^2: the lift is a centering */

@@ -17,7 +17,7 @@ import torch
 from ._build import LIB as _LIB_PATH
 
 __all__ = [
-    "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
+    "GW_OK", "PREC_FP32", "PREC_BF16", "PREC_BF16X3", "PREC_F16X3", "PREC_FP8", "PEN_SQEUCLID", "PEN_POWER", "PEN_GAUSS",
     "EN", "GWError", "lib", "gw_sinkhorn_softmin", "gw_cross_cov", "gw_energy", "gw_solve",
     "gw_lift", "gw_grad_x", "gw_workspace_size", "gw_last_error", "gw_version", "workspace",
     "gw_kernel_launches", "gw_sinkhorn_softmin_noalloc", "Server", "gw_coarsen", "gw_multiscale", "gw_sgw", "gw_kernel_gw", "gw_transfer", "gw_sinkhorn_iteration",
@@ -25,7 +25,7 @@ __all__ = [
 ]
 
 GW_OK = 0
-PREC_FP32, PREC_BF16, PREC_BF16X3, PREC_F16X3 = 0, 1, 2, 3
+PREC_FP32, PREC_BF16, PREC_BF16X3, PREC_F16X3, PREC_FP8 = 0, 1, 2, 3, 4
 PEN_SQEUCLID, PEN_POWER, PEN_GAUSS = 0, 1, 2
 OP_SOFTMIN, OP_CROSS_COV, OP_ENERGY, OP_SOLVE, OP_LIFT, OP_GRAD, OP_COARSEN, OP_ITERATION = range(8)
 EN_LEN = 16

@@ -68,7 +68,7 @@ tc::WaitCtl wait_ctl() { return tc::WaitCtl{g_wait_limit_ns.load(), gave_up_coun
 
 namespace {
 
-bool prec_ok(int prec) { return prec >= GW_PREC_FP32 && prec <= GW_PREC_F16X3; }
+bool prec_ok(int prec) { return prec >= GW_PREC_FP32 && prec <= GW_PREC_FP8; }
 
 int check_eps(float eps) {
   GW_REQUIRE(eps > 0.0f && isfinite(eps), GW_EINVAL, "eps must be finite and > 0 (got %g)",
@@ -87,7 +87,7 @@ int check_dims(int64_t n, int64_t m, int D, int E) {
 }
 
 int check_prec(int prec) {
-  GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_F16X3, GW_EINVAL, "unknown precision %d",
+  GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_FP8, GW_EINVAL, "unknown precision %d",
              prec);
   GW_REQUIRE(prec_ok(prec), GW_EUNSUPPORTED, "precision %d is not supported", prec);
   return GW_OK;

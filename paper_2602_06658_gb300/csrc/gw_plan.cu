@@ -657,7 +657,7 @@ static void launch_colsum(const ColSumArgs& A, dim3 grid, cudaStream_t st) {
 // Enqueue everything up to the Gamma partials; the caller finalizes.
 static int cross_cov_stage(const PlanArgs& p, int prec, double* W_user, Carver& ws,
                            cudaStream_t st, CrossCovLayout* out, bool want_kl = false) {
-  GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_F16X3, GW_EUNSUPPORTED, "precision %d", prec);
+  GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_FP8, GW_EUNSUPPORTED, "precision %d", prec);
   CrossCovLayout L = carve_cross_cov(ws, p.n, p.m, p.D, p.E, W_user == nullptr);
   GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for cross-covariance");
   if (W_user) L.W = W_user;

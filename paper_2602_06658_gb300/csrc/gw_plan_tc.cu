@@ -66,9 +66,13 @@ struct PlanTask {
   float* Wp;         // [splits][rows][D + 2]
   float* Ep;         // [splits][rows][2]: A_j, B_j of the KL term (or null)
   int* flag;
+  int k8;            // FP8: leading K-steps of E4M3 features
+  const float* fsA;  // FP8: power-of-two scale per 128 targets
+  const float* fsB;  // FP8: the same per 128 sources (two source tiles)
+  float alpha8;      // FP8: 16 log2(e) / eps, applied in the epilogue
 };
 
-template <int KP, int S, int NW, bool BF16>
+template <int KP, int S, int NW, bool BF16, bool F8>
 __global__ void __launch_bounds__(kPlanThreads, 1)
     plan_tc_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                    const __grid_constant__ CUtensorMap mUh, const __grid_constant__ CUtensorMap mUl,
@@ -167,6 +171,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       // ------------------------------------------------------- MMA issuer
       const uint32_t idesc = tc::f16_idesc(128, kPlanBN, BF16);
       const uint32_t idesc2 = tc::f16_idesc(128, NW, false);
+      constexpr uint32_t idesc8 = tc::f16_idesc(128, kPlanBN, false);   // E4M3 x E4M3
+      const int k8 = F8 ? T.k8 : 0;
       const int nks = T.ksteps;
       bool ok = tc::mbar_wait(afull, 0, ab, lim);
       // exponent tile t into TMEM buffer t & 1
@@ -184,8 +190,12 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
             if (ks >= nks) break;   // the rest of the operand row is zero padding
             const uint32_t aaddr = tc::smem_u32(As + (h * KB + ks / 4) * 16384 + (ks % 4) * 32);
             const uint32_t baddr = tc::smem_u32(Bst + (ks / 4) * L::kBBlock + (ks % 4) * 32);
-            tc::mma_f16(tbase + (b * 2 + h) * kPlanBN, tc::sw128_desc(aaddr),
-                        tc::sw128_desc(baddr), idesc, ks > 0 ? 1u : 0u);
+            if (F8 && ks < k8)
+              tc::mma_f8(tbase + (b * 2 + h) * kPlanBN, tc::sw128_desc(aaddr),
+                         tc::sw128_desc(baddr), idesc8, ks > 0 ? 1u : 0u);
+            else
+              tc::mma_f16(tbase + (b * 2 + h) * kPlanBN, tc::sw128_desc(aaddr),
+                          tc::sw128_desc(baddr), idesc, ks > 0 ? 1u : 0u);
           }
         }
         tc::mma_commit(&tfull[b]);
@@ -239,6 +249,8 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     unsigned char* Ph = Ps + (h * 2 + 0) * L::kPBytes;
     unsigned char* Pl = Ps + (h * 2 + 1) * L::kPBytes;
     const uint32_t prow = static_cast<uint32_t>((rloc >> 3) * 1024 + (rloc & 7) * 128);
+    // FP8: alpha / the scale of this half's 128 targets (n_pad covered)
+    const float a_over = F8 ? T.alpha8 / T.fsA[(row0 >> 7) + h] : 1.0f;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
       int got = 0;
@@ -257,6 +269,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
+      if constexpr (F8) unscale(r, a_over / T.fsB[(tile0 + t) >> 1]);
       // q = 2^12 pi_ij / b_j as f16 hi + lo, packed in pairs along the sources:
       // hi keeps the top 11 significant bits (exact in f16 for q >= 2^-14),
       // lo = q - hi is exact in FP32 and rounded once
@@ -413,10 +426,10 @@ int make_u_map(CUtensorMap* map, void* ptr, int64_t n_pad, int NW) {
 
 int plan_nw(int D) { return D + 3 <= 16 ? 16 : D + 3 <= 32 ? 32 : D + 3 <= 48 ? 48 : 64; }
 
-template <int KP, int S, int NW, bool BF16>
+template <int KP, int S, int NW, bool BF16, bool F8>
 int launch_plan(const CUtensorMap* maps, const PlanTask& T, int blocks, cudaStream_t st) {
   using L = PlanSmem<KP, S, NW>;
-  auto kern = plan_tc_kernel<KP, S, NW, BF16>;
+  auto kern = plan_tc_kernel<KP, S, NW, BF16, F8>;
   static std::once_flag once;
   static cudaError_t attr_rc = cudaSuccess;
   std::call_once(once, [&] {
@@ -428,13 +441,13 @@ int launch_plan(const CUtensorMap* maps, const PlanTask& T, int blocks, cudaStre
   return GW_OK;
 }
 
-template <int KP, int S, bool BF16>
+template <int KP, int S, bool BF16, bool F8 = false>
 int launch_plan_nw(int NW, const CUtensorMap* maps, const PlanTask& T, int blocks, cudaStream_t st) {
   switch (NW) {
-    case 16: return launch_plan<KP, S, 16, BF16>(maps, T, blocks, st);
-    case 32: return launch_plan<KP, S, 32, BF16>(maps, T, blocks, st);
-    case 48: return launch_plan<KP, S, 48, BF16>(maps, T, blocks, st);
-    default: return launch_plan<KP, S, 64, BF16>(maps, T, blocks, st);
+    case 16: return launch_plan<KP, S, 16, BF16, F8>(maps, T, blocks, st);
+    case 32: return launch_plan<KP, S, 32, BF16, F8>(maps, T, blocks, st);
+    case 48: return launch_plan<KP, S, 48, BF16, F8>(maps, T, blocks, st);
+    default: return launch_plan<KP, S, 64, BF16, F8>(maps, T, blocks, st);
   }
 }
 
@@ -482,6 +495,7 @@ struct PlanBufs {
   int* flag;
   float* Wp;
   float* Ep;
+  float *fsA, *fsB;   // FP8 group scales (targets, sources)
 };
 
 PlanBufs carve_plan(Carver& c, int64_t n, int64_t m, int D, int prec) {
@@ -500,13 +514,20 @@ PlanBufs carve_plan(Carver& c, int64_t n, int64_t m, int D, int prec) {
   B.flag = c.take<int>(4);
   B.Wp = c.take<float>(static_cast<size_t>(Lt.splits) * m * (D + 2));
   B.Ep = c.take<float>(static_cast<size_t>(Lt.splits) * m * 2);
+  B.fsA = B.fsB = nullptr;
+  if (shp.k8 > 0) {
+    B.fsA = c.take<float>(static_cast<size_t>(Lt.rows_pad / kFp8Group));
+    B.fsB = c.take<float>(static_cast<size_t>(ceil_div(Lt.cols_pad, kFp8Group)));
+  }
   return B;
 }
 
 }  // namespace
 
 bool plan_tc_supported(int D, int prec) {
-  if (prec != GW_PREC_BF16 && prec != GW_PREC_BF16X3 && prec != GW_PREC_F16X3) return false;
+  if (prec != GW_PREC_BF16 && prec != GW_PREC_BF16X3 && prec != GW_PREC_F16X3 &&
+      prec != GW_PREC_FP8)
+    return false;
   return D + 3 <= 64 && tc_shape(D, prec).KP <= 128;
 }
 
@@ -538,15 +559,24 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, flo
   GW_LAUNCH_CHECK();
   const float alpha = 16.0f * kLog2e * inv_eps;
   const float beta = 4.0f * kLog2e * inv_eps;
+  if (shp.k8 > 0) {
+    // FP8: the same 128-row group scales the softmin gives V and X
+    const int64_t ga = Lt.rows_pad / kFp8Group, gb = ceil_div(Lt.cols_pad, kFp8Group);
+    fp8_scale_kernel<<<ceil_div(ga * 32, 256), 256, 0, st>>>(V, p.m, p.D, ga, B.fsA);
+    GW_LAUNCH_CHECK();
+    fp8_scale_kernel<<<ceil_div(gb * 32, 256), 256, 0, st>>>(p.X, p.n, p.D, gb, B.fsB);
+    GW_LAUNCH_CHECK();
+  }
   dim3 blk(64, 4);
   if (bf16) {
     tc_prep_kernel<__nv_bfloat16><<<ceil_div(Lt.rows_pad, 4), blk, 0, st>>>(
         V, p.t, nullptr, nullptr, p.g, p.m, Lt.rows_pad, shp, 0, alpha, beta, inv_eps, B.mx,
-        reinterpret_cast<__nv_bfloat16*>(B.opA), kPlanShiftBias);
+        reinterpret_cast<__nv_bfloat16*>(B.opA), kPlanShiftBias, nullptr, TcOperandShape{}, 0,
+        B.fsA);
     GW_LAUNCH_CHECK();
     tc_prep_kernel<__nv_bfloat16><<<ceil_div(Lt.cols_pad, 4), blk, 0, st>>>(
         p.X, p.s, p.f, B.loga, nullptr, p.n, Lt.cols_pad, shp, 1, alpha, beta, inv_eps, B.mx,
-        reinterpret_cast<__nv_bfloat16*>(B.opB));
+        reinterpret_cast<__nv_bfloat16*>(B.opB), kShiftBias, nullptr, TcOperandShape{}, 0, B.fsB);
     GW_LAUNCH_CHECK();
   } else {
     tc_prep_kernel<__half><<<ceil_div(Lt.rows_pad, 4), blk, 0, st>>>(
@@ -583,9 +613,16 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, flo
   T.Ep = Ep_out ? B.Ep : nullptr;
   T.flag = B.flag;
   T.wc = wait_ctl();
+  T.k8 = shp.k8;
+  T.fsA = B.fsA;
+  T.fsB = B.fsB;
+  T.alpha8 = alpha;
   const int blocks = Lt.row_tiles * Lt.splits;
   int rc;
-  if (shp.KP == 64) {
+  if (shp.k8 > 0) {
+    rc = shp.KP == 64 ? launch_plan_nw<64, 4, true, true>(NW, maps, T, blocks, st)
+                      : launch_plan_nw<128, 3, true, true>(NW, maps, T, blocks, st);
+  } else if (shp.KP == 64) {
     rc = bf16 ? launch_plan_nw<64, 4, true>(NW, maps, T, blocks, st)
               : launch_plan_nw<64, 4, false>(NW, maps, T, blocks, st);
   } else {

@@ -77,6 +77,10 @@ struct TcTask {
   float* out;
   float* pm;
   float* ps;
+  int k8;                 // FP8: leading K-steps of E4M3 features (kind::f8f6f4)
+  const float* fsA;       // FP8: power-of-two scale of each 128-row group of A
+  const float* fsB;       // FP8: the same per 128-row group of B (one per tile)
+  float alpha8;           // FP8: 16 log2(e) / eps, applied in the epilogue
 };
 
 template <int KP, int S, int BN>
@@ -168,7 +172,7 @@ __device__ __forceinline__ void chunk(const uint32_t (&r)[32], float& shift, flo
   }
 }
 
-template <int KP, int S, int BN, bool BF16, bool FAST>
+template <int KP, int S, int BN, bool BF16, bool FAST, bool F8>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     softmin_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mB0,
                       const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mB1,
@@ -267,6 +271,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     if (lane == 0) {
       // ------------------------------------------------------- MMA issuer
       const uint32_t idesc = tc::f16_idesc(128, BN, BF16);
+      constexpr uint32_t idesc8 = tc::f16_idesc(128, BN, false);   // E4M3 x E4M3
+      const int k8 = F8 ? T.k8 : 0;
       bool ok = tc::mbar_wait(afull, 0, ab, lim);
       for (int t = 0; ok && t < ntiles; ++t) {
         const int s = t % S, b = t & 1;
@@ -282,8 +288,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             if (ks >= nks) break;   // the rest of the operand row is zero padding
             const uint32_t aaddr = tc::smem_u32(As + (h * KB + ks / 4) * 16384 + (ks % 4) * 32);
             const uint32_t baddr = tc::smem_u32(Bst + (ks / 4) * L::kBBlock + (ks % 4) * 32);
-            tc::mma_f16(tbase + (b * 2 + h) * BN, tc::sw128_desc(aaddr), tc::sw128_desc(baddr),
-                        idesc, ks > 0 ? 1u : 0u);
+            if (F8 && ks < k8)
+              tc::mma_f8(tbase + (b * 2 + h) * BN, tc::sw128_desc(aaddr), tc::sw128_desc(baddr),
+                         idesc8, ks > 0 ? 1u : 0u);
+            else
+              tc::mma_f16(tbase + (b * 2 + h) * BN, tc::sw128_desc(aaddr), tc::sw128_desc(baddr),
+                          idesc, ks > 0 ? 1u : 0u);
           }
         }
         tc::mma_commit(&empty[s]);
@@ -307,6 +317,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     // fast pass: the MMA already subtracted the shift e_i, the sum starts at 0
     float mrun = FAST ? 0.0f : kRunInit, srun = 0.0f;
     bool ok = true;
+    // FP8: alpha / fsA of this half's row group (the scales cover n_pad rows)
+    static_assert(!F8 || BN == kFp8Group, "FP8 column tiles are the scale groups");
+    const float a_over = F8 ? T.alpha8 / T.fsA[(row0 >> 7) + h] : 1.0f;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
       // one lane waits, the warp follows: tcgen05.ld needs a converged warp
@@ -326,11 +339,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         uint32_t r64[64];
         tc::tmem_ld64_issue(tcol, r64);
         tc::tmem_ld_wait(r64);
+        if constexpr (F8) unscale(r64, a_over / T.fsB[tile0 + t]);
         chunk<FAST>(*reinterpret_cast<const uint32_t(*)[32]>(&r64[0]), mrun, srun);
         chunk<FAST>(*reinterpret_cast<const uint32_t(*)[32]>(&r64[32]), mrun, srun);
       } else {
         tc::tmem_ld32_issue(tcol, ra);
         tc::tmem_ld_wait(ra);
+        if constexpr (F8) unscale(ra, a_over / T.fsB[tile0 + t]);
         chunk<FAST>(ra, mrun, srun);
       }
       tc::tc_fence_before();
@@ -507,11 +522,11 @@ int tc_splits(int row_tiles, int col_tiles, int other_blocks) {
   return best;
 }
 
-template <int KP, int S, bool BF16, bool FAST>
+template <int KP, int S, bool BF16, bool FAST, bool F8 = false>
 int launch_tc_kernel(const CUtensorMap* maps, const TcTask& a, const TcTask& b, cudaStream_t st) {
   constexpr int BN = tile_cols(KP);
   using L = TcSmem<KP, S, BN>;
-  auto kern = softmin_tc_kernel<KP, S, BN, BF16, FAST>;
+  auto kern = softmin_tc_kernel<KP, S, BN, BF16, FAST, F8>;
   static std::once_flag once;   // the attribute is the same for every call
   static cudaError_t attr_rc = cudaSuccess;
   std::call_once(once, [&] {
@@ -536,8 +551,23 @@ int dispatch_tc(int KP, const CUtensorMap* maps, const TcTask& a, const TcTask& 
   return GW_EUNSUPPORTED;
 }
 
+// FP8 operands (E4M3 features, BF16 bias columns): KP 64 or 128 only
+template <bool FAST>
+int dispatch_tc_f8(int KP, const CUtensorMap* maps, const TcTask& a, const TcTask& b,
+                   cudaStream_t st) {
+  switch (KP) {
+    case 64: return launch_tc_kernel<64, 4, true, FAST, true>(maps, a, b, st);
+    case 128: return launch_tc_kernel<128, 3, true, FAST, true>(maps, a, b, st);
+    default: break;
+  }
+  set_error("tensor-core softmin (FP8): operand width %d (K too large)", KP);
+  return GW_EUNSUPPORTED;
+}
+
 int run_tc(bool bf16, bool fast, int KP, const CUtensorMap* maps, const TcTask& a, const TcTask& b,
            cudaStream_t st) {
+  if (a.k8 > 0) return fast ? dispatch_tc_f8<true>(KP, maps, a, b, st)
+                            : dispatch_tc_f8<false>(KP, maps, a, b, st);
   if (bf16) return fast ? dispatch_tc<true, true>(KP, maps, a, b, st)
                         : dispatch_tc<true, false>(KP, maps, a, b, st);
   return fast ? dispatch_tc<false, true>(KP, maps, a, b, st)
@@ -547,6 +577,7 @@ int run_tc(bool bf16, bool fast, int KP, const CUtensorMap* maps, const TcTask& 
 }  // namespace
 
 bool softmin_tc_supported(int K, int prec) {
+  if (prec == GW_PREC_FP8) return tc_shape(K, prec).KP <= 128;
   if (prec != GW_PREC_BF16 && prec != GW_PREC_BF16X3 && prec != GW_PREC_F16X3) return false;
   return tc_shape(K, prec).KP <= 256;
 }
@@ -582,6 +613,10 @@ size_t softmin_tc_ws_bytes(int64_t n, int64_t m, int K, int prec) {
     c.take<int>(2 + 128);                              // layout decision
   }
   c.take<float>(static_cast<size_t>(2 * 2 * kSmCount));  // per-block maxima of the refresh
+  if (shp.k8 > 0) {
+    c.take<float>(static_cast<size_t>(n_pad / kFp8Group));   // FP8 group scales of A
+    c.take<float>(static_cast<size_t>(m_pad / kFp8Group));   // and of B
+  }
   return c.used();
 }
 
@@ -653,6 +688,12 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
       mxd = ws.take<unsigned>(256);
       lay = ws.take<int>(2 + 128);
     }
+    float* fsA = nullptr;
+    float* fsB = nullptr;
+    if (shp.k8 > 0) {
+      fsA = ws.take<float>(static_cast<size_t>(n_pad / kFp8Group));
+      fsB = ws.take<float>(static_cast<size_t>(m_pad / kFp8Group));
+    }
     GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
     const int tps_a = narrow ? tps * bn_f / bn_a : tps;
     GW_REQUIRE(!narrow || ceil_div(col_tiles_a, tps_a) == s, GW_ECUDA,
@@ -662,7 +703,8 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
       // main, rank-one and mask columns are unchanged: the bias and shift
       // columns of every task are refreshed after this loop, in two launches
       refresh[q] = RefreshTask{T.h, T.logw, use_est ? T.est : nullptr, T.n, T.m, inv_eps, flags,
-                               row_tiles[q], opA, opB};
+                               row_tiles[q], opA, opB, fsA, fsB,
+                               shp.k8 > 0 ? 16.0f * kLog2e * inv_eps : 1.0f};
     } else {
       GW_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * row_tiles[q], st));
       GW_CUDA_TRY(cudaMemsetAsync(mx, 0, 8 * sizeof(unsigned), st));
@@ -685,16 +727,24 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
       const float alpha = 16.0f * kLog2e * inv_eps;
       const float beta = 4.0f * kLog2e * inv_eps;
       const int64_t mrows = m_pad > m_pad_a ? m_pad : m_pad_a;
+      if (shp.k8 > 0) {
+        // FP8: one power-of-two scale per 128-row group of A and of B
+        const int64_t ga = n_pad / kFp8Group, gb = m_pad / kFp8Group;
+        fp8_scale_kernel<<<ceil_div(ga * 32, 256), 256, 0, st>>>(T.A, T.n, T.K, ga, fsA);
+        GW_LAUNCH_CHECK();
+        fp8_scale_kernel<<<ceil_div(gb * 32, 256), 256, 0, st>>>(T.B, T.m, T.K, gb, fsB);
+        GW_LAUNCH_CHECK();
+      }
       dim3 blk(64, 4);
       if (bf16) {
         tc_prep_kernel<__nv_bfloat16><<<ceil_div(n_pad, 4), blk, 0, st>>>(
             T.A, T.sA, nullptr, nullptr, use_est ? T.est : nullptr, T.n, n_pad, shp, 0, alpha,
             beta, inv_eps, mx, reinterpret_cast<__nv_bfloat16*>(opA), kShiftBias, lay, shp_a,
-            n_pad);
+            n_pad, fsA);
         GW_LAUNCH_CHECK();
         tc_prep_kernel<__nv_bfloat16><<<ceil_div(mrows, 4), blk, 0, st>>>(
             T.B, T.sB, T.h, T.logw, nullptr, T.m, m_pad, shp, 1, alpha, beta, inv_eps, mx,
-            reinterpret_cast<__nv_bfloat16*>(opB), kShiftBias, lay, shp_a, m_pad_a);
+            reinterpret_cast<__nv_bfloat16*>(opB), kShiftBias, lay, shp_a, m_pad_a, fsB);
         GW_LAUNCH_CHECK();
       } else {
         tc_prep_kernel<__half><<<ceil_div(n_pad, 4), blk, 0, st>>>(
@@ -729,6 +779,10 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
     K.gate = nullptr;
     K.gate_on = 0;
     K.K = T.K;
+    K.k8 = shp.k8;
+    K.fsA = fsA;
+    K.fsB = fsB;
+    K.alpha8 = 16.0f * kLog2e * inv_eps;
     if (narrow) {
       // the split layout over the same buffers (its rows are kp_a wide)
       GW_TRY(make_map(&maps_a[2 * q], opA, n_pad, kp_a, bf16, 128));

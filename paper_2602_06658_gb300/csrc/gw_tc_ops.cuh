@@ -9,6 +9,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include <mutex>
@@ -34,14 +35,18 @@ struct TcOperandShape {
   int col_e;    // first row-estimate column
   int col_k;    // mask column (-inf for padded and zero-weight target columns)
   int used;     // non-zero columns
+  int k8;       // GW_PREC_FP8: leading MMA K-steps of E4M3 features (32 dims each,
+                // two to a 16-bit column); 0 in the 16-bit modes
 };
 
 TcOperandShape tc_shape(int K, int prec) {
   TcOperandShape s;
   s.K = K;
-  s.mult = prec == GW_PREC_BF16 ? 1 : 3;
+  s.mult = (prec == GW_PREC_BF16 || prec == GW_PREC_FP8) ? 1 : 3;
   s.Ks = K;
-  s.col_u = s.mult * K;
+  s.k8 = prec == GW_PREC_FP8 ? (K + 31) / 32 : 0;
+  // FP8: the dims as bytes, 32 per K-step of 16 columns
+  s.col_u = s.k8 > 0 ? 16 * s.k8 : s.mult * K;
   s.col_w = s.col_u + 3;
   s.col_e = s.col_w + 3;
   s.col_k = s.col_e + 3;
@@ -165,6 +170,60 @@ __device__ __forceinline__ void balance(float prod, float mxa, float mxb, float*
   *sb = prod / r;
 }
 
+// Largest e4m3 magnitude, and the power-of-two scale 2^e that brings a
+// group's max |x| to at most 448 (the largest such e; e in [-40, 40] so the
+// bias columns times the scale stay far inside BF16 range; 1 for an all-zero
+// or non-finite group).  m = f 2^E with f in [0.5, 1): f 2^9 <= 448 iff
+// f <= 0.875.
+constexpr float kE4M3Max = 448.0f;
+__device__ __forceinline__ float e4m3_group_scale(float m) {
+  if (!(m > 0.0f) || !isfinite(m)) return 1.0f;
+  int E = 0;
+  const float f = frexpf(m, &E);
+  int e = (f <= 0.875f ? 9 : 8) - E;
+  e = e < -40 ? -40 : (e > 40 ? 40 : e);
+  return ldexpf(1.0f, e);
+}
+
+// FP8 (GW_PREC_FP8) operand scales: one power of two per group of
+// kFp8Group rows of a feature matrix, fs[g] = e4m3_group_scale(max |X_ik|
+// over the group's rows); groups past the last row up to ngroups get 1.  The
+// e4m3 features e4m3(X_ik fs[i / kFp8Group]) depend on the matrix alone, not
+// on the side of the product it takes, so the row and column softmins and
+// the plan sums all multiply the same rounded features.  One warp per group.
+constexpr int kFp8Group = 128;
+__global__ void fp8_scale_kernel(const float* X, int64_t rows, int K, int64_t ngroups, float* fs) {
+  const int64_t g = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= ngroups) return;
+  const int64_t r0 = g * kFp8Group;
+  const int64_t r1 = r0 + kFp8Group < rows ? r0 + kFp8Group : rows;
+  float v = 0.0f;
+  for (int64_t q = r0 * K + lane; q < r1 * K; q += 32) v = fmaxf(v, fabsf(X[q]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) fs[g] = r0 < rows ? e4m3_group_scale(v) : 1.0f;
+}
+
+// FP8: the accumulator holds z / kappa with kappa = alpha / (fs_row fs_col)
+// (the features unscaled by alpha, the other columns divided by it); this
+// multiplies the tile back into base-2 exponent units.
+template <int N>
+__device__ __forceinline__ void unscale(uint32_t (&r)[N], float kap) {
+  const uint64_t k2 = tc::pack2(kap, kap);
+#pragma unroll
+  for (int k = 0; k < N; k += 2) {
+    float a, b;
+    tc::unpack2(tc::mul2(tc::pack2(__uint_as_float(r[k]), __uint_as_float(r[k + 1])), k2), a, b);
+    r[k] = __float_as_uint(a);
+    r[k + 1] = __float_as_uint(b);
+  }
+}
+
+__device__ __forceinline__ uint32_t e4m3_bits(float x) {
+  return static_cast<uint32_t>(__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3));
+}
+
 // Operand rows.  role 0 = A side (row operand), role 1 = B side (column
 // operand, bias columns included).  Rows >= rows_valid are padding: zeros,
 // and for the B side a bias of -65504 * kBiasConst so they add nothing.
@@ -177,7 +236,8 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
                                TcOperandShape shp_f, int role, float alpha, float beta,
                                float inv_eps, const unsigned* mx, T* op,
                                float shift_bias = kShiftBias, const int* lay = nullptr,
-                               TcOperandShape shp_a = TcOperandShape{}, int64_t rows_pad_a = 0) {
+                               TcOperandShape shp_a = TcOperandShape{}, int64_t rows_pad_a = 0,
+                               const float* fs = nullptr) {
   const bool ad = lay != nullptr && lay[0] != 0;
   const TcOperandShape shp = ad ? shape_ks(shp_a, lay[1]) : shp_f;
   const int64_t rows_pad = ad ? rows_pad_a : rows_pad_f;
@@ -186,18 +246,37 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
   if (r >= rows_pad) return;
   const float mA = __uint_as_float(mx[0]), mB = __uint_as_float(mx[1]);
   const float msA = __uint_as_float(mx[2]), msB = __uint_as_float(mx[3]);
-  const float cw = pow2_scale(__uint_as_float(mx[4]));
-  const float ce = pow2_scale(__uint_as_float(mx[5]));
+  // FP8 (fs given): the features are not scaled by alpha; the rank-one, bias
+  // and shift columns are in units of alpha (beta / alpha = 1/4 exactly), and
+  // the epilogue multiplies by alpha / (fs_row fs_col).  wa = 1 otherwise.
+  const bool f8 = fs != nullptr;
+  const float wa = f8 ? alpha : 1.0f;
+  const float cw = pow2_scale(__uint_as_float(mx[4]) / wa);
+  const float ce = pow2_scale(__uint_as_float(mx[5]) / wa);
   float sa, sb, ua, ub;
   balance(alpha, mA, mB, &sa, &sb);
-  balance(beta, msA, msB, &ua, &ub);
+  balance(f8 ? 0.25f : beta, msA, msB, &ua, &ub);
   const float sc = role == 0 ? sa : sb;
   const float us = role == 0 ? ua : ub;
   T* row = op + r * shp.KP;
   const bool valid = r < rows_valid;
   const int K = shp.K;
+  // FP8: the row group's power-of-two scale multiplies every column
+  const float fr = f8 ? fs[r / kFp8Group] : 1.0f;
   for (int k = threadIdx.x; k < shp.KP; k += blockDim.x) {
     float v = 0.0f;
+    if (f8 && k < shp.col_u) {
+      // two E4M3 dims per 16-bit column, the lower index in the low byte
+      uint32_t bits = 0;
+      if (valid) {
+        const int d0 = 2 * k, d1 = 2 * k + 1;
+        const float x0 = d0 < K ? X[r * K + d0] * fr : 0.0f;
+        const float x1 = d1 < K ? X[r * K + d1] * fr : 0.0f;
+        bits = e4m3_bits(x0) | (e4m3_bits(x1) << 8);
+      }
+      reinterpret_cast<uint16_t*>(row)[k] = static_cast<uint16_t>(bits);
+      continue;
+    }
     if (valid) {
       if (k < shp.col_u) {
         // three-product dims: slots [0, Ks) as parts 0, 1, 2; one-product
@@ -228,14 +307,14 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
           v = cw;
         } else {
           const float w = (h[r] * inv_eps + logw[r]) * kLog2e;
-          v = isfinite(w) ? split3<T>(w / cw, k - shp.col_w) : 0.0f;
+          v = isfinite(w) ? split3<T>(w / wa / cw, k - shp.col_w) : 0.0f;
         }
       } else if (k < shp.col_k) {
         // row shift e_i = -est_i log2(e) / eps - kShiftBias as -c_e * split(-e_i / c_e)
         if (role == 1) {
           v = ce;
         } else if (est) {
-          v = split3<T>((est[r] * inv_eps * kLog2e + shift_bias) / ce, k - shp.col_e);
+          v = split3<T>((est[r] * inv_eps * kLog2e + shift_bias) / wa / ce, k - shp.col_e);
         }
       } else if (k == shp.col_k) {
         // mask: zero-weight target columns never contribute
@@ -245,7 +324,7 @@ __global__ void tc_prep_kernel(const float* X, const float* sq, const float* h, 
     } else if (role == 1 && k == shp.col_k) {
       v = -kHalfMax;   // padding columns never contribute
     }
-    row[k] = to16<T>(v);
+    row[k] = to16<T>(v * fr);
   }
 }
 
@@ -265,6 +344,9 @@ struct RefreshTask {
   int nflags;
   void* opA;
   void* opB;
+  const float* fsA;     // FP8: per-group scales of the A side, or null
+  const float* fsB;     // FP8: per-group scales of the B side
+  float wa;             // FP8: alpha (the bias and shift columns in its units); else 1
 };
 
 __global__ void tc_refresh_max_kernel(RefreshTask t0, RefreshTask t1, int ntasks, float* part) {
@@ -326,8 +408,9 @@ __global__ void tc_refresh_multi_kernel(RefreshTask t0, RefreshTask t1, int ntas
         b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
       }
       if (threadIdx.x == 0) {
-        cw[q] = pow2_scale(a);
-        ce[q] = pow2_scale(b);
+        const float wa = (q == 0 ? t0 : t1).wa;
+        cw[q] = pow2_scale(a / wa);
+        ce[q] = pow2_scale(b / wa);
       }
     }
   }
@@ -338,10 +421,11 @@ __global__ void tc_refresh_multi_kernel(RefreshTask t0, RefreshTask t1, int ntas
     const RefreshTask& K = q == 0 ? t0 : t1;
     if (r < K.n) {
       T* row = static_cast<T*>(K.opA) + r * shp.KP;
-      const float e = K.est ? (K.est[r] * K.inv_eps * kLog2e + kShiftBias) / ce[q] : 0.0f;
+      const float e = K.est ? (K.est[r] * K.inv_eps * kLog2e + kShiftBias) / K.wa / ce[q] : 0.0f;
+      const float fr = K.fsA ? K.fsA[r / kFp8Group] : 1.0f;
       for (int k = 0; k < 3; ++k) {
-        row[shp.col_w + k] = to16<T>(cw[q]);
-        row[shp.col_e + k] = to16<T>(K.est ? split3<T>(e, k) : 0.0f);
+        row[shp.col_w + k] = to16<T>(cw[q] * fr);
+        row[shp.col_e + k] = to16<T>((K.est ? split3<T>(e, k) : 0.0f) * fr);
       }
       return;
     }
@@ -350,9 +434,10 @@ __global__ void tc_refresh_multi_kernel(RefreshTask t0, RefreshTask t1, int ntas
       T* row = static_cast<T*>(K.opB) + r * shp.KP;
       const float w = (K.h[r] * K.inv_eps + K.logw[r]) * kLog2e;
       const bool fin = isfinite(w);
+      const float fr = K.fsB ? K.fsB[r / kFp8Group] : 1.0f;
       for (int k = 0; k < 3; ++k) {
-        row[shp.col_w + k] = to16<T>(fin ? split3<T>(w / cw[q], k) : 0.0f);
-        row[shp.col_e + k] = to16<T>(ce[q]);
+        row[shp.col_w + k] = to16<T>((fin ? split3<T>(w / K.wa / cw[q], k) : 0.0f) * fr);
+        row[shp.col_e + k] = to16<T>(ce[q] * fr);
       }
       return;
     }

@@ -154,3 +154,71 @@ def grad_tolerance(pi, X, Y, a, eps):
     scale = 16 * np.abs(X).max() * np.abs(Y).max() + 8 * (X * X).sum(1).max() * (Y * Y).sum(1).max()
     rel = (X.shape[1] + 4) * 2.0 ** -24 * scale / eps + np.sqrt(max(X.shape[0], Y.shape[0])) * 2.0 ** -22
     return 8.0 * rel
+
+
+# --------------------------------------------------------------- FP8 mode
+E4M3_MAX = 448.0
+LOG2E_F32 = np.float32(1.4426950408889634)
+
+
+def round_e4m3(x):
+    """Round to the nearest e4m3 value (bias 7: normals down to 2^-6 with 3
+    mantissa bits, subnormals in steps of 2^-9, largest finite 448); ties to
+    even.  |x| <= 448 is assumed (the scales guarantee it)."""
+    x = np.asarray(x, np.float64)
+    ax = np.abs(x)
+    e = np.maximum(np.floor(np.log2(np.maximum(ax, 2.0 ** -9))), -6.0)
+    step = 2.0 ** (e - 3.0)
+    return np.sign(x) * np.minimum(np.round(ax / step) * step, E4M3_MAX)
+
+
+def e4m3_group_scale(m):
+    """The power of two 2^e, e in [-40, 40], largest with m 2^e <= 448 (the
+    scale GW_PREC_FP8 gives a group of operand values of largest magnitude
+    m); 1 for m = 0 or a non-finite m."""
+    m = float(m)
+    if not (m > 0.0) or not math.isfinite(m):
+        return 1.0
+    fr, E = math.frexp(m)                       # m = fr 2^E, fr in [0.5, 1)
+    e = (9 if fr <= 0.875 else 8) - E           # fr 2^9 <= 448 iff fr <= 0.875
+    return 2.0 ** min(max(e, -40), 40)
+
+
+def fp8_operands(A, B, eps=None, group=128, scales=False):
+    """The feature operands GW_PREC_FP8 multiplies, from the mode's
+    definition (gw.h): each matrix (as FP32) gets one power-of-two scale per
+    group of `group` rows (e4m3_group_scale of the group's largest |value|)
+    and is rounded to e4m3; the same rounding whichever side of the product
+    the matrix takes.  Returns (Ahat, Bhat), the rounded values in the units
+    of A and B: the mode's exponent is 16 <Ahat_i, Bhat_j> / eps (up to FP32
+    rounding of the coefficient).  scales=True also returns the per-row
+    factors that take Ahat and Bhat to the e4m3 values.  (eps is accepted for
+    symmetry with the callers; the rounding does not depend on it.)"""
+    out, facs = [], []
+    for M in (A, B):
+        M32 = np.asarray(M, np.float32)
+        grp = np.arange(len(M32)) // group
+        fg = np.array([e4m3_group_scale(np.abs(M32[grp == q]).max()) for q in range(grp.max() + 1)])
+        fr = fg[grp]
+        out.append(round_e4m3(M32.astype(np.float64) * fr[:, None]) / fr[:, None])
+        facs.append(fr)
+    if scales:
+        return out[0], out[1], facs[0], facs[1]
+    return out[0], out[1]
+
+
+def softmin_tolerance_fp8_emulated(Ahat, Bhat, sA, sB, h, logw, eps):
+    """Bound for GW_PREC_FP8 against the oracle on the rounded operands
+    (fp8_operands): the e4m3 products are exact, what remains is the FP32
+    accumulation, the split-BF16 bias and rank-one columns (relative 2^-15
+    per term, as the split BF16 mode's), the FP32 coefficient alpha and its
+    quotient by the scales (a few 2^-24 of each term)."""
+    Ahat = np.asarray(Ahat, np.float64)
+    Bhat = np.asarray(Bhat, np.float64)
+    K = Ahat.shape[1]
+    m = Bhat.shape[0]
+    lw = np.where(np.isfinite(logw), np.abs(logw), 0.0)
+    S = (16.0 * np.abs(Ahat) @ np.abs(Bhat).T + 4.0 * np.abs(np.outer(sA, sB))
+         + np.abs(h)[None, :] + eps * lw[None, :]).max(axis=1)
+    return 2.0 * ((K + 2) * 2.0 ** -15 * S
+                  + eps * (2.0 ** -8 + 2.0 ** -21 + math.sqrt(m) * 2.0 ** -22))
