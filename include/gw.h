@@ -226,7 +226,13 @@ typedef struct gw_options {
   int symmetric;      /* 1: Algorithm 3 (Jacobi averaging); 0: Algorithm 2 */
   int prec;           /* GW_PREC_* for the cost tiles */
   int record;         /* 1: energy record after every outer step into history */
-  int use_graph;      /* 1: capture the whole solve as one CUDA graph */
+  int use_graph;      /* 1: capture the whole solve as one CUDA graph; 2: per outer step,
+                       * run the first Sinkhorn iteration directly and replay the others
+                       * from a graph of up to 10 iterations captured for that step (the
+                       * host enqueues O(n_outer) work instead of O(n_outer n_inner));
+                       * 0: direct launches.  All three enqueue the same kernels with the
+                       * same arguments: results are bitwise equal.  Graphs need a
+                       * non-null stream (else direct launches). */
   const double* Gamma0; /* D x E initial map, NULL = 0 (the start of Algorithm 1) */
   const float* f0;    /* initial potentials (warm start), NULL = 0 */
   const float* g0;

@@ -37,6 +37,17 @@ _STATUS = {1: "GW_EINVAL", 2: "GW_ENOMEM", 3: "GW_ECUDA", 4: "GW_ENONFINITE", 5:
            6: "GW_EUNSUPPORTED", 7: "GW_ECANCELED"}
 
 
+def _graph_mode(use_graph) -> int:
+    """gw_options.use_graph: False / 0 direct launches, True / 1 the whole
+    solve as one CUDA graph, 2 per-outer-step replay of captured iterations."""
+    if isinstance(use_graph, bool):
+        return int(use_graph)
+    v = int(use_graph)
+    if v not in (0, 1, 2):
+        raise ValueError("use_graph must be 0, 1 or 2")
+    return v
+
+
 class GWError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{_STATUS.get(code, code)}: {msg}")
@@ -349,7 +360,7 @@ def gw_solve(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=T
     P = GwProblem(_ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
                   _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
     O = GwOptions(float(eps), float(eps_final), int(n_outer), int(n_inner), int(bool(symmetric)),
-                  int(prec), int(bool(record)), int(bool(use_graph)),
+                  int(prec), int(bool(record)), _graph_mode(use_graph),
                   _ptr(_f64(Gamma0, "Gamma0")), _ptr(_f32(f0, "f0")), _ptr(_f32(g0, "g0")),
                   int(bool(adaptive)), int(n_inner_max), float(adapt_rtol), float(stop_tol),
                   int(stop_every), int(outer_offset), int(outer_total))
@@ -411,9 +422,9 @@ def gw_multiscale(X, Y, s, t, a, b, eps, init_x, init_y, km_iter, coarse_outer, 
     P = GwProblem(_ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
                   _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
     Oc = GwOptions(float(eps), 0.0, int(coarse_outer), int(coarse_inner), int(bool(symmetric)),
-                   int(prec), 0, int(bool(use_graph)), _ptr(_f64(Gamma0, "Gamma0")), None, None)
+                   int(prec), 0, _graph_mode(use_graph), _ptr(_f64(Gamma0, "Gamma0")), None, None)
     Of = GwOptions(float(eps), float(eps_final), int(fine_outer), int(fine_inner),
-                   int(bool(symmetric)), int(prec), int(bool(record)), int(bool(use_graph)),
+                   int(bool(symmetric)), int(prec), int(bool(record)), _graph_mode(use_graph),
                    None, None, None)
     R = GwResult(_ptr(out["Gamma"]), _ptr(out["Gamma_plan"]), _ptr(out["f"]), _ptr(out["g"]),
                  _ptr(out["energy"]), _ptr(out["history"]))
@@ -507,7 +518,7 @@ def gw_sgw(X, Y, s, t, a, b, eps, n_outer, n_inner, eps_final=0.0, symmetric=Tru
     P = GwProblem(_ptr(_f32(X, "X")), _ptr(_f32(Y, "Y")), _ptr(_f32(s, "s")), _ptr(_f32(t, "t")),
                   _ptr(_f32(a, "a")), _ptr(_f32(b, "b")), n, m, D, E)
     O = GwOptions(float(eps), float(eps_final), int(n_outer), int(n_inner), int(bool(symmetric)),
-                  int(prec), 0, int(bool(use_graph)), None, None, None,
+                  int(prec), 0, _graph_mode(use_graph), None, None, None,
                   int(bool(solve_kw.get("adaptive", False))), int(solve_kw.get("n_inner_max", 0)),
                   float(solve_kw.get("adapt_rtol", 0.0)), float(solve_kw.get("stop_tol", 0.0)),
                   int(solve_kw.get("stop_every", 1)))

@@ -196,7 +196,7 @@ int read_back(const double* d, double* h, cudaStream_t st) {
 }
 
 int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, void* ws,
-                  size_t ws_bytes, cudaStream_t st) {
+                  size_t ws_bytes, cudaStream_t st, bool replay = false) {
   Carver c(ws, ws_bytes);
   SolveBufs B;
   B.loga = c.take<float>(p.n);
@@ -269,12 +269,48 @@ int enqueue_solve(const gw_problem& p, const gw_options& o, const gw_result& r, 
     GW_TRY(launch_gamma_y(B.G[Gc], p.Y, p.m, p.D, p.E, B.V, st));
     int n_run = n_cur;
     bool checked = false;
-    for (int it = 0; it < n_cur; ++it) {
+    auto iterate = [&](bool reuse) -> int {
       GW_TRY(launch_iteration(p.X, B.V, p.s, p.t, B.loga, B.logb, B.f[fc], B.g[gc], B.f[fc ^ 1],
-                              B.g[gc ^ 1], eps, p.n, p.m, p.D, o.prec, o.symmetric != 0, it > 0,
+                              B.g[gc ^ 1], eps, p.n, p.m, p.D, o.prec, o.symmetric != 0, reuse,
                               base + mark, ws_bytes - mark, st));
       fc ^= 1;
       gc ^= 1;
+      return GW_OK;
+    };
+    int it0 = 0;
+    if (replay && !stop_rule && n_cur >= 3) {
+      // the first iteration prepares the outer step's operands; the others
+      // differ only in which potential buffers they read and write, so an
+      // even number of them (f, g back in the buffers they started in) is
+      // captured once and replayed
+      GW_TRY(iterate(false));
+      const int left = n_cur - 1;
+      const int body = left >= 20 ? 10 : 2;
+      cudaGraph_t graph = nullptr;
+      GW_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      int rc = GW_OK;
+      for (int k = 0; k < body && rc == GW_OK; ++k) rc = iterate(true);
+      const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+      if (rc != GW_OK || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != GW_OK) return rc;
+        set_error("iteration graph capture failed: %s", cudaGetErrorString(ec));
+        return GW_ECUDA;
+      }
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      GW_REQUIRE(ei == cudaSuccess, GW_ECUDA, "iteration graph instantiate failed: %s",
+                 cudaGetErrorString(ei));
+      cudaError_t el = cudaSuccess;
+      for (int k = 0; k < left / body && el == cudaSuccess; ++k) el = cudaGraphLaunch(exec, st);
+      cudaGraphExecDestroy(exec);
+      GW_REQUIRE(el == cudaSuccess, GW_ECUDA, "iteration graph launch failed: %s",
+                 cudaGetErrorString(el));
+      it0 = 1 + (left / body) * body;
+    }
+    for (int it = it0; it < n_cur; ++it) {
+      GW_TRY(iterate(it > 0));
       if (stop_rule && (it + 1) % o.stop_every == 0) {
         // hybrid stop: Err of the plan this iteration measured
         GW_TRY(run_marginal_error(B.f[fc ^ 1], B.f[fc], p.a, p.n, B.g[gc ^ 1], B.g[gc], p.b, p.m,
@@ -521,6 +557,7 @@ int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, s
   NvtxRange range("gw_solve");
   const bool host_driven = o->adaptive || o->stop_tol > 0.0f;
   if (!o->use_graph || st == nullptr || host_driven) return enqueue_solve(*p, *o, *r, ws, ws_bytes, st);
+  if (o->use_graph == 2) return enqueue_solve(*p, *o, *r, ws, ws_bytes, st, true);
 
   cudaGraph_t graph = nullptr;
   GW_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));

@@ -252,7 +252,6 @@ bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
       }
     }
     gw_problem P{X, Y, s, t, a, b, r.n, r.m, D, D};
-    const bool small = small_request(r);
     while (J->outer_done < r.n_outer) {
       gw_options O{};
       O.eps = r.eps;
@@ -265,9 +264,9 @@ bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
       O.symmetric = 1;
       O.prec = run_prec(r);
       O.record = 0;
-      // A request's graph runs once: below the threshold its capture and
-      // instantiation cost more host time than launching the kernels directly.
-      O.use_graph = small ? 0 : 1;
+      // per outer step, the Sinkhorn iterations replay from one captured
+      // graph: the host enqueues O(n_outer) work per request
+      O.use_graph = 2;
       // every slice after the first starts from the state the previous left
       if (J->outer_done > 0) {
         O.Gamma0 = G;

@@ -150,3 +150,33 @@ def test_solve_wide_features_tensor_core(gw, D, prec):
     hist = host(out["history"])
     for k, h in enumerate(res["history"]):
         assert abs(hist[k, gw.EN["E"]] - h["E"]) <= 1e-4 * abs(h["E"]), (k, hist[k, 0], h["E"])
+
+
+@pytest.mark.parametrize("prec", [0, 3])
+def test_graph_modes_are_bitwise_equal(gw, prec):
+    """use_graph 0 (direct launches), 1 (the whole solve as one graph) and 2
+    (per outer step: the first iteration direct, the others replayed from a
+    captured graph of 10 or 2 iterations, the remainder direct) enqueue the
+    same kernels with the same arguments: records, Gamma and potentials are
+    bitwise equal, for inner counts that take each branch."""
+    import torch
+    w = W.gmm_rigid(1200, seed=4, m=1100)
+    dev = lambda v: torch.tensor(np.ascontiguousarray(v, np.float32), device="cuda")
+    a = torch.full((1200,), 1 / 1200, device="cuda")
+    b = torch.full((1100,), 1 / 1100, device="cuda")
+    lx = gw.gw_lift(dev(w["x"]), 16, kind=gw.PEN_POWER, param=1.0, w=a)
+    ly = gw.gw_lift(dev(w["y"]), 16, kind=gw.PEN_POWER, param=1.0, w=b)
+    args = (lx["X"], ly["X"], lx["s"], ly["s"], a, b)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for n_inner in (2, 3, 25):
+        outs = []
+        for mode in (0, 1, 2):
+            with torch.cuda.stream(side):
+                o = gw.gw_solve(*args, 0.1, 3, n_inner, eps_final=0.03, prec=prec, record=True,
+                                use_graph=mode)
+            side.synchronize()
+            outs.append(o)
+        for o in outs[1:]:
+            for k in ("energy", "history", "Gamma", "f", "g"):
+                assert bool((o[k] == outs[0][k]).all()), (prec, n_inner, k)
