@@ -534,6 +534,14 @@ int gw_server_submit(gw_server* s, const gw_request* r, const float* h_x, const 
  * gw_solve's outer_offset, with the same result as an uninterrupted run.
  * Applies to requests admitted after the call. */
 int gw_server_set_slice(gw_server* s, int outer_steps);
+/* Batch lane (on by default): small squared-penalty requests (d <= 4,
+ * n m <= 1.5e6, both clouds in one CTA's shared memory) skip the worker
+ * slots; those waiting when the lane is free (the same d, n_outer, n_inner)
+ * are solved together in one gw_solve_batch launch, one CTA each, on the
+ * lane's own thread and stream, after a per-problem centering on the device.
+ * Results: gw_solve_batch's (FP32 arithmetic), independent of the batch.
+ * on = 0 sends every request through the slots (gw_solve). */
+int gw_server_set_batching(gw_server* s, int on);
 /* Cancel request `id`: a pending request is answered at once, a running one
  * at its next slice boundary (with time slicing; without it, when its solve
  * ends), in both cases with status GW_ECANCELED.  GW_EINVAL if no request

@@ -149,6 +149,8 @@ lib.gw_server_request_bytes.argtypes = [ctypes.POINTER(GwRequest)]
 lib.gw_server_request_bytes.restype = _sz
 lib.gw_server_set_slice.argtypes = [_p, _int]
 lib.gw_server_set_slice.restype = _int
+lib.gw_server_set_batching.argtypes = [_p, _int]
+lib.gw_server_set_batching.restype = _int
 lib.gw_server_cancel.argtypes = [_p, ctypes.c_uint64]
 lib.gw_server_cancel.restype = _int
 lib.gw_server_set_deadline.argtypes = [_p, ctypes.c_double]
@@ -665,6 +667,10 @@ class Server:
     def set_slice(self, outer_steps: int):
         """Time slicing with checkpoint / resume (gw.h: gw_server_set_slice)."""
         _check(lib.gw_server_set_slice(self.h, int(outer_steps)))
+
+    def set_batching(self, on: bool):
+        """Batch lane for small squared requests (gw.h: gw_server_set_batching)."""
+        _check(lib.gw_server_set_batching(self.h, int(bool(on))))
 
     def cancel(self, id):
         """Cancel request `id` (gw.h: gw_server_cancel); answered with GW_ECANCELED."""

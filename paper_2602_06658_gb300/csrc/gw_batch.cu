@@ -517,6 +517,11 @@ __global__ void __launch_bounds__(kBt, 2) batch_solve_kernel(BatchArgs A) {
 
 size_t batch_ws_bytes() { return 256; }
 
+bool batch_fits(int64_t n_max, int64_t m_max, int D) {
+  return D >= 1 && D <= 4 && n_max >= 1 && m_max >= 1 &&
+         batch_smem_bytes(n_max, m_max, D) <= 227 * 1024 - 64;
+}
+
 int run_solve_batch(int nprob, const int64_t* xo, const int64_t* yo, int64_t n_max, int64_t m_max,
                     int D, int E, const float* X, const float* Y, const float* s, const float* t,
                     const float* a, const float* b, const float* eps0, const float* eps1,

@@ -221,6 +221,8 @@ int run_energy(const PlanArgs& p, int prec, const double* C_pre, const float* lo
 
 // Persistent batched solver (gw_batch.cu); arguments as gw_solve_batch.
 size_t batch_ws_bytes();
+// Problems of up to n_max + m_max points at feature width D fit one CTA.
+bool batch_fits(int64_t n_max, int64_t m_max, int D);
 int run_solve_batch(int nprob, const int64_t* xo, const int64_t* yo, int64_t n_max, int64_t m_max,
                     int D, int E, const float* X, const float* Y, const float* s, const float* t,
                     const float* a, const float* b, const float* eps0, const float* eps1,

@@ -136,6 +136,97 @@ __global__ void fill_kernel(float* p, int64_t n, float v) {
   if (i < n) p[i] = v;
 }
 
+// ------------------------------------------------------------ batch lane
+// Small squared-penalty requests (the lift is a centering, D = d <= 4) go to
+// the persistent batched solver: the requests waiting when the lane is free
+// are solved in one gw_solve_batch launch, one CTA per request, on the lane's
+// own stream and thread (no worker slot).  One SM solves such a request in
+// about 0.1 s at 20 x 50 iterations; the lane keeps them off the slots the
+// large requests queue for.  A request's path depends on the request alone,
+// and the batched solver's result does not depend on the batch, so a result
+// is the same alone and in the mix.
+constexpr double kBatchCells = 1.5e6;     // n m at most
+constexpr int kBatchMax = 2 * kSmCount;   // requests per launch
+
+bool batchable(const gw_request& r) {
+  return r.kind == GW_PEN_SQEUCLID && r.d <= 4 &&
+         static_cast<double>(r.n) * static_cast<double>(r.m) <= kBatchCells &&
+         batch_fits(r.n, r.m, r.d);
+}
+
+struct BatchJob {
+  std::vector<Job*> members;
+  int d = 0, n_outer = 0, n_inner = 0;
+  int64_t n_max = 0, m_max = 0;
+  size_t bytes = 0;
+  char* mem = nullptr;
+};
+
+// Device layout of a batch (carved in this order; nullptr base: sizing).
+struct BatchBufs {
+  float *x, *y, *X, *Y, *s, *t, *a, *b, *f, *g, *eps0, *eps1;
+  int64_t *xo, *yo;
+  double *G, *Gp, *en;
+  char* ws;
+};
+
+BatchBufs carve_batch(Carver& c, int64_t SN, int64_t SM, int Q, int d) {
+  BatchBufs B;
+  B.x = c.take<float>(static_cast<size_t>(SN) * d);
+  B.y = c.take<float>(static_cast<size_t>(SM) * d);
+  B.X = c.take<float>(static_cast<size_t>(SN) * d);
+  B.Y = c.take<float>(static_cast<size_t>(SM) * d);
+  B.s = c.take<float>(SN);
+  B.t = c.take<float>(SM);
+  B.a = c.take<float>(SN);
+  B.b = c.take<float>(SM);
+  B.f = c.take<float>(SN);
+  B.g = c.take<float>(SM);
+  B.eps0 = c.take<float>(Q);
+  B.eps1 = c.take<float>(Q);
+  B.xo = c.take<int64_t>(Q + 1);
+  B.yo = c.take<int64_t>(Q + 1);
+  B.G = c.take<double>(static_cast<size_t>(Q) * d * d);
+  B.Gp = c.take<double>(static_cast<size_t>(Q) * d * d);
+  B.en = c.take<double>(static_cast<size_t>(Q) * GW_EN_LEN);
+  B.ws = c.take<char>(batch_ws_bytes());
+  return B;
+}
+
+// Centering of each problem's cloud (the lift of the squared penalty with
+// uniform weights): X_i = x_i - mean, s_i = ||X_i||^2, a_i = 1 / n; one block
+// per problem, the mean summed in FP64 in a fixed order.
+__global__ void batch_center_kernel(const float* x, const int64_t* off, int d, float* X,
+                                    float* sq, float* w) {
+  __shared__ double red[256][4];
+  __shared__ double mean[4];
+  const int q = blockIdx.x;
+  const int64_t i0 = off[q], i1 = off[q + 1];
+  const int64_t n = i1 - i0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+    for (int k = 0; k < d; ++k) acc[k] += static_cast<double>(x[i * d + k]);
+  for (int k = 0; k < 4; ++k) red[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (static_cast<int>(threadIdx.x) < h)
+      for (int k = 0; k < 4; ++k) red[threadIdx.x][k] += red[threadIdx.x + h][k];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) mean[threadIdx.x] = n > 0 ? red[0][threadIdx.x] / static_cast<double>(n) : 0.0;
+  __syncthreads();
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    float s = 0.0f;
+    for (int k = 0; k < d; ++k) {
+      const float v = static_cast<float>(static_cast<double>(x[i * d + k]) - mean[k]);
+      X[i * d + k] = v;
+      s = fmaf(v, v, s);
+    }
+    sq[i] = s;
+    w[i] = 1.0f / static_cast<float>(n);
+  }
+}
+
 }  // namespace
 }  // namespace gw
 
@@ -153,6 +244,11 @@ struct gw_server {
   double deadline = 0.0;                 // seconds after submission (0: none)
   std::vector<gw::Job*> running;         // admitted (ready or on a worker)
   bool stop = false;
+  bool batching = true;                  // small squared requests through gw_solve_batch
+  bool batch_busy = false;               // a batch is formed and not yet answered
+  std::deque<gw::BatchJob*> batch_ready;
+  std::condition_variable cv_batch;
+  std::thread batch_thread;
   std::thread scheduler;
   std::vector<std::thread> workers;
   std::deque<gw::Job*> ready;   // admitted, waiting for a worker
@@ -287,8 +383,13 @@ bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
       if ((rc = stop_code()) != GW_OK) break;
       bool waiting = false;
       {
+        // a request waits for a slot (batchable ones wait for the lane instead)
         std::lock_guard<std::mutex> lk(S->mu);
-        waiting = !S->pending.empty();
+        for (const Job* P : S->pending)
+          if (!(S->batching && batchable(P->req))) {
+            waiting = true;
+            break;
+          }
       }
       if (waiting) {
         // checkpoint: the features and the state to host memory, then requeue
@@ -364,16 +465,185 @@ void worker_loop(gw_server* S) {
   cudaStreamDestroy(st);
 }
 
+// Solve one batch on stream st and post its responses.
+void run_batch(gw_server* S, BatchJob* BJ, cudaStream_t st) {
+  const int Q = static_cast<int>(BJ->members.size());
+  const int d = BJ->d;
+  std::vector<int64_t> xo(Q + 1, 0), yo(Q + 1, 0);
+  for (int q = 0; q < Q; ++q) {
+    xo[q + 1] = xo[q] + BJ->members[q]->req.n;
+    yo[q + 1] = yo[q] + BJ->members[q]->req.m;
+  }
+  const int64_t SN = xo[Q], SM = yo[Q];
+  Carver c(BJ->mem, BJ->bytes);
+  BatchBufs B = carve_batch(c, SN, SM, Q, d);
+  std::vector<float> hx(static_cast<size_t>(SN) * d), hy(static_cast<size_t>(SM) * d);
+  std::vector<float> e0(Q), e1(Q);
+  for (int q = 0; q < Q; ++q) {
+    const Job* J = BJ->members[q];
+    std::copy(J->x.begin(), J->x.end(), hx.begin() + xo[q] * d);
+    std::copy(J->y.begin(), J->y.end(), hy.begin() + yo[q] * d);
+    e0[q] = J->req.eps;
+    e1[q] = J->req.eps_final > 0.0f ? J->req.eps_final : J->req.eps;
+  }
+  std::vector<double> en(static_cast<size_t>(Q) * GW_EN_LEN, 0.0);
+  int rc = GW_OK;
+  do {
+    if (c.overflow) {
+      rc = GW_ENOMEM;
+      break;
+    }
+    auto h2d = [&](void* dst, const void* src, size_t bytes) {
+      return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    if (!h2d(B.x, hx.data(), hx.size() * sizeof(float)) ||
+        !h2d(B.y, hy.data(), hy.size() * sizeof(float)) ||
+        !h2d(B.xo, xo.data(), xo.size() * sizeof(int64_t)) ||
+        !h2d(B.yo, yo.data(), yo.size() * sizeof(int64_t)) ||
+        !h2d(B.eps0, e0.data(), e0.size() * sizeof(float)) ||
+        !h2d(B.eps1, e1.data(), e1.size() * sizeof(float))) {
+      rc = GW_ECUDA;
+      break;
+    }
+    batch_center_kernel<<<Q, 256, 0, st>>>(B.x, B.xo, d, B.X, B.s, B.a);
+    batch_center_kernel<<<Q, 256, 0, st>>>(B.y, B.yo, d, B.Y, B.t, B.b);
+    count_launch();
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      rc = GW_ECUDA;
+      break;
+    }
+    rc = run_solve_batch(Q, B.xo, B.yo, BJ->n_max, BJ->m_max, d, d, B.X, B.Y, B.s, B.t, B.a, B.b,
+                         B.eps0, B.eps1, BJ->n_outer, BJ->n_inner, 1, B.f, B.g, B.G, B.Gp, B.en,
+                         nullptr, B.ws, batch_ws_bytes(), st);
+    if (rc != GW_OK) break;
+    if (cudaMemcpyAsync(en.data(), B.en, en.size() * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = GW_ECUDA;
+  } while (false);
+  if (rc != GW_OK) cudaStreamSynchronize(st);
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->pool->release(BJ->mem);
+  const double t_done = now_s();
+  for (int q = 0; q < Q; ++q) {
+    Job* J = BJ->members[q];
+    gw_response out;
+    memset(&out, 0, sizeof(out));
+    out.id = J->req.id;
+    out.t_submit = J->t_submit;
+    out.t_admit = J->t_admit;
+    out.t_done = t_done;
+    int st_q = rc;
+    if (rc == GW_OK) {
+      memcpy(out.energy, en.data() + static_cast<size_t>(q) * GW_EN_LEN, sizeof(out.energy));
+      const double es = out.energy[GW_EN_STATUS];
+      if (es != 0.0)
+        st_q = es == static_cast<double>(GW_EINVAL)     ? GW_EINVAL
+               : es == static_cast<double>(GW_ETIMEOUT) ? GW_ETIMEOUT
+                                                        : GW_ENONFINITE;
+    }
+    // asked to stop while the batch ran: its answer is the stop
+    if (J->stop_code != 0) st_q = J->stop_code;
+    out.status = st_q;
+    S->done.push_back(out);
+    S->running.erase(std::remove(S->running.begin(), S->running.end(), J), S->running.end());
+    delete J;
+  }
+  S->batch_busy = false;
+  S->cv_sched.notify_all();
+  S->cv_done.notify_all();
+}
+
+void batch_loop(gw_server* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  while (true) {
+    BatchJob* BJ = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_batch.wait(lk, [&] { return S->stop || !S->batch_ready.empty(); });
+      if (S->batch_ready.empty()) break;
+      BJ = S->batch_ready.front();
+      S->batch_ready.pop_front();
+    }
+    run_batch(S, BJ, st);
+    delete BJ;
+  }
+  cudaStreamDestroy(st);
+}
+
+// With the lane free, gather the waiting batchable requests that share the
+// first one's (d, n_outer, n_inner), in arrival order, while the batch's
+// largest clouds still fit one CTA; reserve their memory and hand the batch
+// to the lane.  Called with S->mu held.
+bool form_batch(gw_server* S) {
+  if (!S->batching || S->batch_busy) return false;
+  BatchJob* BJ = nullptr;
+  for (Job* J : S->pending) {
+    if (!batchable(J->req)) continue;
+    if (BJ == nullptr) {
+      BJ = new BatchJob();
+      BJ->d = J->req.d;
+      BJ->n_outer = J->req.n_outer;
+      BJ->n_inner = J->req.n_inner;
+    } else if (J->req.d != BJ->d || J->req.n_outer != BJ->n_outer ||
+               J->req.n_inner != BJ->n_inner) {
+      continue;
+    }
+    const int64_t nm = std::max<int64_t>(BJ->n_max, J->req.n);
+    const int64_t mm = std::max<int64_t>(BJ->m_max, J->req.m);
+    if (!batch_fits(nm, mm, BJ->d)) continue;
+    BJ->n_max = nm;
+    BJ->m_max = mm;
+    BJ->members.push_back(J);
+    if (static_cast<int>(BJ->members.size()) >= kBatchMax) break;
+  }
+  if (BJ == nullptr) return false;
+  int64_t SN = 0, SM = 0;
+  for (Job* J : BJ->members) {
+    SN += J->req.n;
+    SM += J->req.m;
+  }
+  Carver c(nullptr, ~size_t(0));
+  carve_batch(c, SN, SM, static_cast<int>(BJ->members.size()), BJ->d);
+  BJ->bytes = c.used() + 256;
+  BJ->mem = S->pool->alloc(BJ->bytes);
+  if (BJ->mem == nullptr) {
+    delete BJ;
+    return false;
+  }
+  const double t = now_s();
+  for (Job* J : BJ->members) {
+    S->pending.erase(std::find(S->pending.begin(), S->pending.end(), J));
+    S->running.push_back(J);
+    J->t_admit = t;
+  }
+  S->batch_busy = true;
+  S->batch_ready.push_back(BJ);
+  S->cv_batch.notify_one();
+  return true;
+}
+
 void scheduler_loop(gw_server* S) {
   std::unique_lock<std::mutex> lk(S->mu);
   while (!S->stop) {
     // admit in arrival order while a slot and memory are free
     bool admitted = false;
-    if (!S->pending.empty() && S->deadline > 0.0 &&
-        now_s() > S->pending.front()->t_submit + S->deadline) {
+    Job* expired = nullptr;
+    if (S->deadline > 0.0) {
+      const double now = now_s();
+      for (Job* J : S->pending)
+        if (now > J->t_submit + S->deadline) {
+          expired = J;
+          break;
+        }
+    }
+    if (expired != nullptr) {
       // past its deadline before it could run: answered without running
-      Job* J = S->pending.front();
-      S->pending.pop_front();
+      Job* J = expired;
+      S->pending.erase(std::find(S->pending.begin(), S->pending.end(), J));
       gw_response out;
       memset(&out, 0, sizeof(out));
       out.id = J->req.id;
@@ -387,11 +657,18 @@ void scheduler_loop(gw_server* S) {
       delete J;
       continue;
     }
-    if (!S->pending.empty() && S->active < S->max_active) {
-      Job* J = S->pending.front();
+    if (form_batch(S)) continue;
+    // the first waiting request of the slot path (batchable ones wait for the lane)
+    Job* J = nullptr;
+    for (Job* P : S->pending)
+      if (!(S->batching && batchable(P->req))) {
+        J = P;
+        break;
+      }
+    if (J != nullptr && S->active < S->max_active) {
       char* mem = S->pool->alloc(J->bytes);
       if (mem) {
-        S->pending.pop_front();
+        S->pending.erase(std::find(S->pending.begin(), S->pending.end(), J));
         S->running.push_back(J);
         if (J->preempted == 0) J->t_admit = now_s();
         J->mem = mem;
@@ -431,6 +708,7 @@ gw_server* gw_server_create(void* pool, size_t pool_bytes, int max_active, int d
   S->max_active = max_active;
   S->pool = new Pool(static_cast<char*>(pool), pool_bytes);
   for (int k = 0; k < max_active; ++k) S->workers.emplace_back(worker_loop, S);
+  S->batch_thread = std::thread(batch_loop, S);
   S->scheduler = std::thread(scheduler_loop, S);
   return S;
 }
@@ -519,6 +797,15 @@ int gw_server_cancel(gw_server* S, uint64_t id) {
   return GW_EINVAL;
 }
 
+int gw_server_set_batching(gw_server* S, int on) {
+  set_error("");
+  GW_REQUIRE(S != nullptr, GW_EINVAL, "gw_server_set_batching: null server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->batching = on != 0;
+  S->cv_sched.notify_all();
+  return GW_OK;
+}
+
 int gw_server_set_deadline(gw_server* S, double seconds) {
   set_error("");
   GW_REQUIRE(S != nullptr && isfinite(seconds), GW_EINVAL, "gw_server_set_deadline: bad argument");
@@ -548,11 +835,17 @@ void gw_server_destroy(gw_server* S) {
     S->stop = true;
     S->cv_sched.notify_all();
     S->cv_work.notify_all();
+    S->cv_batch.notify_all();
   }
   S->scheduler.join();
   for (auto& w : S->workers) w.join();
+  S->batch_thread.join();
   for (Job* J : S->pending) delete J;
   for (Job* J : S->ready) delete J;
+  for (BatchJob* B : S->batch_ready) {
+    for (Job* J : B->members) delete J;
+    delete B;
+  }
   delete S->pool;
   delete S;
 }

@@ -6,6 +6,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle as O
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -59,6 +60,7 @@ def test_server_matches_a_direct_solve(gw):
     req = make_request(7, 1200, 900, 0, 0, 0.05, seed=3)
     srv = gw.Server(pool_bytes=1 << 30, max_active=2)
     try:
+        srv.set_batching(False)          # the slot path: gw_solve itself
         res = run_all(srv, [req])[7]
     finally:
         srv.close()
@@ -250,3 +252,40 @@ def test_deadline_watchdog(gw):
         srv.close()
     with pytest.raises(gw.GWError):
         gw.Server(pool_bytes=1 << 20, max_active=1).set_deadline(float("nan"))
+
+
+def test_batch_lane_matches_oracle_alone_and_in_a_batch(gw):
+    """Small squared requests go through the batch lane (gw_solve_batch, one
+    CTA each): submitted together they share one launch (one admission
+    time), each result is bitwise the one it gets alone, and the energies
+    meet the FP32 bar against the oracle (Algorithm 1 on the centered clouds,
+    the same schedule)."""
+    sizes = [(1200, 900), (700, 1100), (1000, 1000), (600, 650), (1100, 800)]
+    reqs = [make_request(40 + k, n, m, 0, 0, 0.05 + 0.01 * k, seed=60 + k)
+            for k, (n, m) in enumerate(sizes)]
+    alone = {}
+    for r in reqs:
+        srv = gw.Server(pool_bytes=1 << 30, max_active=2)
+        try:
+            alone.update(run_all(srv, [r]))
+        finally:
+            srv.close()
+    srv = gw.Server(pool_bytes=1 << 30, max_active=2)
+    try:
+        together = run_all(srv, reqs)
+    finally:
+        srv.close()
+    admits = [together[r["id"]]["t_admit"] for r in reqs]
+    assert len(set(admits)) < len(reqs)              # at least two shared a launch
+    for r in reqs[:3]:
+        a_res, t_res = alone[r["id"]], together[r["id"]]
+        assert a_res["status"] == 0 and t_res["status"] == 0
+        assert a_res["energy"] == t_res["energy"], r["id"]
+        n, m = len(r["x"]), len(r["y"])
+        a = np.full(n, 1.0 / n)
+        b = np.full(m, 1.0 / m)
+        X = r["x"] - a @ r["x"]
+        Y = r["y"] - b @ r["y"]
+        ref = O.cnt_gw(a, b, X, Y, r["eps"], r["n_outer"], r["n_inner"], symmetric=True,
+                       record=True)["history"][-1]["E"]
+        assert abs(t_res["energy"][0] - ref) <= 1e-4 * abs(ref), (r["id"], t_res["energy"][0], ref)
