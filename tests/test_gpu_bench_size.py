@@ -153,3 +153,42 @@ def test_plan_sums_at_bench_size(gw, big, prec):
     err = np.abs(Wd[J] - W_ref)
     assert np.all(err <= Wb + 1e-15), (prec, np.max(err / (Wb + 1e-15)))
     assert np.isfinite(host(G)).all()
+
+
+def test_fp8_fused_iteration_at_bench_size(gw, big):
+    """The FP8 mode's fused iteration at N = M = 100k, D = 32 on sampled rows
+    (fast pass and the far rows' safe pass) against the oracle over all 100k
+    points of the other side on the features helpers.fp8_operands rounds
+    (one power-of-two scale per 128 rows of X and of V, e4m3), within the
+    FP32-accumulation and split-BF16 bound; beside it, the rounding's own
+    effect against the exact features is at most eps times the largest
+    exponent change it makes in the row."""
+    from helpers import fp8_operands, softmin_tolerance_fp8_emulated
+    P = big
+    Xh, Vh = fp8_operands(P["X"], P["V"])
+    fo, go = gw.gw_sinkhorn_iteration(f32(P["X"]), f32(P["V"]), f32(P["s"]), f32(P["t"]),
+                                      f32(P["la"]), f32(P["lb"]), f32(P["f"]), f32(P["h"]), EPS,
+                                      prec=4, symmetric=True)
+    fo, go = host(fo), host(go)
+    far_rows = np.flatnonzero(P["far"])[:40]
+    I = sampled(N, 160, 17, must=far_rows)
+    want_f = np.array([0.5 * (P["f"][i] + O.softmin_bilinear_one(i, Xh, Vh, P["s"], P["t"],
+                                                                  P["h"], P["lb"], EPS)) for i in I])
+    tf = np.array([0.5 * softmin_tolerance_fp8_emulated(Xh[i:i + 1], Vh, P["s"][i:i + 1], P["t"],
+                                                        P["h"], P["lb"], EPS)[0] for i in I]) \
+        + 1e-7 * np.abs(want_f)
+    ef = np.abs(fo[I] - want_f)
+    assert np.all(ef <= tf), (ef.max(), I[np.argmax(ef - tf)])
+    J = sampled(N, 160, 18)
+    want_g = np.array([0.5 * (P["h"][j] + O.softmin_bilinear_one(j, Vh, Xh, P["t"], P["s"],
+                                                                  P["f"], P["la"], EPS)) for j in J])
+    tg = np.array([0.5 * softmin_tolerance_fp8_emulated(Vh[j:j + 1], Xh, P["t"][j:j + 1], P["s"],
+                                                        P["f"], P["la"], EPS)[0] for j in J]) \
+        + 1e-7 * np.abs(want_g)
+    eg = np.abs(go[J] - want_g)
+    assert np.all(eg <= tg), (eg.max(), J[np.argmax(eg - tg)])
+    # the rounding's own error on the row half against the exact features
+    exact = np.array([0.5 * (P["f"][i] + O.softmin_bilinear_one(i, P["X"], P["V"], P["s"], P["t"],
+                                                                 P["h"], P["lb"], EPS)) for i in I[:40]])
+    dz = np.array([16.0 * np.abs(Xh[i] @ Vh.T - P["X"][i] @ P["V"].T).max() for i in I[:40]])
+    assert np.all(np.abs(fo[I[:40]] - exact) <= 0.5 * dz + tf[:40])
