@@ -238,60 +238,89 @@ __global__ void center_apply_kernel(const float* x, const double* mean, int64_t 
 // then discarded by the caller).  Dynamic shared memory: RP x RP doubles.
 __global__ void __launch_bounds__(256) chol_inv_kernel(const double* G, int RP, double* M,
                                                        int* status) {
+  // R: the factor in the upper triangle; below the diagonal, M's entries
+  // M_kc (k < c) at R[c][k] once the inverse is formed
   extern __shared__ double R[];   // [RP][RP]
   __shared__ double red[8];
+  __shared__ double rd[128];      // diagonal of R, then its reciprocals
+  __shared__ double md[128];      // diagonal of M
+  __shared__ double ivd[128];     // 1 / pivot, formed once by the lane that updates it
   __shared__ int bad;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nw = static_cast<int>(blockDim.x >> 5);
   const int RR = RP * RP;
   double tr = 0.0;
-  for (int e = tid; e < RR; e += blockDim.x) {
-    R[e] = G[e];
-    if (e / RP == e % RP) tr += G[e];
-  }
+  for (int e = tid; e < RR; e += blockDim.x) R[e] = G[e];
+  for (int i = tid; i < RP; i += blockDim.x) tr += G[i * RP + i];
   tr = warp_sum(tr);
-  if ((tid & 31) == 0) red[tid >> 5] = tr;
+  if (lane == 0) red[wid] = tr;
   if (tid == 0) bad = 0;
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    for (int q = 0; q < static_cast<int>(blockDim.x >> 5); ++q) t += red[q];
+    for (int q = 0; q < nw; ++q) t += red[q];
     red[0] = t;
     if (!(t > 0.0) || !isfinite(t)) bad = 1;
   }
   __syncthreads();
   const double shift = 1e-13 * red[0] / RP;
   for (int i = tid; i < RP; i += blockDim.x) R[i * RP + i] += shift;
+  if (tid == 0) ivd[0] = 1.0 / (G[0] + shift);
   __syncthreads();
-  // right-looking: pivot j, then row j of R, then the trailing update
-  for (int j = 0; j < RP && !bad; ++j) {
-    if (tid == 0) {
-      const double d = R[j * RP + j];
-      if (!(d > 0.0)) bad = 1;
-      else R[j * RP + j] = sqrt(d);
+  // right-looking, one barrier per pivot: the trailing update takes row j
+  // unscaled (R_jr R_jc = a_jr a_jc / d_j); the rows are scaled afterwards.
+  // FP64 division is slow on this GPU, so 1 / d_{j+1} is formed once, by the
+  // lane that writes d_{j+1}.  Every thread reads the same pivot, so all
+  // leave the loop together.
+  bool fail = bad != 0;
+  for (int j = 0; j < RP && !fail; ++j) {
+    const double d = R[j * RP + j];
+    if (!(d > 0.0)) {
+      fail = true;
+      break;
     }
-    __syncthreads();
-    if (bad) break;
-    const double dj = R[j * RP + j];
-    for (int i = j + 1 + tid; i < RP; i += blockDim.x) R[j * RP + i] /= dj;
-    __syncthreads();
-    for (int e = tid; e < RR; e += blockDim.x) {
-      const int r = e / RP, c = e % RP;
-      if (r > j && c >= r) R[r * RP + c] -= R[j * RP + r] * R[j * RP + c];
+    const double inv = ivd[j];
+    for (int r = j + 1 + wid; r < RP; r += nw) {
+      const double f = R[j * RP + r] * inv;
+      for (int c = r + lane; c < RP; c += 32) {
+        const double v = R[r * RP + c] - f * R[j * RP + c];
+        R[r * RP + c] = v;
+        if (c == j + 1) ivd[c] = 1.0 / v;   // the next pivot
+      }
     }
     __syncthreads();
   }
-  if (bad) {
+  if (fail) {
     for (int e = tid; e < RR; e += blockDim.x) M[e] = (e / RP == e % RP) ? 1.0 : 0.0;
     if (tid == 0) *status = 1;
     return;
   }
-  // M = R^{-1}: column c by back substitution (one thread per column)
+  for (int i = tid; i < RP; i += blockDim.x) {
+    const double q = sqrt(R[i * RP + i]);
+    R[i * RP + i] = q;
+    rd[i] = 1.0 / q;
+  }
+  __syncthreads();
+  for (int e = tid; e < RR; e += blockDim.x) {
+    const int r = e / RP, c = e - r * RP;
+    if (c > r) R[e] *= rd[r];
+  }
+  __syncthreads();
+  // M = R^{-1}: column c by back substitution (one thread per column), its
+  // entries kept in shared memory (row c below the diagonal, and md[c])
   for (int c = tid; c < RP; c += blockDim.x) {
-    for (int i = RP - 1; i >= 0; --i) {
+    for (int i = c; i >= 0; --i) {
       double acc = (i == c) ? 1.0 : 0.0;
-      for (int k = i + 1; k <= c; ++k) acc -= R[i * RP + k] * M[k * RP + c];
-      M[i * RP + c] = i <= c ? acc / R[i * RP + i] : 0.0;
+      for (int k = i + 1; k <= c; ++k) acc -= R[i * RP + k] * (k == c ? md[c] : R[c * RP + k]);
+      const double v = acc * rd[i];
+      if (i == c) md[c] = v;
+      else R[c * RP + i] = v;
     }
+  }
+  __syncthreads();
+  for (int e = tid; e < RR; e += blockDim.x) {
+    const int r = e / RP, c = e - r * RP;
+    M[e] = r < c ? R[c * RP + r] : (r == c ? md[r] : 0.0);
   }
 }
 
