@@ -46,12 +46,25 @@ __global__ void colsum_partial_kernel(const float* Q, const float* w, double wu,
   part[static_cast<int64_t>(blockIdx.x) * RP + r] = acc;
 }
 
+// Sum of cnt values at p[0], p[stride], ... in a fixed order, as four
+// interleaved chains (FP64 adds are long-latency here) combined at the end.
+__device__ __forceinline__ double strided_sum4(const double* p, int cnt, int64_t stride) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int b = 0;
+  for (; b + 4 <= cnt; b += 4) {
+    a0 += p[(b + 0) * stride];
+    a1 += p[(b + 1) * stride];
+    a2 += p[(b + 2) * stride];
+    a3 += p[(b + 3) * stride];
+  }
+  for (; b < cnt; ++b) a0 += p[b * stride];
+  return (a0 + a1) + (a2 + a3);
+}
+
 __global__ void colsum_final_kernel(const double* part, int blocks, int RP, double* out) {
   const int r = threadIdx.x;
   if (r >= RP) return;
-  double acc = 0.0;
-  for (int b = 0; b < blocks; ++b) acc += part[static_cast<int64_t>(b) * RP + r];
-  out[r] = acc;
+  out[r] = strided_sum4(part + r, blocks, RP);
 }
 
 // P = Q - w (1^T Q)
@@ -126,21 +139,42 @@ __global__ void gram_final_kernel(const double* part, int blocks, int RP, bool s
   if (e >= RR) return;
   const int r1 = e / RP, r2 = e % RP;
   const int src = (sym && r1 > r2) ? r2 * RP + r1 : e;   // the mirrored entry
-  double a = 0.0;
-  for (int b = 0; b < blocks; ++b) a += part[static_cast<int64_t>(b) * RR + src];
-  G[e] = a;
+  G[e] = strided_sum4(part + src, blocks, RR);
 }
 
-// Out_i[c] = sum_r In_i[r] M[r][c]  (M: RP x cols, float64), cols <= RP
-__global__ void right_mult_kernel(const float* In, int64_t n, int RP, const double* M, int cols,
-                                  int out_stride, float* Out) {
+// A float64 matrix entry stored as two floats: hi = fl(v), lo = fl(v - hi).
+__device__ __forceinline__ void store_split(float* M, int64_t lo_off, int64_t e, double v) {
+  const float hi = static_cast<float>(v);
+  M[e] = hi;
+  M[lo_off + e] = static_cast<float>(v - static_cast<double>(hi));
+}
+
+// Out_i[c] = sum_r In_i[r] M[r][c]  (M: RP x cols as hi + lo float pairs, the
+// lo block lo_off entries after the hi block), cols <= RP.  FP64 is 1/64 rate
+// on this GPU, so the sum runs in double-float on the FP32 lanes: each product
+// In_ir (M_hi + M_lo) is exact to ~2^-48 by Dekker's TwoProduct (one FMA for
+// the error of In_ir M_hi) and accumulated by Knuth's TwoSum, the rounding
+// errors collected in a second float; the result (~44 bits) is rounded to
+// FP32 once, as the float64 form did.
+__global__ void right_mult_kernel(const float* In, int64_t n, int RP, const float* M,
+                                  int64_t lo_off, int cols, int out_stride, float* Out) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= n * cols) return;
   const int64_t i = q / cols;
   const int c = static_cast<int>(q % cols);
-  double a = 0.0;
-  for (int r = 0; r < RP; ++r) a = fma(static_cast<double>(In[i * RP + r]), M[r * cols + c], a);
-  Out[i * out_stride + c] = static_cast<float>(a);
+  float sh = 0.0f, sl = 0.0f;
+  for (int r = 0; r < RP; ++r) {
+    const float a = In[i * RP + r];
+    const float mh = M[r * cols + c], ml = M[lo_off + r * cols + c];
+    const float ph = __fmul_rn(a, mh);
+    const float pl = __fadd_rn(__fmaf_rn(a, mh, -ph), __fmul_rn(a, ml));
+    const float sn = __fadd_rn(sh, ph);
+    const float v = __fsub_rn(sn, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(sn, v)), __fsub_rn(ph, v));
+    sh = sn;
+    sl = __fadd_rn(sl, __fadd_rn(err, pl));
+  }
+  Out[i * out_stride + c] = __fadd_rn(sh, sl);
 }
 
 // Deterministic start block: uniform(-1, 1) from a counter hash (splitmix64).
@@ -236,7 +270,7 @@ __global__ void center_apply_kernel(const float* x, const double* mean, int64_t 
 // when a direction vanishes.  A trace that is not positive and finite, or a
 // pivot that is not positive, sets *status = 1 and leaves M = I (the result is
 // then discarded by the caller).  Dynamic shared memory: RP x RP doubles.
-__global__ void __launch_bounds__(256) chol_inv_kernel(const double* G, int RP, double* M,
+__global__ void __launch_bounds__(256) chol_inv_kernel(const double* G, int RP, float* M,
                                                        int* status) {
   // R: the factor in the upper triangle; below the diagonal, M's entries
   // M_kc (k < c) at R[c][k] once the inverse is formed
@@ -291,7 +325,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const double* G, int RP, 
     __syncthreads();
   }
   if (fail) {
-    for (int e = tid; e < RR; e += blockDim.x) M[e] = (e / RP == e % RP) ? 1.0 : 0.0;
+    for (int e = tid; e < RR; e += blockDim.x) store_split(M, RR, e, (e / RP == e % RP) ? 1.0 : 0.0);
     if (tid == 0) *status = 1;
     return;
   }
@@ -320,7 +354,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const double* G, int RP, 
   __syncthreads();
   for (int e = tid; e < RR; e += blockDim.x) {
     const int r = e / RP, c = e - r * RP;
-    M[e] = r < c ? R[c * RP + r] : (r == c ? md[r] : 0.0);
+    store_split(M, RR, e, r < c ? R[c * RP + r] : (r == c ? md[r] : 0.0));
   }
 }
 
@@ -332,7 +366,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const double* G, int RP, 
 // the off-diagonal mass is below 1e-30 of the total (at most 100).
 // Dynamic shared memory: RP x RP doubles.
 __global__ void __launch_bounds__(256) ritz_eig_kernel(const double* T, int RP, int D, double* U,
-                                                       double* Msel, float* lam, float* sl) {
+                                                       float* Msel, float* lam, float* sl) {
   extern __shared__ double A[];   // [RP][RP]
   __shared__ double cs[64][2];
   __shared__ double red[2][8];
@@ -429,7 +463,7 @@ __global__ void __launch_bounds__(256) ritz_eig_kernel(const double* T, int RP, 
     if (rank < D) {
       lam[rank] = static_cast<float>(lk);
       sl[rank] = static_cast<float>(sqrt(lk > 0.0 ? lk : 0.0));
-      for (int r = 0; r < RP; ++r) Msel[r * D + rank] = U[r * RP + k];
+      for (int r = 0; r < RP; ++r) store_split(Msel, RR, r * D + rank, U[r * RP + k]);
     }
   }
 }
@@ -458,7 +492,8 @@ int rpad(int D) {
 
 struct LiftBufs {
   float *Q, *P, *Z, *Zp, *V, *sl, *lam;
-  double *cs_part, *cs, *g_part, *G, *M;
+  double *cs_part, *cs, *g_part, *G;
+  float* M;   // R^-1 (or the Ritz vectors) as hi + lo float pairs
   int* status;
   int splits, RP;
   LiftTcBufs tc;
@@ -481,7 +516,7 @@ LiftBufs carve_lift(Carver& c, int64_t n, int D) {
   B.cs = c.take<double>(B.RP);
   B.g_part = c.take<double>(static_cast<size_t>(kGramBlocks) * B.RP * B.RP);
   B.G = c.take<double>(static_cast<size_t>(B.RP) * B.RP);
-  B.M = c.take<double>(static_cast<size_t>(B.RP) * B.RP);
+  B.M = c.take<float>(static_cast<size_t>(2) * B.RP * B.RP);   // hi, then lo
   B.status = c.take<int>(4);
   return B;
 }
@@ -547,7 +582,9 @@ int orthonormalize(int64_t n, LiftBufs& B, cudaStream_t st) {
   GW_TRY(gram(B.Z, B.Z, n, RP, B, st));
   chol_inv_kernel<<<1, 256, sizeof(double) * RP * RP, st>>>(B.G, RP, B.M, B.status);
   GW_LAUNCH_CHECK();
-  right_mult_kernel<<<ceil_div(n * RP, 256), 256, 0, st>>>(B.Z, n, RP, B.M, RP, RP, B.Q);
+  right_mult_kernel<<<ceil_div(n * RP, 256), 256, 0, st>>>(B.Z, n, RP, B.M,
+                                                            static_cast<int64_t>(RP) * RP, RP, RP,
+                                                            B.Q);
   GW_LAUNCH_CHECK();
   return GW_OK;
 }
@@ -601,7 +638,9 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
   ritz_eig_kernel<<<1, 256, sizeof(double) * RP * RP, st>>>(B.G, RP, D, B.g_part, B.M, B.lam,
                                                              B.sl);
   GW_LAUNCH_CHECK();
-  right_mult_kernel<<<ceil_div(n * D, 256), 256, 0, st>>>(B.Q, n, RP, B.M, D, D, B.V);
+  right_mult_kernel<<<ceil_div(n * D, 256), 256, 0, st>>>(B.Q, n, RP, B.M,
+                                                           static_cast<int64_t>(RP) * RP, D, D,
+                                                           B.V);
   GW_LAUNCH_CHECK();
   sign_partial_kernel<<<kGramBlocks, 128, 0, st>>>(B.V, n, D, B.g_part, B.g_part + kGramBlocks * D);
   GW_LAUNCH_CHECK();
