@@ -105,34 +105,6 @@ struct WaitCtl {
 // The current limit (gw_set_wait_limit_ns) and this device's give-up counter.
 tc::WaitCtl wait_ctl();
 
-// ------------------------------------------- programmatic dependent launch
-// The Sinkhorn iteration's kernels (operand refresh, the softmin passes and
-// their merges) are launched with programmatic stream serialization, so a
-// kernel's launch overlaps the one before it.  Each of them starts with
-// pdl_enter(): wait until the previous kernel of the stream has completed
-// and its memory is visible (before any global access), then let the next
-// kernel be launched.  Launched without the attribute both are no-ops.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                       cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
-
 // ------------------------------------------------------------ device math
 __device__ __forceinline__ float ex2(float x) {
   float y;

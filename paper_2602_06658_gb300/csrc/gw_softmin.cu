@@ -30,7 +30,6 @@ struct RowsPerThread {
 template <int KP, int R>
 __global__ void __launch_bounds__(kThreads)
     softmin_fp32_kernel(SoftminTask t0, SoftminTask t1, int blocks0) {
-  pdl_enter();
   const bool second = static_cast<int>(blockIdx.x) >= blocks0;
   const SoftminTask T = second ? t1 : t0;
   const int bid = second ? blockIdx.x - blocks0 : blockIdx.x;
@@ -141,7 +140,6 @@ __global__ void __launch_bounds__(kThreads)
 
 // Merge the per-split (max, sum) pairs of up to two tasks.
 __global__ void softmin_combine_kernel(SoftminTask t0, SoftminTask t1, int64_t n0) {
-  pdl_enter();
   const int64_t gi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool second = gi >= n0;
   const SoftminTask T = second ? t1 : t0;
@@ -174,7 +172,7 @@ template <int KP>
 void launch_fp32(const SoftminTask& t0, const SoftminTask& t1, int blocks0, int blocks,
                  cudaStream_t st) {
   constexpr int R = RowsPerThread<KP>::value;
-  (void)launch_pdl(softmin_fp32_kernel<KP, R>, dim3(blocks), dim3(kThreads), 0, st, t0, t1, blocks0);
+  softmin_fp32_kernel<KP, R><<<blocks, kThreads, 0, st>>>(t0, t1, blocks0);
 }
 
 }  // namespace
@@ -255,8 +253,7 @@ int launch_softmin(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cudaStr
   if (need_combine) {
     const int64_t nn = t[0].n + t[1].n;
     const int thr = 256;
-    GW_CUDA_TRY(launch_pdl(softmin_combine_kernel, dim3(ceil_div(nn, thr)), dim3(thr), 0, st, t[0],
-                           t[1], t[0].n));
+    softmin_combine_kernel<<<ceil_div(nn, thr), thr, 0, st>>>(t[0], t[1], t[0].n);
     GW_LAUNCH_CHECK();
   }
   return GW_OK;

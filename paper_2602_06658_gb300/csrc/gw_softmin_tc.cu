@@ -177,7 +177,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     softmin_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mB0,
                       const __grid_constant__ CUtensorMap mA1, const __grid_constant__ CUtensorMap mB1,
                       TcTask t0, TcTask t1) {
-  pdl_enter();
   using L = TcSmem<KP, S, BN>;
   constexpr int KB = L::KB;
   constexpr int kTmemCols = 4 * BN;   // 2 buffers x 2 halves
@@ -470,7 +469,6 @@ __global__ void tc_layout_kernel(const unsigned* mxA, const unsigned* mxB, int K
 // rows of unflagged tiles whose total is in range are written, the others
 // flag their tile; mode 2 (after the safe pass): rows of flagged tiles only.
 __global__ void tc_combine_kernel(TcTask t0, TcTask t1, int64_t n0, int mode) {
-  pdl_enter();
   const int64_t gi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool second = gi >= n0;
   const TcTask& T = second ? t1 : t0;
@@ -498,8 +496,7 @@ __global__ void tc_combine_kernel(TcTask t0, TcTask t1, int64_t n0, int mode) {
 int run_combine(const TcTask& a, const TcTask& b, int mode, cudaStream_t st) {
   if (a.splits == 1 && (b.blocks == 0 || b.splits == 1)) return GW_OK;
   const int64_t nn = a.n + (b.blocks ? b.n : 0);
-  GW_CUDA_TRY(launch_pdl(tc_combine_kernel, dim3(ceil_div(nn, 256)), dim3(256), 0, st, a, b, a.n,
-                         mode));
+  tc_combine_kernel<<<ceil_div(nn, 256), 256, 0, st>>>(a, b, a.n, mode);
   GW_LAUNCH_CHECK();
   return GW_OK;
 }
@@ -536,8 +533,7 @@ int launch_tc_kernel(const CUtensorMap* maps, const TcTask& a, const TcTask& b, 
     attr_rc = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
   });
   GW_CUDA_TRY(attr_rc);
-  GW_CUDA_TRY(launch_pdl(kern, dim3(a.blocks + b.blocks), dim3(kThreadsTc), L::kBytes, st, maps[0],
-                         maps[1], maps[2], maps[3], a, b));
+  kern<<<a.blocks + b.blocks, kThreadsTc, L::kBytes, st>>>(maps[0], maps[1], maps[2], maps[3], a, b);
   GW_LAUNCH_CHECK();
   return GW_OK;
 }
@@ -805,21 +801,16 @@ int launch_softmin_tc(SoftminTask* tasks, int ntasks, int prec, Carver& ws, cuda
   if (tasks[0].reuse_ops) {
     float* part = ws.take<float>(static_cast<size_t>(2 * 2 * kSmCount));
     GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for the tensor-core softmin");
-    GW_CUDA_TRY(launch_pdl(tc_refresh_max_kernel, dim3(kSmCount), dim3(256), 0, st, refresh[0],
-                           refresh[1], ntasks, part));
+    tc_refresh_max_kernel<<<kSmCount, 256, 0, st>>>(refresh[0], refresh[1], ntasks, part);
     GW_LAUNCH_CHECK();
     int64_t rows = 0;
     for (int q = 0; q < ntasks; ++q) rows += refresh[q].n + refresh[q].m;
     if (bf16) {
-      GW_CUDA_TRY(launch_pdl(tc_refresh_multi_kernel<__nv_bfloat16>, dim3(ceil_div(rows, 256)),
-                             dim3(256), 0, st, refresh[0], refresh[1], ntasks, shp,
-                             static_cast<const float*>(part), static_cast<int>(kSmCount),
-                             static_cast<const int*>(lay), shp_a));
+      tc_refresh_multi_kernel<__nv_bfloat16><<<ceil_div(rows, 256), 256, 0, st>>>(
+          refresh[0], refresh[1], ntasks, shp, part, kSmCount, lay, shp_a);
     } else {
-      GW_CUDA_TRY(launch_pdl(tc_refresh_multi_kernel<__half>, dim3(ceil_div(rows, 256)), dim3(256),
-                             0, st, refresh[0], refresh[1], ntasks, shp,
-                             static_cast<const float*>(part), static_cast<int>(kSmCount),
-                             static_cast<const int*>(lay), shp_a));
+      tc_refresh_multi_kernel<__half><<<ceil_div(rows, 256), 256, 0, st>>>(
+          refresh[0], refresh[1], ntasks, shp, part, kSmCount, lay, shp_a);
     }
     GW_LAUNCH_CHECK();
   }

@@ -351,7 +351,6 @@ struct RefreshTask {
 
 __global__ void tc_refresh_max_kernel(RefreshTask t0, RefreshTask t1, int ntasks, float* part) {
   __shared__ float red[2][8];
-  pdl_enter();
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   for (int q = 0; q < ntasks; ++q) {
@@ -394,7 +393,6 @@ __global__ void tc_refresh_multi_kernel(RefreshTask t0, RefreshTask t1, int ntas
                                         TcOperandShape shp_f, const float* part, int nparts,
                                         const int* lay = nullptr,
                                         TcOperandShape shp_a = TcOperandShape{}) {
-  pdl_enter();
   const TcOperandShape shp = (lay != nullptr && lay[0] != 0) ? shape_ks(shp_a, lay[1]) : shp_f;
   __shared__ float cw[2], ce[2];
   if (threadIdx.x < 32) {
