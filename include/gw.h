@@ -66,7 +66,10 @@ typedef struct CUstream_st* gw_stream_t;
                             * same rounding in the row and column softmins and the plan
                             * sums), the rank-one, bias and shift columns as split BF16 in
                             * the same FP32 accumulator, 16 log2(e) / eps applied in the
-                            * epilogue.  A measured mode: e4m3's 3 mantissa bits move the
+                            * epilogue.  The softmin takes K <= 128; the plan sums, the
+                            * solve and the energy take D <= 61 (GW_EUNSUPPORTED beyond,
+                            * where no plan kernel rounds the same features).
+                            * A measured mode: e4m3's 3 mantissa bits move the
                             * exponent by whole log2 units already at eps = 0.1 on
                             * unit-scale features (the error is stated per eps beside the
                             * other modes); not an accuracy-preserving form. */
