@@ -58,7 +58,9 @@ typedef struct CUstream_st* gw_stream_t;
  * potentials and all accumulations stay float32 (Gamma and energies float64)
  * in every mode. */
 #define GW_PREC_FP32 0     /* FP32 dot products on the CUDA cores */
-#define GW_PREC_BF16 1     /* BF16 operands on tcgen05, FP32 accumulate */
+#define GW_PREC_BF16 1     /* BF16 operands on tcgen05, FP32 accumulate (a speed reference:
+                            * its exponent error grows as 1 / eps; with D + 3 > 64 its plan
+                            * sums run in FP32 on the exact features) */
 #define GW_PREC_BF16X3 2   /* split BF16 (hi*hi + hi*lo + lo*hi) on tcgen05 */
 #define GW_PREC_F16X3 3    /* split FP16 with scaling (hi*hi + hi*lo + lo*hi) on tcgen05 */
 #define GW_PREC_FP8 4      /* E4M3 features on tcgen05 (kind::f8f6f4): each feature matrix
