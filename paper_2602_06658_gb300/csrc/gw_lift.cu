@@ -36,14 +36,27 @@ struct CostParams {
 // Column sums weighted by w (or plain) of an n x RP matrix: partials per block.
 __global__ void colsum_partial_kernel(const float* Q, const float* w, double wu, int64_t n,
                                       int RP, double* part) {
-  // blockDim.x == RP (<= 128); rows strided over blocks; weight w_i, or wu
-  const int r = threadIdx.x;
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-    const double wi = w ? static_cast<double>(w[i]) : wu;
-    acc += wi * static_cast<double>(Q[i * RP + r]);
+  // blockDim = (RP <= 128, 4): column r, row group y; the rows are strided
+  // over blocks and groups, two in flight per thread (the loads' latency,
+  // not the adds, bounds this); the groups' sums merge in a fixed order.
+  // Weight w_i, or wu.
+  __shared__ double red[4][128];
+  const int r = threadIdx.x, y = threadIdx.y;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * 4;
+  double a0 = 0.0, a1 = 0.0;
+  int64_t i = static_cast<int64_t>(blockIdx.x) * 4 + y;
+  for (; i + step < n; i += 2 * step) {
+    const int64_t i1 = i + step;
+    const double w0 = w ? static_cast<double>(w[i]) : wu;
+    const double w1 = w ? static_cast<double>(w[i1]) : wu;
+    a0 += w0 * static_cast<double>(Q[i * RP + r]);
+    a1 += w1 * static_cast<double>(Q[i1 * RP + r]);
   }
-  part[static_cast<int64_t>(blockIdx.x) * RP + r] = acc;
+  if (i < n) a0 += (w ? static_cast<double>(w[i]) : wu) * static_cast<double>(Q[i * RP + r]);
+  red[y][r] = a0 + a1;
+  __syncthreads();
+  if (y == 0)
+    part[static_cast<int64_t>(blockIdx.x) * RP + r] = (red[0][r] + red[1][r]) + (red[2][r] + red[3][r]);
 }
 
 // Sum of cnt values at p[0], p[stride], ... in a fixed order, as four
@@ -98,9 +111,11 @@ __global__ void center_left_kernel(float* Z, const double* wz, int64_t n, int RP
 // (when sym, U == Z and only r1 <= r2 is computed)
 __global__ void gram_partial_kernel(const float* U, const float* Z, int64_t n, int RP, bool sym,
                                     double* part) {
-  extern __shared__ float sh[];
-  float* Us = sh;               // [32][RP]
-  float* Zs = sh + 32 * RP;     // [32][RP]
+  // the chunk's rows as float64, converted once on load (each is used by
+  // every entry of the Gram; conversions run on the slow FP64 pipe too)
+  extern __shared__ double shd[];
+  double* Us = shd;             // [32][RP]
+  double* Zs = shd + 32 * RP;   // [32][RP]
   const int RR = RP * RP;
   const int per = (RR + blockDim.x - 1) / blockDim.x;
   double acc[64];
@@ -112,8 +127,8 @@ __global__ void gram_partial_kernel(const float* U, const float* Z, int64_t n, i
     __syncthreads();
     const int cnt = static_cast<int>(i1 - ib < 32 ? i1 - ib : 32);
     for (int idx = threadIdx.x; idx < cnt * RP; idx += blockDim.x) {
-      Us[idx] = U[ib * RP + idx];
-      Zs[idx] = Z[ib * RP + idx];
+      Us[idx] = static_cast<double>(U[ib * RP + idx]);
+      Zs[idx] = static_cast<double>(Z[ib * RP + idx]);
     }
     __syncthreads();
     for (int q = 0; q < per; ++q) {
@@ -122,8 +137,7 @@ __global__ void gram_partial_kernel(const float* U, const float* Z, int64_t n, i
       const int r1 = e / RP, r2 = e % RP;
       if (sym && r1 > r2) continue;
       double a = 0.0;
-      for (int ii = 0; ii < cnt; ++ii)
-        a = fma(static_cast<double>(Us[ii * RP + r1]), static_cast<double>(Zs[ii * RP + r2]), a);
+      for (int ii = 0; ii < cnt; ++ii) a = fma(Us[ii * RP + r1], Zs[ii * RP + r2], a);
       acc[q] += a;
     }
   }
@@ -523,7 +537,7 @@ LiftBufs carve_lift(Carver& c, int64_t n, int D) {
 
 int weighted_colsum(const float* Q, const float* w, double wu, int64_t n, int RP, LiftBufs& B,
                     cudaStream_t st) {
-  colsum_partial_kernel<<<kGramBlocks, RP, 0, st>>>(Q, w, wu, n, RP, B.cs_part);
+  colsum_partial_kernel<<<kGramBlocks, dim3(RP, 4), 0, st>>>(Q, w, wu, n, RP, B.cs_part);
   GW_LAUNCH_CHECK();
   colsum_final_kernel<<<1, 128, 0, st>>>(B.cs_part, kGramBlocks, RP, B.cs);
   GW_LAUNCH_CHECK();
@@ -552,7 +566,7 @@ int apply_kernel(int64_t n, int d, const float* w, CostParams cp, LiftBufs& B, c
 
 // G = U^T Z on the device (float64, fixed-order partials)
 int gram(const float* U, const float* Z, int64_t n, int RP, LiftBufs& B, cudaStream_t st) {
-  const size_t shb = sizeof(float) * 2 * 32 * RP;
+  const size_t shb = sizeof(double) * 2 * 32 * RP;
   const bool sym = U == Z;
   gram_partial_kernel<<<kGramBlocks, 256, shb, st>>>(U, Z, n, RP, sym, B.g_part);
   GW_LAUNCH_CHECK();
@@ -568,6 +582,9 @@ int small_kernel_attrs() {
   std::call_once(once, [] {
     rc = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               128 * 128 * 8);
+    if (rc == cudaSuccess)   // the Gram's row chunks: 2 x 32 x 128 doubles at most
+      rc = cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * 32 * 128 * 8);
     if (rc == cudaSuccess)
       rc = cudaFuncSetAttribute(ritz_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 128 * 128 * 8);
@@ -605,7 +622,7 @@ int run_lift(const float* x, int64_t n, int d, const float* w, int kind, float p
     double* part = c.take<double>(static_cast<size_t>(kGramBlocks) * d);
     double* mean = c.take<double>(static_cast<size_t>(d));
     GW_TRY(check_ws(c, ws));
-    colsum_partial_kernel<<<kGramBlocks, d, 0, st>>>(x, w, 1.0 / static_cast<double>(n), n, d,
+    colsum_partial_kernel<<<kGramBlocks, dim3(d, 4), 0, st>>>(x, w, 1.0 / static_cast<double>(n), n, d,
                                                        part);
     GW_LAUNCH_CHECK();
     colsum_final_kernel<<<1, 128, 0, st>>>(part, kGramBlocks, d, mean);

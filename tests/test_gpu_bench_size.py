@@ -192,3 +192,36 @@ def test_fp8_fused_iteration_at_bench_size(gw, big):
                                                                  P["h"], P["lb"], EPS)) for i in I[:40]])
     dz = np.array([16.0 * np.abs(Xh[i] @ Vh.T - P["X"][i] @ P["V"].T).max() for i in I[:40]])
     assert np.all(np.abs(fo[I[:40]] - exact) <= 0.5 * dz + tf[:40])
+
+
+def test_fp8_plan_sums_at_bench_size(gw, big):
+    """The FP8 plan sums with 100k sources (many source splits) for sampled
+    targets, against the oracle's plan columns over all sources on the
+    e4m3-rounded features (helpers.fp8_operands); Gamma_t = I / 4 so that
+    V = Gamma_t Y is exact in FP32 and both sides round the same V.  The
+    column potential makes pi_ij / b_j <= 1 on the rounded cost, as in the
+    16-bit test."""
+    from helpers import fp8_operands
+    P = big
+    Gt = 0.25 * np.eye(D)
+    V4 = 0.25 * P["Y"]
+    Xh, Vh = fp8_operands(P["X"], V4)
+    zc = max_exponent(Vh, Xh, P["t"], P["s"], P["f"], P["la"], EPS)
+    g_plan = r32(-EPS * zc)
+    G, stats, Wd = gw.gw_cross_cov(f32(P["X"]), f32(P["Y"]), f32(P["s"]), f32(P["t"]), f32(P["a"]),
+                                   f32(P["b"]), f32(P["f"]), f32(g_plan), f64(Gt), EPS, prec=4,
+                                   want_W=True)
+    Wd = host(Wd)
+    J = sampled(N, 96, 19)
+    U = np.concatenate([P["X"], P["s"][:, None], np.ones((N, 1))], axis=1)
+    C = -16.0 * Xh @ Vh[J].T - 4.0 * np.outer(P["s"], P["t"][J])
+    pi = O.plan(P["a"], P["b"][J], P["f"], g_plan[J], C, EPS)
+    W_ref = pi.T @ U
+    S = (16.0 * np.abs(Xh) @ np.abs(Vh[J]).T + 4.0 * np.outer(P["s"], P["t"][J])
+         + np.abs(P["f"])[:, None] + np.abs(g_plan[J])[None, :]
+         + EPS * (np.abs(P["la"])[:, None] + np.abs(P["lb"][J])[None, :])).max()
+    rel = 2.0 * ((D + 4) * 2.0 ** -15 * S / EPS + math.sqrt(N) * 2.0 ** -23 + 2.0 ** -20)
+    Wb = rel * (pi.T @ np.abs(U))
+    err = np.abs(Wd[J] - W_ref)
+    assert np.all(err <= Wb + 1e-15), np.max(err / (Wb + 1e-15))
+    assert np.isfinite(host(G)).all()
