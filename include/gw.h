@@ -59,7 +59,7 @@ typedef struct CUstream_st* gw_stream_t;
  * in every mode. */
 #define GW_PREC_FP32 0     /* FP32 dot products on the CUDA cores */
 #define GW_PREC_BF16 1     /* BF16 operands on tcgen05, FP32 accumulate (a speed reference:
-                            * its exponent error grows as 1 / eps; with D + 3 > 64 its plan
+                            * its exponent error grows as 1 / eps; with D + 3 > 80 its plan
                             * sums run in FP32 on the exact features) */
 #define GW_PREC_BF16X3 2   /* split BF16 (hi*hi + hi*lo + lo*hi) on tcgen05 */
 #define GW_PREC_F16X3 3    /* split FP16 with scaling (hi*hi + hi*lo + lo*hi) on tcgen05 */
@@ -69,7 +69,7 @@ typedef struct CUstream_st* gw_stream_t;
                             * sums), the rank-one, bias and shift columns as split BF16 in
                             * the same FP32 accumulator, 16 log2(e) / eps applied in the
                             * epilogue.  The softmin takes K <= 128; the plan sums, the
-                            * solve and the energy take D <= 61 (GW_EUNSUPPORTED beyond,
+                            * solve and the energy take D <= 77 (GW_EUNSUPPORTED beyond,
                             * where no plan kernel rounds the same features).
                             * A measured mode: e4m3's 3 mantissa bits move the
                             * exponent by whole log2 units already at eps = 0.1 on

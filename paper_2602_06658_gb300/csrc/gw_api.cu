@@ -530,9 +530,9 @@ int gw_solve(const gw_problem* p, const gw_options* o, gw_result* r, void* ws, s
   GW_REQUIRE(o->n_outer >= 1 && o->n_inner >= 1, GW_EINVAL, "n_outer, n_inner must be >= 1");
   GW_REQUIRE(o->n_outer <= 100000 && o->n_inner <= 1000000, GW_EINVAL, "iteration counts too large");
   GW_TRY(check_prec(o->prec));
-  // the FP8 softmin needs plan sums on the same rounded features (tensor-core plan, D + 3 <= 64)
+  // the FP8 softmin needs plan sums on the same rounded features (tensor-core plan, D + 3 <= 80)
   GW_REQUIRE(o->prec != GW_PREC_FP8 || plan_tc_supported(p->D, o->prec), GW_EUNSUPPORTED,
-             "GW_PREC_FP8 solves need D + 3 <= 64 (D = %d); the FP8 softmin alone takes D <= 128",
+             "GW_PREC_FP8 solves need D + 3 <= 80 (D = %d); the FP8 softmin alone takes D <= 128",
              p->D);
   NONNULL(p->X);
   NONNULL(p->Y);

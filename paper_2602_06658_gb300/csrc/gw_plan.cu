@@ -660,7 +660,7 @@ static int cross_cov_stage(const PlanArgs& p, int prec, double* W_user, Carver& 
   GW_REQUIRE(prec >= GW_PREC_FP32 && prec <= GW_PREC_FP8, GW_EUNSUPPORTED, "precision %d", prec);
   // FP8 plan sums must see the softmin's rounded features: only the tensor-core form does
   GW_REQUIRE(prec != GW_PREC_FP8 || plan_tc_supported(p.D, prec), GW_EUNSUPPORTED,
-             "GW_PREC_FP8 plan sums need D + 3 <= 64 (D = %d)", p.D);
+             "GW_PREC_FP8 plan sums need D + 3 <= 80 (D = %d)", p.D);
   CrossCovLayout L = carve_cross_cov(ws, p.n, p.m, p.D, p.E, W_user == nullptr);
   GW_REQUIRE(!ws.overflow, GW_ENOMEM, "workspace too small for cross-covariance");
   if (W_user) L.W = W_user;

@@ -335,26 +335,30 @@ __global__ void __launch_bounds__(kPlanThreads, 1)
     if (go) {
       tc::tc_fence_after();
       if (ch == 0) {
-        uint32_t w0[32], w1[32];
+        // the W row in chunks of 32 columns (the last chunk may run past NW
+        // into columns this row does not use; TMEM holds 512)
         const uint32_t wa = tbase + (static_cast<uint32_t>(q * 32) << 16) + kPlanWCol + h * NW;
-        tc::tmem_ld32_issue(wa, w0);
-        tc::tmem_ld_wait(w0);
-        tc::tmem_ld32_issue(wa + 32, w1);
-        tc::tmem_ld_wait(w1);
         const int64_t j = static_cast<int64_t>(row0) + h * 128 + rloc;
-        if (j < T.rows) {
-          const float bj = T.b[j];
-          float* out = T.Wp + (static_cast<int64_t>(sp) * T.rows + j) * (T.D + 2);
-          for (int d = 0; d < T.D + 2; ++d) {
-            const float v = __uint_as_float(d < 32 ? w0[d] : w1[d - 32]);
-            out[d] = v * bj * T.uinv[d];
-          }
-          if (T.Ep != nullptr) {
-            const int d = T.D + 2;   // the log a column
-            const float v = __uint_as_float(d < 32 ? w0[d] : w1[d - 32]);
-            float* e2 = T.Ep + (static_cast<int64_t>(sp) * T.rows + j) * 2;
-            e2[0] = ent * bj * (1.0f / kPlanQScale);
-            e2[1] = v * bj * T.uinv[d];
+        const bool in = j < T.rows;
+        const float bj = in ? T.b[j] : 0.0f;
+        float* out = T.Wp + (static_cast<int64_t>(sp) * T.rows + (in ? j : 0)) * (T.D + 2);
+        float* e2 = T.Ep ? T.Ep + (static_cast<int64_t>(sp) * T.rows + (in ? j : 0)) * 2 : nullptr;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NW; c0 += 32) {
+          uint32_t w[32];
+          tc::tmem_ld32_issue(wa + c0, w);
+          tc::tmem_ld_wait(w);
+          if (!in) continue;
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int d = c0 + k;
+            const float v = __uint_as_float(w[k]);
+            if (d < T.D + 2) {
+              out[d] = v * bj * T.uinv[d];
+            } else if (d == T.D + 2 && T.Ep != nullptr) {   // the log a column, and the KL sum
+              e2[0] = ent * bj * (1.0f / kPlanQScale);
+              e2[1] = v * bj * T.uinv[d];
+            }
           }
         }
       }
@@ -424,7 +428,9 @@ int make_u_map(CUtensorMap* map, void* ptr, int64_t n_pad, int NW) {
   return GW_OK;
 }
 
-int plan_nw(int D) { return D + 3 <= 16 ? 16 : D + 3 <= 32 ? 32 : D + 3 <= 48 ? 48 : 64; }
+int plan_nw(int D) {
+  return D + 3 <= 16 ? 16 : D + 3 <= 32 ? 32 : D + 3 <= 48 ? 48 : D + 3 <= 64 ? 64 : 80;
+}
 
 template <int KP, int S, int NW, bool BF16, bool F8>
 int launch_plan(const CUtensorMap* maps, const PlanTask& T, int blocks, cudaStream_t st) {
@@ -447,8 +453,13 @@ int launch_plan_nw(int NW, const CUtensorMap* maps, const PlanTask& T, int block
     case 16: return launch_plan<KP, S, 16, BF16, F8>(maps, T, blocks, st);
     case 32: return launch_plan<KP, S, 32, BF16, F8>(maps, T, blocks, st);
     case 48: return launch_plan<KP, S, 48, BF16, F8>(maps, T, blocks, st);
-    default: return launch_plan<KP, S, 64, BF16, F8>(maps, T, blocks, st);
+    case 64: return launch_plan<KP, S, 64, BF16, F8>(maps, T, blocks, st);
+    default: break;
   }
+  // NW = 80 (D + 3 <= 80): the U tiles take more shared memory, so 128-column
+  // operands keep 2 stages
+  if constexpr (KP == 64) return launch_plan<64, S, 80, BF16, F8>(maps, T, blocks, st);
+  else return launch_plan<KP, 2, 80, BF16, F8>(maps, T, blocks, st);
 }
 
 struct PlanLayout {
@@ -506,9 +517,9 @@ PlanBufs carve_plan(Carver& c, int64_t n, int64_t m, int D, int prec) {
   B.opA = c.take<uint16_t>(static_cast<size_t>(Lt.rows_pad) * shp.KP);
   B.opB = c.take<uint16_t>(static_cast<size_t>(Lt.cols_pad) * shp.KP);
   B.mx = c.take<unsigned>(8);
-  B.umax = c.take<unsigned>(64);
+  B.umax = c.take<unsigned>(128);
   B.loga = c.take<float>(static_cast<size_t>(n));
-  B.uinv = c.take<float>(64);
+  B.uinv = c.take<float>(128);
   B.Uh = c.take<__half>(static_cast<size_t>(NW) * Lt.cols_pad);
   B.Ul = c.take<__half>(static_cast<size_t>(NW) * Lt.cols_pad);
   B.flag = c.take<int>(4);
@@ -528,7 +539,7 @@ bool plan_tc_supported(int D, int prec) {
   if (prec != GW_PREC_BF16 && prec != GW_PREC_BF16X3 && prec != GW_PREC_F16X3 &&
       prec != GW_PREC_FP8)
     return false;
-  return D + 3 <= 64 && tc_shape(D, prec).KP <= 128;
+  return D + 3 <= 80 && tc_shape(D, prec).KP <= 128;
 }
 
 size_t plan_tc_ws_bytes(int64_t n, int64_t m, int D, int prec) {
@@ -589,7 +600,7 @@ int run_plan_tc(const PlanArgs& p, int prec, const float* V, float** Wp_out, flo
     GW_LAUNCH_CHECK();
   }
   // U = [X, s, 1, log a], feature-major, per-column power-of-two scales
-  GW_CUDA_TRY(cudaMemsetAsync(B.umax, 0, 64 * sizeof(unsigned), st));
+  GW_CUDA_TRY(cudaMemsetAsync(B.umax, 0, 128 * sizeof(unsigned), st));
   u_absmax_kernel<<<kSmCount, 256, 0, st>>>(p.X, p.s, B.loga, p.n, p.D, B.umax);
   GW_LAUNCH_CHECK();
   u_prep_kernel<<<ceil_div(static_cast<int64_t>(NW) * Lt.cols_pad, 256), 256, 0, st>>>(

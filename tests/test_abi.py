@@ -144,8 +144,8 @@ def test_solve_schedule_offset_is_validated_on_the_host():
     assert b"outer_offset" in lib.gw_last_error()
     neg = Options(0.1, 0.01, 4, 10, 1, 0, 0, 0, None, None, None, 0, 0, 0.0, 0.0, 1, -1, 8)
     assert lib.gw_solve(ctypes.byref(P), ctypes.byref(neg), ctypes.byref(R), d, 1 << 30, None) == 1
-    # an FP8 solve needs the tensor-core plan sums (D + 3 <= 64): refused beyond, on the host
-    P64 = Problem(d, d, d, d, d, d, 100, 100, 64, 64)
+    # an FP8 solve needs the tensor-core plan sums (D + 3 <= 80): refused beyond, on the host
+    P64 = Problem(d, d, d, d, d, d, 100, 100, 96, 96)
     fp8 = Options(0.1, 0.01, 4, 10, 1, 4, 0, 0, None, None, None, 0, 0, 0.0, 0.0, 1, 0, 0)
     assert lib.gw_solve(ctypes.byref(P64), ctypes.byref(fp8), ctypes.byref(R), d, 1 << 30, None) == 6
     assert b"GW_PREC_FP8" in lib.gw_last_error()

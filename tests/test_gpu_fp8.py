@@ -116,14 +116,16 @@ def test_fp8_iteration_and_reuse(gw):
     assert bool((fr == fo).all()) and bool((gr == go).all())
 
 
-def test_cross_cov_fp8_matches_oracle_on_rounded_operands(gw):
+@pytest.mark.parametrize("D", [16, 64])
+def test_cross_cov_fp8_matches_oracle_on_rounded_operands(gw, D):
     """The plan-weighted sums with the exponent on E4M3 features: W_j =
     sum_i pi_ij [X_i, s_i, 1] and Gamma_{t+1} against the dense FP64 plan of
     the cost on the rounded features (Gamma_t = I / 4 so that V = Gamma_t Y is
     exact in FP32 and both sides round the same V), potentials from oracle
-    Sinkhorn iterations on that cost."""
+    Sinkhorn iterations on that cost.  D = 64 takes the plan kernel's widest
+    W accumulator (D + 3 columns in 80)."""
     from helpers import f64
-    n, m, D, eps = 1500, 1300, 16, 0.05
+    n, m, eps = 1500, 1300, 0.05
     g = W.rng(9)
     a, b = W.random_weights(n, 10, 0.3), W.random_weights(m, 11, 0.3)
     r32 = lambda x: np.asarray(x, np.float32).astype(np.float64)
@@ -177,3 +179,24 @@ def test_fp8_solve_runs_and_states_its_error(gw):
     print("relative energy error: F16X3 %.3g, FP8 %.3g" % (errs[3], errs[PREC_FP8]))
     assert errs[3] < 1e-3
     assert errs[PREC_FP8] > 10.0 * errs[3]
+
+
+def test_fp8_solve_at_d64_runs(gw):
+    """An FP8 solve with D = 64 (the large-scale configuration's width): the
+    plan sums run on tcgen05 with the same rounded features, so the annealed
+    solve stays finite with a clean status down to eps = 5e-3."""
+    import torch
+    g = W.rng(12)
+    n, D = 3000, 64
+    sig = (1.0 + np.arange(D)) ** -1.0
+    X = g.standard_normal((n, D)) * sig
+    Y = g.standard_normal((n, D)) * sig
+    X, Y = X - X.mean(0), Y - Y.mean(0)
+    dev = lambda v: torch.tensor(np.ascontiguousarray(v, np.float32), device="cuda")
+    X, Y = dev(X), dev(Y)
+    s, t = (X * X).sum(1).contiguous(), (Y * Y).sum(1).contiguous()
+    a = torch.full((n,), 1.0 / n, device="cuda")
+    res = gw.gw_solve(X, Y, s, t, a, a.clone(), 0.1, 8, 40, eps_final=0.005, prec=PREC_FP8,
+                      record=True)
+    h = res["history"].cpu().numpy()
+    assert np.isfinite(h[:, gw.EN["E"]]).all() and (h[:, gw.EN["status"]] == 0).all()
