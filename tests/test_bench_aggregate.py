@@ -46,3 +46,27 @@ def test_aggregate_max_time_sum_units_two_ranks():
 def test_aggregate_single_rank_is_identity():
     import bench
     assert bench.aggregate(1.5, 7.0, 1) == (1.5, 7.0)
+
+
+def test_kernel_traffic_follows_the_source_hash(tmp_path, monkeypatch):
+    """roofline.traffic is the DRAM count of the committed ncu summary only
+    while the kernel sources still hash to the value recorded there: a
+    copy whose softmin source differs by one byte reports none."""
+    import shutil
+    import bench
+    traffic, why = bench.tc_kernel_traffic()
+    assert isinstance(traffic, int) and traffic > 0, why
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "softmin_tc_gmm8_100k_D32_f16x3.md"),
+                root / "profiles")
+    csrc = root / "paper_2602_06658_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("gw_softmin_tc.cu", "gw_tc.cuh", "gw_tc_ops.cuh"):
+        shutil.copy(os.path.join(bench.ROOT, "paper_2602_06658_gb300", "csrc", f), csrc)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.tc_kernel_traffic()[0] == traffic
+    with open(csrc / "gw_tc.cuh", "a") as fh:
+        fh.write("\n")
+    t2, why2 = bench.tc_kernel_traffic()
+    assert t2 is None and "changed" in why2
