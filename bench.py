@@ -479,7 +479,7 @@ def tc_kernel_traffic():
 
 
 def measure_ex2_peak(gw, torch, reps=5):
-    """Measured exponential throughput of this GPU: the gw_probe_ex2 kernel
+    """Measured exponential throughput of the GPU the bench runs on: the gw_probe_ex2 kernel
     (8 independent register chains of ex2.approx per thread, 4 x 512 threads
     per SM), timed with CUDA events after warm-up; the best of `reps`
     launches, as the driver takes the best of its copy and GEMM runs."""

@@ -164,8 +164,8 @@ __device__ __forceinline__ void store_split(float* M, int64_t lo_off, int64_t e,
 }
 
 // Out_i[c] = sum_r In_i[r] M[r][c]  (M: RP x cols as hi + lo float pairs, the
-// lo block lo_off entries after the hi block), cols <= RP.  FP64 is 1/64 rate
-// on this GPU, so the sum runs in double-float on the FP32 lanes: each product
+// lo block lo_off entries after the hi block), cols <= RP.  FP64 runs at 1/64
+// of the FP32 rate on GB300, so the sum is double-float on the FP32 lanes: each product
 // In_ir (M_hi + M_lo) is exact to ~2^-48 by Dekker's TwoProduct (one FMA for
 // the error of In_ir M_hi) and accumulated by Knuth's TwoSum, the rounding
 // errors collected in a second float; the result (~44 bits) is rounded to
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const double* G, int RP, 
   __syncthreads();
   // right-looking, one barrier per pivot: the trailing update takes row j
   // unscaled (R_jr R_jc = a_jr a_jc / d_j); the rows are scaled afterwards.
-  // FP64 division is slow on this GPU, so 1 / d_{j+1} is formed once, by the
+  // FP64 division is slow on GB300, so 1 / d_{j+1} is formed once, by the
   // lane that writes d_{j+1}.  Every thread reads the same pivot, so all
   // leave the loop together.
   bool fail = bad != 0;
