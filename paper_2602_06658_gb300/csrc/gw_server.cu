@@ -429,6 +429,9 @@ bool run_job(gw_server* S, Job* J, cudaStream_t st, char* mem) {
     requeue = false;      // asked to stop during the checkpoint
     rc = J->stop_code;
   }
+  // cancelled while its last slice (or, without slicing, its whole solve) ran:
+  // the answer is the cancellation (the record it carries is complete)
+  if (!requeue && rc == GW_OK && J->stop_code == GW_ECANCELED) rc = GW_ECANCELED;
   if (requeue && rc == GW_OK) {
     J->preempted += 1;
     J->mem = nullptr;

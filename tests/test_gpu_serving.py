@@ -289,3 +289,21 @@ def test_batch_lane_matches_oracle_alone_and_in_a_batch(gw):
         ref = O.cnt_gw(a, b, X, Y, r["eps"], r["n_outer"], r["n_inner"], symmetric=True,
                        record=True)["history"][-1]["E"]
         assert abs(t_res["energy"][0] - ref) <= 1e-4 * abs(ref), (r["id"], t_res["energy"][0], ref)
+
+
+def test_cancel_without_slicing_answers_cancelled(gw):
+    """Without time slicing a running request is not interrupted; cancelled
+    while it runs, it is still answered GW_ECANCELED (with its record)."""
+    srv = gw.Server(pool_bytes=3 << 30, max_active=1)
+    try:
+        srv.submit(**long_request(50, 20000, 60, seed=61))
+        assert wait_for(lambda: srv.stats()["active"] == 1)
+        srv.cancel(50)
+        out = {}
+        t_end = time.time() + 300
+        while not out and time.time() < t_end:
+            for res in srv.poll(8, wait_ms=200):
+                out[res["id"]] = res
+    finally:
+        srv.close()
+    assert out[50]["status"] == 7
